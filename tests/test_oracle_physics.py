@@ -1,0 +1,157 @@
+"""Physics pins of the oracle's time step: brute force on tiny grids, exact mass conservation,
+mirror symmetry, Maxwell coexistence of a flat interface, the Poiseuille closed form with magic
+MRT rates, the Laplace law, and the flat-wall contact angle of the standard IVD case."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import eos as E, lbm, contact_angle as CA
+from tests.brute_force import brute_step
+
+CS07 = E.cs_config().at_reduced_temperature(0.7)
+G07, L07 = E.maxwell(CS07)
+PR086 = E.pr_paper().at_reduced_temperature(0.86)
+GPR, LPR = E.maxwell(PR086)
+
+
+def _params(name, eos, g, l, **kw):
+    base = dict(sigma=0.12, rho_l=l, rho_g=g)
+    base.update(kw)
+    return lbm.Params(name, eos, **base)
+
+
+@pytest.mark.parametrize("name,shape,kappa,wall", [
+    ("D2Q9", (8, 8), 0.3, "IVD"),
+    ("D2Q9", (7, 9), -0.05, "IVD"),
+    ("D2Q9", (8, 8), 0.0, "VD"),
+    ("D3Q19", (6, 6, 5), 0.2, "IVD"),
+    ("D3Q19", (5, 6, 6), -0.05, "IVD"),
+])
+def test_brute_force_agreement(name, shape, kappa, wall):
+    rng = np.random.default_rng(5)
+    mask = np.zeros(shape, np.uint8)
+    if len(shape) == 2:
+        mask[2:4, 3:5] = 1
+        mask[6, 1] = 1
+    else:
+        mask[1:3, 2:4, 2:4] = 1
+    geo = lbm.Geometry(mask, name)
+    rho0 = rng.uniform(G07 * 2, L07 * 0.9, shape)
+    u0 = rng.uniform(-0.01, 0.01, (geo.lat.d,) + shape)
+    p = _params(name, CS07, G07, L07, kappa=kappa, wall=wall, rho_w_const=0.2,
+                body_force=(1e-5, -2e-5, 3e-6), s_e=0.7, s_eps=1.2, s_q=1.15, s_nu=1.4, s_pi=1.05, s_m=1.3)
+    f = lbm.init_state(rho0, geo, u0)
+    f = f * (1 + 0.02 * rng.uniform(-1, 1, f.shape))
+    for _ in range(3):
+        ref = brute_step(f, geo.solid, p)
+        got = lbm.step(f, geo, p)
+        assert np.max(np.abs(got - ref)) < 1e-14
+        f = got
+
+
+def _c1_state(n_steps, noise=True):
+    wl = W.c1_parity_cylinder()
+    if not noise:
+        wl.noise = 0.0
+    geo = lbm.Geometry(wl.mask(), "D2Q9")
+    p = _params("D2Q9", CS07, G07, L07, kappa=wl.kappa)
+    f = lbm.init_state(wl.rho0(L07, G07), geo)
+    return lbm.run(f, geo, p, n_steps), f, geo, p
+
+
+def test_mass_conservation_c1():
+    f, f0, geo, p = _c1_state(200)
+    m0 = f0.sum()
+    m1 = f.sum()
+    assert abs(m1 / m0 - 1) < 1e-12
+
+
+def test_mirror_symmetry_c1():
+    """Without noise the cylinder + drop state is symmetric about x = 50 (node x <-> 100 - x)."""
+    f, _, geo, p = _c1_state(150, noise=False)
+    o, rho, u = lbm.observables(f, geo, p)
+    mir = np.roll(rho[:, ::-1], 1, axis=1)           # rho(100 - x)
+    assert np.max(np.abs(rho - mir)) < 1e-12
+    umir = np.roll(u[0][:, ::-1], 1, axis=1)
+    assert np.max(np.abs(u[0] + umir)) < 1e-13      # u_x is odd
+    assert o.u_max > 1e-5                            # the state is not trivially at rest
+
+
+def test_flat_interface_coexistence_pr():
+    """A flat liquid slab relaxes to the Maxwell coexistence densities (Sec. II.A; Sec. IV.A
+    rho_g ~ 0.38, rho_l ~ 6.5) with the consistency constant sigma = 0.11."""
+    shape = (160, 2)
+    rho0 = W.slab_density(shape, 40, 120, LPR, GPR)
+    geo = lbm.Geometry(np.zeros(shape, np.uint8), "D2Q9")
+    p = lbm.Params("D2Q9", PR086, sigma=0.11, rho_l=LPR, rho_g=GPR)
+    f = lbm.run(lbm.init_state(rho0, geo), geo, p, 6000)
+    o, rho, u = lbm.observables(f, geo, p)
+    assert abs(o.rho_max / LPR - 1) < 0.01
+    assert abs(o.rho_min / GPR - 1) < 0.05
+
+
+def test_poiseuille_closed_form():
+    """Sec. IV.B: a liquid-filled channel with a body force.  With IVD (phi >= 1) the wall density
+    equals the liquid density, so F_m = 0 and the flow is the parabola u = F_b/(2 mu) y'(L - y')
+    (walls halfway between nodes); with the 'magic' rate product 3/16 it is exact."""
+    ny, nx = 18, 3
+    mask = W.plates_mask((ny, nx))
+    geo = lbm.Geometry(mask, "D2Q9")
+    nu = 1.0 / 6.0
+    s_nu = 1.0 / (3 * nu + 0.5)
+    s_q = 8 * (2 - s_nu) / (8 - s_nu)
+    Fb = 1e-5
+    p = lbm.Params("D2Q9", PR086, sigma=0.11, rho_l=LPR, rho_g=GPR, kappa=0.2, s_nu=s_nu, s_q=s_q,
+                   body_force=(Fb, 0.0, 0.0))
+    rho0 = np.full((ny, nx), LPR)
+    f = lbm.run(lbm.init_state(rho0, geo), geo, p, 4000)
+    o, rho, u = lbm.observables(f, geo, p)
+    Lw = ny - 2.0
+    y = np.arange(ny) - 0.5
+    ua = Fb / (2 * LPR * nu) * y * (Lw - y)
+    ux = u[0][1:-1, 1]
+    err = np.sum(np.abs(ux - ua[1:-1])) / np.sum(np.abs(ua[1:-1]))   # E_r of Sec. IV.B
+    assert err < 1e-6
+    assert np.max(np.abs(rho[1:-1] - LPR)) < 1e-8 * LPR    # O(u^2) compressibility only
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Free drops: p_in - p_out = gamma / r (2D).  With interfaces about 4 nodes wide the product
+    dp * r of a drop of radius 9 and one of radius 16 agree to within 15 %."""
+    gam = []
+    for r in (10.0, 16.0):
+        n = 64
+        shape = (n, n)
+        rho0 = W.tanh_drop_density(shape, (n / 2, n / 2), r, L07, G07)
+        geo = lbm.Geometry(np.zeros(shape, np.uint8), "D2Q9")
+        p = _params("D2Q9", CS07, G07, L07)
+        f = lbm.run(lbm.init_state(rho0, geo), geo, p, 3000)
+        o, rho, u = lbm.observables(f, geo, p)
+        r_in, r_out = rho[n // 2, n // 2], rho[0, 0]
+        area = np.sum((rho - r_out) / (r_in - r_out))
+        req = np.sqrt(area / np.pi)
+        dp = float(CS07.pressure(r_in) - CS07.pressure(r_out))
+        gam.append(dp * req)
+    assert gam[0] > 0
+    assert abs(gam[0] / gam[1] - 1) < 0.15
+
+
+@pytest.mark.slow
+def test_flat_wall_angles():
+    """Sec. III.B: phi = 1 gives about 90 degrees; phi > 1 lowers theta; drho > 0 raises it."""
+    shape = (48, 80)
+    thick = 4
+    mask = W.flat_wall_mask(shape, thick)
+    geo = lbm.Geometry(mask, "D2Q9")
+    thetas = []
+    for kappa in (0.25, 0.0, -0.1 * (L07 - G07)):
+        rho0 = W.tanh_drop_density(shape, (40.0, thick + 4.0), 14.0, L07, G07)
+        rho0 = np.where(mask != 0, G07, rho0)
+        p = _params("D2Q9", CS07, G07, L07, kappa=kappa)
+        f = lbm.run(lbm.init_state(rho0, geo), geo, p, 3000)
+        o, rho, u = lbm.observables(f, geo, p)
+        th, c, r, npts = CA.contact_angle(rho, mask, L07, G07, (40.0, thick + 4.0), wall_y=thick - 0.5)
+        thetas.append(th)
+    assert thetas[0] < thetas[1] < thetas[2]
+    assert abs(thetas[1] - 90.0) < 12.0
