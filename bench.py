@@ -1,0 +1,363 @@
+"""Benchmark of the fused pseudopotential MRT-LB step with improved virtual-density walls.
+
+Default workload: the 600 x 400 D2Q9 droplet-on-cylinder (cylinder R = 60, drop r = 70, C-S EOS at
+0.6 Tc, improved virtual-density walls), FP32 deviation storage.  One bench step is one lattice
+Boltzmann time step over the whole grid.  Metric: MLUPS (million lattice-node updates per second,
+all nodes counted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2|c1|c3]
+
+Timing: W untimed steps, then K steps, each bracketed by CUDA events on the stream the step kernel
+is launched on; the L2 cache is flushed (a 2 x L2-sized buffer is rewritten) before every timed
+step, outside the events, because this grid's state fits in L2.  Under torchrun (N > 1) every rank
+runs an independent replica of the workload (no data-path collective): value = N x nodes x K / the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS (million lattice updates per second) of the fused time step"
+UNIT = "MLUPS"
+
+# DRAM bytes per launch of the step kernel measured by ncu on the workload below, keyed by a hash
+# of the kernel sources: when the sources change the figure is stale and reported as null.
+NCU_TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step.cu", "lattice.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload(name: str):
+    if name == "c1":
+        return W.c1_parity_cylinder(), "fp64"
+    if name == "c3":
+        return W.c3_sphere_256(), "fp32"
+    return W.c2_cylinder_600x400(kappa=0.15), "fp32"
+
+
+def sigma_for(wl) -> float:
+    return 0.12
+
+
+def bytes_per_lu(lattice: str, precision: str) -> int:
+    q = 9 if lattice == "D2Q9" else 19
+    return 2 * q * (8 if precision == "fp64" else 4)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# the CPU oracle (reported baseline and --impl reference)
+# ---------------------------------------------------------------------------------------------
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import eos as E, lbm
+wl = W.{ctor}
+e = (E.cs_config() if wl.eos == "CS" else E.pr_paper()).at_reduced_temperature(wl.t_over_tc)
+g, l = E.maxwell(e)
+geo = lbm.Geometry(wl.mask(), wl.lattice)
+p = lbm.Params(wl.lattice, e, sigma={sigma}, rho_l=l, rho_g=g, kappa=wl.kappa)
+f = lbm.init_state(wl.rho0(l, g), geo)
+for _ in range({warmup}):
+    f = lbm.step(f, geo, p)
+times = []
+for _ in range({steps}):
+    t = time.perf_counter()
+    f = lbm.step(f, geo, p)
+    times.append(time.perf_counter() - t)
+print(json.dumps({{"times": times, "nodes": wl.nodes}}))
+"""
+
+
+def run_oracle(wl_name: str, steps: int, warmup: int):
+    ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()"}.get(wl_name, "c2_cylinder_600x400(kappa=0.15)")
+    wl, _ = workload(wl_name)
+    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=sigma_for(wl), warmup=warmup, steps=steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["times"], d["nodes"]
+
+
+def cpu_baseline(wl_name: str, target_s: float = 15.0):
+    wl, _ = workload(wl_name)
+    # estimate the step time from one step, then take a sample of about target_s seconds
+    t1, nodes = run_oracle(wl_name, 1, 0)
+    n = max(1, min(2000, int(target_s / max(t1[0], 1e-4))))
+    times, nodes = run_oracle(wl_name, n, 0)
+    total = sum(times)
+    return {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of the {wl.name} workload ({nodes} nodes), one thread"}
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_sim(L, wl, precision, stream, rho_g, rho_l):
+    e = L.make_eos(wl.eos, 0.25, 4.0, 1.0, 0.0)
+    e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
+    cfg = L.make_config(wl.lattice, precision, wl.shape, e, sigma=sigma_for(wl), rho_l=rho_l, rho_g=rho_g,
+                        kappa=wl.kappa, rho_ref=rho_g, body=("ball", wl.body_center, wl.body_radius),
+                        drop_hint=wl.drop_center)
+    return cfg
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    from paper_1908_04443_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1908_04443_gb300 import lbmwet as L
+
+    wl, precision = workload(args.workload)
+    if args.precision:
+        precision = args.precision
+    e = L.make_eos(wl.eos, 0.25, 4.0, 1.0, 0.0)
+    e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
+    rho_g, rho_l = L.lbm_coexistence(e)
+    mask = wl.mask()
+    rho0 = wl.rho0(rho_l, rho_g)
+    stream = torch.cuda.Stream()
+    cfg = make_sim(L, wl, precision, stream, rho_g, rho_l)
+    sim = L.Simulation(cfg, mask, rho0, None, None, stream)
+
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device="cuda")
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        sim.enqueue(args.warmup)
+        sim.check()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = sim.launches()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()                      # evict the state from L2 (outside the events)
+                starts[k].record(stream)
+                sim.enqueue(1)
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    sim.check()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e_) for s, e_ in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    launches = sim.launches() - launches0
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    nodes = wl.nodes
+    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the step kernel: algorithmic bytes (read + write of every distribution once)
+    bpl = bytes_per_lu(wl.lattice, precision)
+    alg_bytes = bpl * nodes
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        with open(pk_path) as fh:
+            peaks = json.load(fh)
+    peak = peaks.get("hbm_gbs", 6800.0)
+    khash = kernel_hash()
+    traffic = NCU_TRAFFIC.get((args.workload, precision, khash))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the public API with host buffers: lbm_init from host arrays, K calls of
+    # lbm_step(h, 1) (each reads back the 4-byte device status), lbm_observables with the host
+    # density and velocity fields, lbm_destroy
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = L.lbm_init(cfg, mask, rho0, None, None, stream)
+    for _ in range(args.steps):
+        L.lbm_step(h, 1)
+    rho_h = np.empty(nodes)
+    u_h = np.empty(nodes * (2 if wl.lattice == "D2Q9" else 3))
+    obs = L.lbm_observables(h, rho_h, u_h)
+    L.lbm_destroy(h)
+    e2e_s = time.perf_counter() - t0
+    h2d = mask.size + rho0.size * 8
+    d2h = 4 * args.steps + 8 * 18 + rho_h.nbytes + u_h.nbytes
+    e2e = {"value": round(world * nodes * args.steps / e2e_s / 1e6, 2), "unit": UNIT,
+           "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
+           "definition": "lbm_init(host mask, host rho0) + K x lbm_step(h,1) + lbm_observables(host rho,u)"}
+    o_final = sim.observables()[0]
+    sim.close()
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 6), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64",
+            "data": "synthetic (seeded droplet-on-cylinder geometry of the paper's Sec. IV.A shape)",
+            "config": {"workload": wl.name, "lattice": wl.lattice, "grid": list(wl.shape[::-1]),
+                       "nodes": nodes, "precision": "fp32-deviation" if precision == "fp32" else "fp64",
+                       "eos": f"{wl.eos} T={wl.t_over_tc}Tc", "wall": f"IVD kappa={wl.kappa}",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step (2 x L2 buffer rewrite, outside the events)"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "wall_s_timed_region": round(t_wall, 4),
+            "observables_after": {"mass": o_final.mass, "rho_max": o_final.rho_max, "rho_min": o_final.rho_min,
+                                  "u_max": o_final.u_max, "theta_deg": o_final.theta_deg,
+                                  "step": o_final.step},
+            "kernel_hash": khash}
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        except Exception as exc:  # the oracle sample is a reported baseline only
+            line["cpu_baseline"] = {"error": str(exc)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    wl, precision = workload(args.workload)
+    times, nodes = run_oracle(args.workload, args.steps, args.warmup)
+    total = sum(times)
+    value = nodes * args.steps / total / 1e6
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "lattice": wl.lattice, "grid": list(wl.shape[::-1]), "nodes": nodes},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle steps of {wl.name} after {args.warmup} warm-up"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * lbmwet.h - C ABI of a GB300 (sm_103a) implementation of one time step of the pseudopotential
+ * multiple-relaxation-time lattice Boltzmann method with contact angles on curved walls:
+ * Q. Li, Y. Yu, K. H. Luo, "Implementation of contact angles in the pseudopotential lattice
+ * Boltzmann simulations with curved boundaries", arXiv:1908.04443.
+ *
+ * One time step (Sec. II.A, Sec. III.B) is, per fluid node x:
+ *   streaming with halfway bounce-back at walls        Eq. 3, Fig. 3
+ *   rho = sum_a f_a                                      Eq. 4
+ *   psi(rho) from the equation of state                  Eq. 6 with Eq. 18 (PR) or Carnahan-Starling
+ *   virtual wall density rho_w at solid nodes next to fluid, improved scheme with limiter
+ *                                                         Eqs. 16-17 (Sec. III.B); constant VD Sec. II.B
+ *   F_m = -G psi(x) sum_a w_a psi(x + e_a) e_a            Eq. 5
+ *   rho u = sum_a e_a f_a + F/2                          Eq. 4
+ *   MRT collision with the consistency forcing            Eqs. 1, 2, 7
+ *
+ * Conventions for every entry point:
+ *   - Grids are periodic in every direction; node (x, y, z) has linear index x + nx*(y + ny*z)
+ *     (x fastest).  2D lattices use nz = 1.
+ *   - Host pointers are read (or written) only during the call; the caller keeps ownership.
+ *     Device memory is owned by the handle and freed by lbm_destroy.
+ *   - All device work is enqueued on the caller's CUDA stream given at lbm_init (NULL = the
+ *     legacy default stream).  Calls that return host data synchronise that stream.
+ *   - Calls return an lbm_status and never abort or throw.  lbm_last_error() gives a message.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Device-side numerical faults (a non-positive square-root argument in Eq. 6, a non-positive
+ *     or non-finite density) set a sticky flag on the device; lbm_step and lbm_observables read
+ *     it once per call and return LBM_ERR_UNSTABLE.  Nothing on the device waits or traps.
+ */
+#ifndef LBMWET_H
+#define LBMWET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,       /* invalid argument or configuration                                */
+    LBM_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in lbm_last_error)           */
+    LBM_ERR_OOM = 3,       /* device allocation failed                                          */
+    LBM_ERR_UNSTABLE = 4,  /* the device flagged psi's square-root argument <= 0, rho <= 0 or NaN */
+    LBM_ERR_STATE = 5      /* call not valid in the handle's current state                     */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Storage/compute precision of the distributions.
+ * LBM_FP64:     f stored and computed in double.
+ * LBM_FP32_DEV: f stored in float as deviations f_a - w_a rho_ref (w_a the equilibrium weights),
+ *               computed in float; reductions of observables in double. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+
+/* Equations of state.  PR: Eq. 18 with Tc = 0.0778 a / (0.45724 b R).
+ * CS: p = rho R T (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2, eta = b rho / 4. */
+typedef enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 } lbm_eos_kind;
+
+/* Wall schemes.  IVD: Eqs. 16-17 with the limiter rho_g <= rho_w <= rho_l (Sec. III.B), the
+ * parameter in the unified form kappa >= 0 -> phi = 1 + kappa, kappa < 0 -> drho = -kappa.
+ * VD: the constant virtual density rho_w_const of Benzi et al. (Sec. II.B). */
+typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1 } lbm_wall_kind;
+
+/* Solid body used for the contact-angle observable.  BALL: a circle (2D) / sphere (3D) of
+ * radius body_radius about body_center, wall at body_radius + 1/2 (halfway bounce-back).
+ * PLANE: a flat wall at y = body_center[1] (the halfway position), liquid at larger y. */
+typedef enum { LBM_BODY_NONE = 0, LBM_BODY_BALL = 1, LBM_BODY_PLANE = 2 } lbm_body_kind;
+
+typedef struct {
+    int32_t kind;      /* lbm_eos_kind                                       */
+    double a, b, R;    /* EOS constants                                      */
+    double T;          /* absolute temperature (> 0, below the critical one) */
+    double omega;      /* PR acentric factor (Sec. IV.A uses 0.344)          */
+} lbm_eos;
+
+typedef struct {
+    int32_t lattice;            /* lbm_lattice                                                    */
+    int32_t precision;          /* lbm_precision                                                  */
+    int32_t nx, ny, nz;         /* grid; nz = 1 for D2Q9; each >= 1                               */
+    lbm_eos eos;
+    double G;                   /* interaction strength of Eqs. 5-6 (the paper uses -1)           */
+    double sigma;               /* consistency constant of Eq. 7                                  */
+    /* MRT rates s = 1/tau (Lambda of Eq. 2).  D2Q9 uses s_rho, s_e, s_eps, s_j, s_q, s_nu;
+     * D3Q19 also s_pi (3pi_xx, pi_ww) and s_m (m_x, m_y, m_z).  Each in (0, 2). */
+    double s_rho, s_e, s_eps, s_j, s_q, s_nu, s_pi, s_m;
+    double rho_l, rho_g;        /* limiter bounds (Sec. III.B); both <= 0 -> Maxwell construction */
+    double rho_ref;             /* LBM_FP32_DEV offset of the stored deviations                  */
+    double body_force[3];       /* constant body force added to F                               */
+    int32_t wall_kind;          /* lbm_wall_kind                                                  */
+    double kappa;               /* IVD parameter for every wall node (unless given per node)    */
+    double rho_w_const;         /* VD constant virtual density                                   */
+    int32_t body_kind;          /* lbm_body_kind (observables only)                              */
+    double body_center[3];
+    double body_radius;
+    double drop_hint[3];        /* a point inside the drop: interface points are unwrapped to the
+                                   periodic image nearest to it                                  */
+} lbm_config;
+
+typedef struct {
+    double mass;            /* sum of rho over fluid nodes                                     */
+    double rho_max, rho_min;/* fluid density extremes (Fig. 11)                                */
+    double u_max;           /* maximum |u| over fluid nodes, u from Eq. 4 (Fig. 10)            */
+    double theta_deg;       /* contact angle through the liquid; NaN if not measurable         */
+    double drop_center[3];  /* fitted drop circle/sphere                                       */
+    double drop_radius;
+    int64_t n_interface;    /* interface points used by the fit                                */
+    int64_t step;           /* time steps taken since lbm_init / lbm_set_state                 */
+} lbm_obs;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Coexistence densities of an EOS by the Maxwell equal-area rule (the target of the paper's
+ * thermodynamic consistency, Sec. II.A; Sec. IV.A quotes rho_g ~ 0.38, rho_l ~ 6.5 for PR at
+ * 0.86 Tc).  Host-only computation.  Errors: LBM_ERR_ARG if T is not below the critical
+ * temperature or an argument is NULL. */
+lbm_status lbm_coexistence(const lbm_eos* eos, double* rho_g, double* rho_l);
+
+/* Critical temperature of an EOS with the given constants (T and omega ignored).  PR from the
+ * definitions of a and b in Eq. 18; CS from dp/drho = d2p/drho2 = 0.  Host-only. */
+lbm_status lbm_critical_temperature(const lbm_eos* eos, double* tc);
+
+/* Create a simulation.
+ *   cfg            configuration (copied).
+ *   solid_mask     host, N = nx*ny*nz bytes, nonzero = solid.  Wall nodes are the solid nodes with
+ *                  a fluid node among their lattice neighbours (Eq. 17 needs one).
+ *   rho0           host, N doubles or NULL (uniform rho_g); values at solid nodes are ignored.
+ *   u0             host, d*N doubles (component-major: u_x for all nodes, then u_y[, u_z]) or NULL.
+ *   kappa_per_wall host, one IVD parameter per wall node in lbm_wall_nodes() order, or NULL to use
+ *                  cfg->kappa everywhere.
+ *   stream         cudaStream_t for all device work of this handle, or NULL.
+ * The initial state is f = f^eq(rho0, u0) at fluid nodes (post-streaming, step 0).
+ * Errors: LBM_ERR_ARG (bad sizes, rates, EOS, an all-solid grid), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0,
+                    const double* u0, const double* kappa_per_wall, void* stream, lbm_handle** out);
+
+/* Advance n >= 0 time steps (Eqs. 1-7 with halfway bounce-back).  Launches are asynchronous on
+ * the handle's stream except for one 4-byte read of the device error flag at the end. */
+lbm_status lbm_step(lbm_handle* h, int64_t n);
+
+/* Enqueue n >= 0 time steps without reading the device error flag (no synchronisation).  A
+ * fault flagged by these steps is reported by the next lbm_step, lbm_check or lbm_observables. */
+lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n);
+
+/* Synchronise the handle's stream and report the sticky device error flag (LBM_ERR_UNSTABLE). */
+lbm_status lbm_check(lbm_handle* h);
+
+/* Observables of the current state: mass, fluid density extremes, maximum |u| (u from Eq. 4 with
+ * the current force), and the contact angle (interface at (rho_l + rho_g)/2 fitted by a Kasa
+ * circle/sphere, points within 3 nodes of a solid dropped).  Optionally copies the density
+ * field (N doubles; 0 at solid nodes) and velocity (d*N doubles, component-major) to the host.
+ * rho_host / u_host may be NULL.  Synchronises the stream. */
+lbm_status lbm_observables(lbm_handle* h, lbm_obs* out, double* rho_host, double* u_host);
+
+/* Device-resident form of the fields of lbm_observables: writes rho (N doubles) and u (d*N
+ * doubles) into caller-owned DEVICE buffers (either may be NULL); no host copy, no sync. */
+lbm_status lbm_fields_device(lbm_handle* h, double* rho_dev, double* u_dev);
+
+/* Wall nodes (linear indices, ascending) - the order of kappa_per_wall.  idx_out may be NULL
+ * to query the count only. */
+lbm_status lbm_wall_nodes(const lbm_handle* h, int64_t* idx_out, int64_t* count);
+
+/* The post-streaming distributions f_a(x) of the current state as doubles, layout [a][node]
+ * (q*N values; 0 at solid nodes).  Velocity order: D2Q9 e0=(0,0), (1,0), (0,1), (-1,0),
+ * (0,-1), (1,1), (-1,1), (-1,-1), (1,-1); D3Q19 e0=0, +-x, +-y, +-z, then (1,1,0), (-1,-1,0),
+ * (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1),
+ * (0,-1,1).  Synchronises the stream. */
+lbm_status lbm_get_state(lbm_handle* h, double* f_host);
+
+/* Replace the state by post-streaming distributions in the layout of lbm_get_state (values at
+ * solid nodes ignored); resets the step counter to `step`. */
+lbm_status lbm_set_state(lbm_handle* h, const double* f_host, int64_t step);
+
+/* Raw checkpoint of the stored state (storage precision) plus the step counter.  With
+ * host_buf == NULL, *bytes receives the size; otherwise *bytes must be at least that size. */
+lbm_status lbm_save_state(lbm_handle* h, void* host_buf, size_t* bytes);
+lbm_status lbm_load_state(lbm_handle* h, const void* host_buf, size_t bytes);
+
+/* Set the per-wall-node IVD parameter (one per wall node, lbm_wall_nodes() order). */
+lbm_status lbm_set_kappa(lbm_handle* h, const double* kappa_per_wall);
+
+/* Resolved coexistence densities used by the limiter (after a Maxwell construction if asked). */
+lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l);
+
+/* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
+int64_t lbm_kernel_launches(const lbm_handle* h);
+
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last failing call on h (or of the last failing lbm_init when h is NULL). */
+const char* lbm_last_error(const lbm_handle* h);
+
+const char* lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMWET_H */

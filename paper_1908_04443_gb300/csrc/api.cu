@@ -1,0 +1,599 @@
+// C ABI of lbmwet (see include/lbmwet.h): handle life cycle, the step driver (CUDA-graph chunks of
+// fused step kernels), observables, state transfer and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmwet.h"
+#include "eos_host.h"
+#include "kernels.h"
+#include "lattice.cuh"
+
+using namespace lbmwet;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int GRAPH_STEPS = 16;   // steps per captured graph (even: the buffer parity is preserved)
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_config cfg{};
+    int lat = 0, prec = 0, Q = 9, D = 2;
+    long long N = 0;
+    cudaStream_t stream = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    size_t fbytes = 0;   // bytes of one distribution buffer
+    uint8_t* d_type = nullptr;
+    int* d_wall_id = nullptr;
+    double* d_kappa = nullptr;
+    unsigned* d_err = nullptr;
+    double* d_rho = nullptr;
+    double* d_u = nullptr;
+    double* d_partials = nullptr;
+    double* d_red = nullptr;
+    std::vector<int64_t> wall_nodes;
+    double rho_g = 0, rho_l = 0;
+    int64_t step = 0;
+    int64_t launches = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    DevParams dp{};
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_handle* h, lbm_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_init_error = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
+
+EosHost to_host(const lbm_eos& e) { return EosHost{e.kind, e.a, e.b, e.R, e.T, e.omega}; }
+
+void free_all(lbm_handle* h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        if (h->f[i]) cudaFree(h->f[i]);
+    }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->d_type);
+    cudaFree(h->d_wall_id);
+    cudaFree(h->d_kappa);
+    cudaFree(h->d_err);
+    cudaFree(h->d_rho);
+    cudaFree(h->d_u);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_red);
+}
+
+lbm_status check_device_error(lbm_handle* h) {
+    unsigned flags = 0;
+    CK(h, cudaMemcpyAsync(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (flags) {
+        std::string m = "device flagged:";
+        if (flags & ERR_PSI) m += " non-positive square-root argument in Eq. 6;";
+        if (flags & ERR_RHO) m += " non-positive or non-finite density;";
+        return fail(h, LBM_ERR_UNSTABLE, m);
+    }
+    return LBM_OK;
+}
+
+lbm_status ensure_obs_buffers(lbm_handle* h) {
+    if (!h->d_rho) CK(h, cudaMalloc(&h->d_rho, sizeof(double) * h->N));
+    if (!h->d_u) CK(h, cudaMalloc(&h->d_u, sizeof(double) * h->N * h->D));
+    if (!h->d_partials) CK(h, cudaMalloc(&h->d_partials, sizeof(double) * reduce_partials_size(h->N)));
+    if (!h->d_red) CK(h, cudaMalloc(&h->d_red, sizeof(double) * NRED));
+    return LBM_OK;
+}
+
+lbm_status launch_one_step(lbm_handle* h, cudaStream_t s, int from) {
+    cudaError_t e = launch_step(h->lat, h->prec, h->f[from], h->f[from ^ 1], h->dp, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+    return LBM_OK;
+}
+
+lbm_status build_graph(lbm_handle* h, int parity) {
+    if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int b = parity;
+    for (int i = 0; i < GRAPH_STEPS; ++i) {
+        cudaError_t e = launch_step(h->lat, h->prec, h->f[b], h->f[b ^ 1], h->dp, h->cap_stream);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(h->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(h, e, "graph capture");
+        }
+        b ^= 1;
+    }
+    CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+lbm_status enqueue_steps(lbm_handle* h, int64_t n) {
+    if (n < 0) return fail(h, LBM_ERR_ARG, "negative step count");
+    while (n > 0) {
+        if (n >= GRAPH_STEPS) {
+            if (!h->graph[h->cur]) {
+                lbm_status st = build_graph(h, h->cur);
+                if (st != LBM_OK) return st;
+            }
+            CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+            h->launches += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+            h->step += GRAPH_STEPS;
+        } else {
+            lbm_status st = launch_one_step(h, h->stream, h->cur);
+            if (st != LBM_OK) return st;
+            h->cur ^= 1;
+            h->launches += 1;
+            n -= 1;
+            h->step += 1;
+        }
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_OOM: return "out of device memory";
+        case LBM_ERR_UNSTABLE: return "numerically unstable state";
+        case LBM_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+lbm_status lbm_critical_temperature(const lbm_eos* eos, double* tc) {
+    if (!eos || !tc) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    if (!(eos->a > 0 && eos->b > 0 && eos->R > 0) || (eos->kind != LBM_EOS_PR && eos->kind != LBM_EOS_CS))
+        return fail(nullptr, LBM_ERR_ARG, "EOS constants must be positive and the kind PR or CS");
+    *tc = critical_temperature(to_host(*eos));
+    return LBM_OK;
+}
+
+lbm_status lbm_coexistence(const lbm_eos* eos, double* rho_g, double* rho_l) {
+    if (!eos || !rho_g || !rho_l) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    double tc;
+    lbm_status st = lbm_critical_temperature(eos, &tc);
+    if (st != LBM_OK) return st;
+    if (!(eos->T > 0 && eos->T < tc)) return fail(nullptr, LBM_ERR_ARG, "temperature must be in (0, Tc)");
+    if (!coexistence(to_host(*eos), rho_g, rho_l)) return fail(nullptr, LBM_ERR_ARG, "no coexistence found");
+    return LBM_OK;
+}
+
+lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0, const double* u0,
+                    const double* kappa_per_wall, void* stream, lbm_handle** out) {
+    if (!cfg || !solid_mask || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    const lbm_config& c = *cfg;
+    if (c.lattice != LBM_D2Q9 && c.lattice != LBM_D3Q19) return fail(nullptr, LBM_ERR_ARG, "unknown lattice");
+    if (c.precision != LBM_FP64 && c.precision != LBM_FP32_DEV) return fail(nullptr, LBM_ERR_ARG, "unknown precision");
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
+    if (c.lattice == LBM_D2Q9 && c.nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz = 1");
+    const long long N = (long long)c.nx * c.ny * c.nz;
+    if (N > (1LL << 31) / 19) return fail(nullptr, LBM_ERR_ARG, "grid too large");
+    if (!rate_ok(c.s_e) || !rate_ok(c.s_eps) || !rate_ok(c.s_q) || !rate_ok(c.s_nu) ||
+        (c.lattice == LBM_D3Q19 && (!rate_ok(c.s_pi) || !rate_ok(c.s_m))))
+        return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
+    if (!(c.G != 0.0) || !std::isfinite(c.G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
+    if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD) return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
+    double tc;
+    lbm_status st = lbm_critical_temperature(&c.eos, &tc);
+    if (st != LBM_OK) return st;
+    if (!(c.eos.T > 0 && c.eos.T < tc)) return fail(nullptr, LBM_ERR_ARG, "temperature must be in (0, Tc)");
+
+    lbm_handle* h = new lbm_handle();
+    h->cfg = c;
+    h->lat = c.lattice;
+    h->prec = c.precision;
+    h->Q = c.lattice == LBM_D2Q9 ? 9 : 19;
+    h->D = c.lattice == LBM_D2Q9 ? 2 : 3;
+    h->N = N;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (c.rho_l > 0 && c.rho_g > 0) {
+        h->rho_g = c.rho_g;
+        h->rho_l = c.rho_l;
+    } else if (!coexistence(to_host(c.eos), &h->rho_g, &h->rho_l)) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "no coexistence densities for this EOS/temperature");
+    }
+    if (!(h->rho_g < h->rho_l)) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "rho_g must be below rho_l");
+    }
+
+    // wall nodes: solid nodes with a fluid lattice neighbour (host list, ascending index)
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    std::vector<int> wall_id(N, -1);
+    long long nfluid = 0;
+    {
+        static const int E2[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                     {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+        static const int E3[19][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+                                      {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
+                                      {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        const int Q = h->Q;
+        const int(*E)[3] = h->D == 2 ? E2 : E3;
+        for (long long g = 0; g < N; ++g) {
+            if (!solid_mask[g]) {
+                ++nfluid;
+                continue;
+            }
+            const int x = int(g % nx), y = int((g / nx) % ny), z = int(g / ((long long)nx * ny));
+            for (int a = 1; a < Q; ++a) {
+                const int sx = (x + E[a][0] + nx) % nx, sy = (y + E[a][1] + ny) % ny, sz = (z + E[a][2] + nz) % nz;
+                if (!solid_mask[((long long)sz * ny + sy) * nx + sx]) {
+                    wall_id[g] = int(h->wall_nodes.size());
+                    h->wall_nodes.push_back(g);
+                    break;
+                }
+            }
+        }
+    }
+    if (nfluid == 0) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "the grid has no fluid node");
+    }
+
+    const size_t ssize = c.precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+    h->fbytes = ssize * h->Q * (size_t)N;
+    auto oom = [&](cudaError_t e, const char* what) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        free_all(h);
+        delete h;
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+    };
+    cudaError_t e;
+#define CKI(call, what) \
+    if ((e = (call)) != cudaSuccess) return oom(e, what)
+    CKI(cudaMalloc(&h->f[0], h->fbytes), "cudaMalloc f");
+    CKI(cudaMalloc(&h->f[1], h->fbytes), "cudaMalloc f");
+    CKI(cudaMalloc(&h->d_type, N), "cudaMalloc type");
+    CKI(cudaMalloc(&h->d_wall_id, sizeof(int) * N), "cudaMalloc wall_id");
+    CKI(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc err");
+    const size_t nw = h->wall_nodes.size();
+    CKI(cudaMalloc(&h->d_kappa, sizeof(double) * (nw ? nw : 1)), "cudaMalloc kappa");
+    CKI(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "memset err");
+    CKI(cudaMemsetAsync(h->f[1], 0, h->fbytes, h->stream), "memset f");
+    CKI(cudaMemcpyAsync(h->d_wall_id, wall_id.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream), "copy wall_id");
+    {
+        std::vector<double> kap(nw ? nw : 1, c.kappa);
+        if (kappa_per_wall)
+            for (size_t i = 0; i < nw; ++i) kap[i] = kappa_per_wall[i];
+        CKI(cudaMemcpyAsync(h->d_kappa, kap.data(), sizeof(double) * kap.size(), cudaMemcpyHostToDevice, h->stream),
+            "copy kappa");
+        CKI(cudaStreamSynchronize(h->stream), "sync");
+    }
+    // node classification on the device from the mask
+    {
+        uint8_t* d_mask = nullptr;
+        CKI(cudaMalloc(&d_mask, N), "cudaMalloc mask");
+        e = cudaMemcpyAsync(d_mask, solid_mask, N, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_classify(h->lat, d_mask, h->d_type, nx, ny, nz, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(d_mask);
+        if (e != cudaSuccess) return oom(e, "classify");
+        h->launches += 1;
+    }
+
+    // device parameters
+    DevParams& p = h->dp;
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.N = N;
+    p.eos_kind = c.eos.kind;
+    p.RT = c.eos.R * c.eos.T;
+    p.a = c.eos.a;
+    p.b = c.eos.b;
+    p.aphi = eos_aphi(to_host(c.eos));
+    p.G = c.G;
+    p.two_over_G = 2.0 / c.G;
+    p.s_e = c.s_e;
+    p.s_eps = c.s_eps;
+    p.s_q = c.s_q;
+    p.s_nu = c.s_nu;
+    p.s_pi = h->D == 3 ? c.s_pi : 1.0;
+    p.s_m = h->D == 3 ? c.s_m : 1.0;
+    // consistency coefficients: 12 sigma/(tau - 1/2) in 2D (Eq. 7); 114 and 33 in 3D
+    const double ke = h->D == 2 ? 12.0 : 114.0, keps = h->D == 2 ? 12.0 : 33.0;
+    p.c_e = ke * c.sigma / (1.0 / c.s_e - 0.5);
+    p.c_eps = keps * c.sigma / (1.0 / c.s_eps - 0.5);
+    p.rho_l = h->rho_l;
+    p.rho_g = h->rho_g;
+    p.rho_ref = c.precision == LBM_FP32_DEV ? c.rho_ref : 0.0;
+    p.fx = c.body_force[0];
+    p.fy = c.body_force[1];
+    p.fz = h->D == 3 ? c.body_force[2] : 0.0;
+    p.wall_kind = c.wall_kind;
+    p.kappa = c.kappa;
+    p.rho_w_const = c.rho_w_const;
+    p.kappa_w = kappa_per_wall ? h->d_kappa : nullptr;
+    p.wall_id = h->d_wall_id;
+    p.type = h->d_type;
+    p.err = h->d_err;
+
+    // initial state f = f^eq(rho0, u0), stored so that the first pull yields it
+    {
+        double* d_rho0 = nullptr;
+        double* d_u0 = nullptr;
+        CKI(cudaMalloc(&d_rho0, sizeof(double) * N), "cudaMalloc rho0");
+        std::vector<double> r0;
+        const double* src = rho0;
+        if (!rho0) {
+            r0.assign(N, h->rho_g);
+            src = r0.data();
+        }
+        e = cudaMemcpyAsync(d_rho0, src, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && u0) {
+            e = cudaMalloc(&d_u0, sizeof(double) * N * h->D);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_u0, u0, sizeof(double) * N * h->D, cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess) e = launch_init(h->lat, h->prec, h->f[0], p, d_rho0, d_u0, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(d_rho0);
+        cudaFree(d_u0);
+        if (e != cudaSuccess) return oom(e, "initial state");
+        h->launches += 1;
+    }
+#undef CKI
+    h->cur = 0;
+    h->step = 0;
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle* h, int64_t n) {
+    if (!h) return LBM_ERR_ARG;
+    lbm_status st = enqueue_steps(h, n);
+    if (st != LBM_OK) return st;
+    CK(h, cudaGetLastError());
+    return check_device_error(h);
+}
+
+lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n) {
+    if (!h) return LBM_ERR_ARG;
+    return enqueue_steps(h, n);
+}
+
+lbm_status lbm_check(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    return check_device_error(h);
+}
+
+lbm_status lbm_fields_device(lbm_handle* h, double* rho_dev, double* u_dev) {
+    if (!h) return LBM_ERR_ARG;
+    cudaError_t e = launch_fields(h->lat, h->prec, h->f[h->cur], h->dp, rho_dev, u_dev, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel");
+    h->launches += 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_handle* h, lbm_obs* out, double* rho_host, double* u_host) {
+    if (!h || !out) return LBM_ERR_ARG;
+    lbm_status st = ensure_obs_buffers(h);
+    if (st != LBM_OK) return st;
+    cudaError_t e = launch_fields(h->lat, h->prec, h->f[h->cur], h->dp, h->d_rho, h->d_u, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel");
+    const double mid = 0.5 * (h->rho_l + h->rho_g);
+    e = launch_reduce(h->D, h->d_rho, h->d_u, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid, h->cfg.drop_hint,
+                      h->d_partials, h->d_red, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce kernel");
+    h->launches += 3;
+    double red[NRED];
+    CK(h, cudaMemcpyAsync(red, h->d_red, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
+    if (rho_host) CK(h, cudaMemcpyAsync(rho_host, h->d_rho, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    if (u_host)
+        CK(h, cudaMemcpyAsync(u_host, h->d_u, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost, h->stream));
+    st = check_device_error(h);
+    if (st != LBM_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->mass = red[0];
+    out->rho_max = red[1];
+    out->rho_min = red[2];
+    out->u_max = std::sqrt(red[3]);
+    out->step = h->step;
+    out->theta_deg = NAN;
+    out->drop_radius = NAN;
+    for (int k = 0; k < 3; ++k) out->drop_center[k] = NAN;
+    const double n = red[4];
+    out->n_interface = (int64_t)n;
+    // Kasa fit: minimise sum (|p|^2 + D.p + F)^2 -> normal equations, p relative to the hint
+    const int D = h->D;
+    if (n >= D + 1) {
+        const double Sx = red[5], Sy = red[6], Sz = red[7], Sxx = red[8], Syy = red[9], Szz = red[10];
+        const double Sxy = red[11], Sxz = red[12], Syz = red[13], Sxr = red[14], Syr = red[15], Szr = red[16],
+                     Sr = red[17];
+        double A[4][5];
+        int m = D + 1;
+        if (D == 2) {
+            double B[3][4] = {{Sxx, Sxy, Sx, -Sxr}, {Sxy, Syy, Sy, -Syr}, {Sx, Sy, n, -Sr}};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 4; ++j) A[i][j] = B[i][j];
+        } else {
+            double B[4][5] = {{Sxx, Sxy, Sxz, Sx, -Sxr}, {Sxy, Syy, Syz, Sy, -Syr}, {Sxz, Syz, Szz, Sz, -Szr},
+                              {Sx, Sy, Sz, n, -Sr}};
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 5; ++j) A[i][j] = B[i][j];
+        }
+        // Gaussian elimination with partial pivoting
+        bool ok = true;
+        for (int col = 0; col < m && ok; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < m; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            if (std::fabs(A[piv][col]) < 1e-300) {
+                ok = false;
+                break;
+            }
+            for (int j = 0; j <= m; ++j) std::swap(A[col][j], A[piv][j]);
+            for (int r = 0; r < m; ++r) {
+                if (r == col) continue;
+                const double fct = A[r][col] / A[col][col];
+                for (int j = col; j <= m; ++j) A[r][j] -= fct * A[col][j];
+            }
+        }
+        if (ok) {
+            double sol[4];
+            for (int i = 0; i < m; ++i) sol[i] = A[i][m] / A[i][i];
+            double c[3] = {0, 0, 0};
+            double cc = 0;
+            for (int k = 0; k < D; ++k) {
+                c[k] = -0.5 * sol[k];
+                cc += c[k] * c[k];
+            }
+            const double r2 = cc - sol[D];
+            if (r2 > 0) {
+                const double r = std::sqrt(r2);
+                for (int k = 0; k < D; ++k) out->drop_center[k] = h->cfg.drop_hint[k] + c[k];
+                out->drop_radius = r;
+                if (h->cfg.body_kind == LBM_BODY_BALL) {
+                    const double Rw = h->cfg.body_radius + 0.5;
+                    double d2 = 0;
+                    for (int k = 0; k < D; ++k) {
+                        const double dd = out->drop_center[k] - h->cfg.body_center[k];
+                        d2 += dd * dd;
+                    }
+                    double cth = (Rw * Rw + r * r - d2) / (2.0 * Rw * r);
+                    cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
+                    out->theta_deg = std::acos(cth) * 180.0 / M_PI;
+                } else if (h->cfg.body_kind == LBM_BODY_PLANE) {
+                    double cth = -(out->drop_center[1] - h->cfg.body_center[1]) / r;
+                    cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
+                    out->theta_deg = std::acos(cth) * 180.0 / M_PI;
+                }
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_wall_nodes(const lbm_handle* h, int64_t* idx_out, int64_t* count) {
+    if (!h || !count) return LBM_ERR_ARG;
+    *count = (int64_t)h->wall_nodes.size();
+    if (idx_out)
+        for (size_t i = 0; i < h->wall_nodes.size(); ++i) idx_out[i] = h->wall_nodes[i];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_handle* h, double* f_host) {
+    if (!h || !f_host) return LBM_ERR_ARG;
+    double* d = nullptr;
+    CK(h, cudaMalloc(&d, sizeof(double) * h->Q * h->N));
+    cudaError_t e = launch_get_state(h->lat, h->prec, h->f[h->cur], h->dp, d, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f_host, d, sizeof(double) * h->Q * h->N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+    h->launches += 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_handle* h, const double* f_host, int64_t step) {
+    if (!h || !f_host) return LBM_ERR_ARG;
+    double* d = nullptr;
+    CK(h, cudaMalloc(&d, sizeof(double) * h->Q * h->N));
+    cudaError_t e = cudaMemcpyAsync(d, f_host, sizeof(double) * h->Q * h->N, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_set_state(h->lat, h->prec, h->f[h->cur], h->dp, d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+    h->launches += 1;
+    h->step = step;
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_handle* h, void* host_buf, size_t* bytes) {
+    if (!h || !bytes) return LBM_ERR_ARG;
+    const size_t need = h->fbytes + sizeof(int64_t);
+    if (!host_buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (*bytes < need) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
+    CK(h, cudaMemcpyAsync(host_buf, h->f[h->cur], h->fbytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(static_cast<char*>(host_buf) + h->fbytes, &h->step, sizeof(int64_t));
+    *bytes = need;
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_handle* h, const void* host_buf, size_t bytes) {
+    if (!h || !host_buf) return LBM_ERR_ARG;
+    if (bytes != h->fbytes + sizeof(int64_t)) return fail(h, LBM_ERR_ARG, "checkpoint size mismatch");
+    CK(h, cudaMemcpyAsync(h->f[h->cur], host_buf, h->fbytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(&h->step, static_cast<const char*>(host_buf) + h->fbytes, sizeof(int64_t));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_kappa(lbm_handle* h, const double* kappa_per_wall) {
+    if (!h || !kappa_per_wall) return LBM_ERR_ARG;
+    const size_t nw = h->wall_nodes.size();
+    if (nw) CK(h, cudaMemcpyAsync(h->d_kappa, kappa_per_wall, sizeof(double) * nw, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->dp.kappa_w) {
+        // the captured graphs hold the old parameters: rebuild them on next use
+        h->dp.kappa_w = h->d_kappa;
+        for (int i = 0; i < 2; ++i)
+            if (h->graph[i]) {
+                cudaGraphExecDestroy(h->graph[i]);
+                h->graph[i] = nullptr;
+            }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l) {
+    if (!h || !rho_g || !rho_l) return LBM_ERR_ARG;
+    *rho_g = h->rho_g;
+    *rho_l = h->rho_l;
+    return LBM_OK;
+}
+
+int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Internal interface between the C-ABI host code and the CUDA kernels (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmwet {
+
+// Everything a step kernel needs, passed by value.  Doubles are converted to the kernel's compute
+// precision inside the kernel.
+struct DevParams {
+    int nx, ny, nz;
+    long long N;                 // nodes
+    int eos_kind;                // 0 PR, 1 CS
+    double RT, a, b, aphi;       // EOS: R*T, a, b, a*phi(T) (PR)
+    double two_over_G, G;        // Eq. 6 and Eq. 5
+    double s_e, s_eps, s_q, s_nu, s_pi, s_m;
+    double c_e, c_eps;           // consistency coefficients of the e and eps rows
+    double rho_l, rho_g, rho_ref;
+    double fx, fy, fz;           // body force
+    int wall_kind;               // 0 IVD, 1 VD
+    double kappa, rho_w_const;
+    const double* kappa_w;       // per wall node (device) or null
+    const int* wall_id;          // per node: index into kappa_w (valid at wall nodes)
+    const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL
+    unsigned* err;               // sticky device error flags
+};
+
+enum Lat { LAT_D2Q9 = 0, LAT_D3Q19 = 1 };
+enum Prec { PREC_FP64 = 0, PREC_FP32 = 1 };
+
+// One fused time step fin -> fout (both post-collision states, storage precision).
+cudaError_t launch_step(int lat, int prec, const void* fin, void* fout, const DevParams& p, cudaStream_t s);
+// Pull + moments + force of the current state: rho (N doubles) and u (d*N doubles) into device
+// buffers; either may be null.
+cudaError_t launch_fields(int lat, int prec, const void* fin, const DevParams& p, double* rho, double* u,
+                          cudaStream_t s);
+// f* such that the next pull yields f^eq(rho0, u0) (rho0: N doubles, u0: d*N doubles or null).
+cudaError_t launch_init(int lat, int prec, void* fout, const DevParams& p, const double* rho0, const double* u0,
+                        cudaStream_t s);
+// Post-streaming state as doubles [q][N] (pull of the stored state).
+cudaError_t launch_get_state(int lat, int prec, const void* fin, const DevParams& p, double* fpost, cudaStream_t s);
+// Stored state from post-streaming doubles [q][N].
+cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, const double* fpost, cudaStream_t s);
+// Node-type flags from the solid mask: T_SOLID, T_WALL (solid with a fluid lattice neighbour) and
+// T_NEARWALL (within Euclidean distance 3 of a solid node).
+cudaError_t launch_classify(int lat, const uint8_t* mask, uint8_t* type, int nx, int ny, int nz, cudaStream_t s);
+
+// Observables reduction over rho/u/type: out[0..3] = mass, rho_max, rho_min, max |u|^2;
+// out[4..17] = interface-point moments (n, Sx, Sy, Sz, Sxx, Syy, Szz, Sxy, Sxz, Syz, Sx r2, Sy r2,
+// Sz r2, S r2) of the points relative to `hint`.  `partials` needs reduce_partials_size() doubles.
+constexpr int NRED = 18;
+size_t reduce_partials_size(long long N);
+cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny, int nz,
+                          double rho_mid, const double* hint, double* partials, double* out, cudaStream_t s);
+
+}  // namespace lbmwet

@@ -1,0 +1,172 @@
+// Observables reduction: total fluid mass, fluid density extremes (Fig. 11), maximum |u| (the
+// spurious-current measure of Fig. 10) and the moments of the interface points used by a Kasa
+// circle/sphere fit of the drop (contact angle).  Two launches: per-block partials with warp-shuffle
+// tree reductions, then one block combining them.  All sums in double.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.h"
+#include "lattice.cuh"
+
+namespace lbmwet {
+
+namespace {
+
+constexpr int RB = 256;   // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// kind of each of the NRED slots: 0 sum, 1 max, 2 min
+__device__ __forceinline__ int slot_kind(int k) { return k == 1 || k == 3 ? 1 : (k == 2 ? 2 : 0); }
+
+__device__ void block_combine(double (&v)[NRED], double* out) {
+    __shared__ double sh[RB / 32][NRED];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+        const int kind = slot_kind(k);
+        const double r = kind == 0 ? warp_sum(v[k]) : (kind == 1 ? warp_max(v[k]) : warp_min(v[k]));
+        if (lane == 0) sh[w][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        const int k = threadIdx.x;
+        const int kind = slot_kind(k);
+        double r = sh[0][k];
+        for (int i = 1; i < RB / 32; ++i) {
+            const double x = sh[i][k];
+            r = kind == 0 ? r + x : (kind == 1 ? fmax(r, x) : fmin(r, x));
+        }
+        out[k] = r;
+    }
+}
+
+__device__ __forceinline__ void init_slots(double (&v)[NRED]) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    v[1] = -DBL_MAX;   // rho_max
+    v[2] = DBL_MAX;    // rho_min
+    v[3] = 0.0;        // max |u|^2
+}
+
+__device__ __forceinline__ int wrapp(int v, int n) { return v >= n ? v - n : v; }
+
+template <int DIM>
+__global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ rho, const double* __restrict__ u,
+                                                     const uint8_t* __restrict__ type, int nx, int ny, int nz,
+                                                     double rho_mid, double hx, double hy, double hz,
+                                                     double* __restrict__ partials) {
+    const long long N = (long long)nx * ny * nz;
+    double v[NRED];
+    init_slots(v);
+    for (long long g = blockIdx.x * (long long)RB + threadIdx.x; g < N; g += (long long)gridDim.x * RB) {
+        const uint8_t t = type[g];
+        if (t & T_SOLID) continue;
+        const double r = rho[g];
+        v[0] += r;
+        v[1] = fmax(v[1], r);
+        v[2] = fmin(v[2], r);
+        double u2 = 0.0;
+        for (int c = 0; c < DIM; ++c) {
+            const double uc = u[(long long)c * N + g];
+            u2 += uc * uc;
+        }
+        v[3] = fmax(v[3], u2);
+        if (t & T_NEARWALL) continue;
+        const int x = int(g % nx);
+        const long long q = g / nx;
+        const int y = int(q % ny), z = int(q / ny);
+        // links +x, +y (, +z) to a fluid neighbour away from walls whose density straddles rho_mid
+        for (int axis = 0; axis < DIM; ++axis) {
+            const int xn = axis == 0 ? wrapp(x + 1, nx) : x;
+            const int yn = axis == 1 ? wrapp(y + 1, ny) : y;
+            const int zn = axis == 2 ? wrapp(z + 1, nz) : z;
+            const long long gn = ((long long)zn * ny + yn) * nx + xn;
+            const uint8_t tn = type[gn];
+            if (tn & (T_SOLID | T_NEARWALL)) continue;
+            const double rn = rho[gn];
+            if (!((r - rho_mid) * (rn - rho_mid) < 0.0)) continue;
+            const double tt = (rho_mid - r) / (rn - r);
+            double px = x, py = y, pz = z;
+            if (axis == 0) px += tt;
+            if (axis == 1) py += tt;
+            if (axis == 2) pz += tt;
+            // periodic image nearest to the hint, relative to the hint
+            double dx = px - hx, dy = py - hy, dz = (DIM == 3) ? pz - hz : 0.0;
+            dx -= nx * rint(dx / nx);
+            dy -= ny * rint(dy / ny);
+            if (DIM == 3) dz -= nz * rint(dz / nz);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            v[4] += 1.0;
+            v[5] += dx;
+            v[6] += dy;
+            v[7] += dz;
+            v[8] += dx * dx;
+            v[9] += dy * dy;
+            v[10] += dz * dz;
+            v[11] += dx * dy;
+            v[12] += dx * dz;
+            v[13] += dy * dz;
+            v[14] += dx * r2;
+            v[15] += dy * r2;
+            v[16] += dz * r2;
+            v[17] += r2;
+        }
+    }
+    block_combine(v, partials + (long long)blockIdx.x * NRED);
+}
+
+__global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+    double v[NRED];
+    init_slots(v);
+    for (int i = threadIdx.x; i < nparts; i += RB) {
+#pragma unroll
+        for (int k = 0; k < NRED; ++k) {
+            const double x = partials[(long long)i * NRED + k];
+            const int kind = slot_kind(k);
+            v[k] = kind == 0 ? v[k] + x : (kind == 1 ? fmax(v[k], x) : fmin(v[k], x));
+        }
+    }
+    block_combine(v, out);
+}
+
+int n_blocks(long long N) {
+    long long b = (N + RB - 1) / RB;
+    const long long cap = 152LL * 8;
+    if (b > cap) b = cap;
+    return int(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t reduce_partials_size(long long N) { return size_t(n_blocks(N)) * NRED; }
+
+cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny, int nz,
+                          double rho_mid, const double* hint, double* partials, double* out, cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    const int nb = n_blocks(N);
+    if (dim == 2)
+        reduce_partial<2><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    else
+        reduce_partial<3><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_final<<<1, RB, 0, s>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmwet

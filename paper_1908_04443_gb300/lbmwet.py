@@ -1,0 +1,333 @@
+"""Python binding of the lbmwet C ABI (include/lbmwet.h): argument marshalling only.
+
+Every computation runs in liblbmwet.so (CUDA kernels for sm_103a, plus its host-side setup); this
+module converts numpy arrays and Python values to the C structs and pointers the ABI takes, and
+turns non-OK status codes into exceptions.  The library is loaded from this package's directory;
+importing this module fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbmwet.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE, LBM_ERR_STATE = range(6)
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_FP64, LBM_FP32_DEV = 0, 1
+LBM_EOS_PR, LBM_EOS_CS = 0, 1
+LBM_WALL_IVD, LBM_WALL_VD = 0, 1
+LBM_BODY_NONE, LBM_BODY_BALL, LBM_BODY_PLANE = 0, 1, 2
+
+
+class lbm_eos(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
+                ("T", C.c_double), ("omega", C.c_double)]
+
+
+class lbm_config(C.Structure):
+    _fields_ = [("lattice", C.c_int32), ("precision", C.c_int32),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("eos", lbm_eos), ("G", C.c_double), ("sigma", C.c_double),
+                ("s_rho", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double), ("s_j", C.c_double),
+                ("s_q", C.c_double), ("s_nu", C.c_double), ("s_pi", C.c_double), ("s_m", C.c_double),
+                ("rho_l", C.c_double), ("rho_g", C.c_double), ("rho_ref", C.c_double),
+                ("body_force", C.c_double * 3), ("wall_kind", C.c_int32), ("kappa", C.c_double),
+                ("rho_w_const", C.c_double), ("body_kind", C.c_int32), ("body_center", C.c_double * 3),
+                ("body_radius", C.c_double), ("drop_hint", C.c_double * 3)]
+
+
+class lbm_obs(C.Structure):
+    _fields_ = [("mass", C.c_double), ("rho_max", C.c_double), ("rho_min", C.c_double),
+                ("u_max", C.c_double), ("theta_deg", C.c_double), ("drop_center", C.c_double * 3),
+                ("drop_radius", C.c_double), ("n_interface", C.c_int64), ("step", C.c_int64)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lbmwet status {status}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1908_04443_gb300.build.build() "
+                          "(this package has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    H = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "lbm_coexistence": (C.c_int, [C.POINTER(lbm_eos), dp, dp]),
+        "lbm_critical_temperature": (C.c_int, [C.POINTER(lbm_eos), dp]),
+        "lbm_init": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(H)]),
+        "lbm_step": (C.c_int, [H, C.c_int64]),
+        "lbm_enqueue_steps": (C.c_int, [H, C.c_int64]),
+        "lbm_check": (C.c_int, [H]),
+        "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
+        "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+        "lbm_wall_nodes": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_int64)]),
+        "lbm_get_state": (C.c_int, [H, C.c_void_p]),
+        "lbm_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
+        "lbm_save_state": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
+        "lbm_load_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
+        "lbm_set_kappa": (C.c_int, [H, C.c_void_p]),
+        "lbm_limiter_bounds": (C.c_int, [H, dp, dp]),
+        "lbm_kernel_launches": (C.c_int64, [H]),
+        "lbm_destroy": (None, [H]),
+        "lbm_last_error": (C.c_char_p, [H]),
+        "lbm_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
+            "lbm_observables", "lbm_fields_device", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
+            "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
+            "lbm_destroy", "lbm_last_error", "lbm_status_string")
+
+
+def library():
+    return _lib
+
+
+def _check(status: int, handle=None):
+    if status != LBM_OK:
+        msg = _lib.lbm_last_error(handle)
+        raise LbmError(status, (msg or b"").decode() or _lib.lbm_status_string(status).decode())
+
+
+def _ptr(a: Optional[np.ndarray], dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+# ---- the ABI's entry points, same names -------------------------------------------------------
+
+def lbm_coexistence(eos: lbm_eos):
+    g, l = C.c_double(), C.c_double()
+    _check(_lib.lbm_coexistence(C.byref(eos), C.byref(g), C.byref(l)))
+    return g.value, l.value
+
+
+def lbm_critical_temperature(eos: lbm_eos) -> float:
+    t = C.c_double()
+    _check(_lib.lbm_critical_temperature(C.byref(eos), C.byref(t)))
+    return t.value
+
+
+def lbm_init(cfg: lbm_config, solid_mask: np.ndarray, rho0=None, u0=None, kappa_per_wall=None, stream=None):
+    n = cfg.nx * cfg.ny * cfg.nz
+    mask, pm = _ptr(np.asarray(solid_mask).reshape(-1) != 0, np.uint8)
+    if mask.size != n:
+        raise ValueError("solid_mask size does not match the grid")
+    r, pr = _ptr(None if rho0 is None else np.asarray(rho0).reshape(-1), np.float64)
+    if r is not None and r.size != n:
+        raise ValueError("rho0 size does not match the grid")
+    u, pu = _ptr(None if u0 is None else np.asarray(u0).reshape(-1), np.float64)
+    k, pk = _ptr(None if kappa_per_wall is None else np.asarray(kappa_per_wall).reshape(-1), np.float64)
+    h = C.c_void_p()
+    st = _lib.lbm_init(C.byref(cfg), pm, pr, pu, pk, _stream_ptr(stream), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def lbm_step(h, n: int):
+    _check(_lib.lbm_step(h, int(n)), h)
+
+
+def lbm_enqueue_steps(h, n: int):
+    _check(_lib.lbm_enqueue_steps(h, int(n)), h)
+
+
+def lbm_check(h):
+    _check(_lib.lbm_check(h), h)
+
+
+def lbm_observables(h, rho_host: Optional[np.ndarray] = None, u_host: Optional[np.ndarray] = None) -> lbm_obs:
+    o = lbm_obs()
+    pr = rho_host.ctypes.data_as(C.c_void_p) if rho_host is not None else None
+    pu = u_host.ctypes.data_as(C.c_void_p) if u_host is not None else None
+    for a in (rho_host, u_host):
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+            raise ValueError("output arrays must be C-contiguous float64")
+    _check(_lib.lbm_observables(h, C.byref(o), pr, pu), h)
+    return o
+
+
+def lbm_fields_device(h, rho_dev_ptr: Optional[int], u_dev_ptr: Optional[int]):
+    _check(_lib.lbm_fields_device(h, rho_dev_ptr, u_dev_ptr), h)
+
+
+def lbm_wall_nodes(h) -> np.ndarray:
+    cnt = C.c_int64()
+    _check(_lib.lbm_wall_nodes(h, None, C.byref(cnt)), h)
+    out = np.zeros(cnt.value, dtype=np.int64)
+    _check(_lib.lbm_wall_nodes(h, out.ctypes.data_as(C.c_void_p), C.byref(cnt)), h)
+    return out
+
+
+def lbm_get_state(h, q: int, n: int) -> np.ndarray:
+    out = np.zeros(q * n, dtype=np.float64)
+    _check(_lib.lbm_get_state(h, out.ctypes.data_as(C.c_void_p)), h)
+    return out
+
+
+def lbm_set_state(h, f_post: np.ndarray, step: int = 0):
+    f, pf = _ptr(np.asarray(f_post).reshape(-1), np.float64)
+    _check(_lib.lbm_set_state(h, pf, int(step)), h)
+
+
+def lbm_save_state(h) -> bytes:
+    nb = C.c_size_t(0)
+    _check(_lib.lbm_save_state(h, None, C.byref(nb)), h)
+    buf = C.create_string_buffer(nb.value)
+    _check(_lib.lbm_save_state(h, buf, C.byref(nb)), h)
+    return buf.raw
+
+
+def lbm_load_state(h, data: bytes):
+    buf = C.create_string_buffer(data, len(data))
+    _check(_lib.lbm_load_state(h, buf, len(data)), h)
+
+
+def lbm_set_kappa(h, kappa_per_wall: np.ndarray):
+    k, pk = _ptr(np.asarray(kappa_per_wall).reshape(-1), np.float64)
+    _check(_lib.lbm_set_kappa(h, pk), h)
+
+
+def lbm_limiter_bounds(h):
+    g, l = C.c_double(), C.c_double()
+    _check(_lib.lbm_limiter_bounds(h, C.byref(g), C.byref(l)), h)
+    return g.value, l.value
+
+
+def lbm_kernel_launches(h) -> int:
+    return int(_lib.lbm_kernel_launches(h))
+
+
+def lbm_destroy(h):
+    _lib.lbm_destroy(h)
+
+
+# ---- configuration helpers ----------------------------------------------------------------------
+
+def make_eos(kind: str, a: float, b: float, R: float = 1.0, T: float = 0.0, omega: float = 0.344) -> lbm_eos:
+    return lbm_eos(kind={"PR": LBM_EOS_PR, "CS": LBM_EOS_CS}[kind], a=a, b=b, R=R, T=T, omega=omega)
+
+
+def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos, *, G=-1.0, sigma=0.12,
+                s_rho=1.0, s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1, s_nu=1.0 / 0.95, s_pi=1.1, s_m=1.1,
+                rho_l=0.0, rho_g=0.0, rho_ref=0.0, body_force=(0.0, 0.0, 0.0), wall="IVD", kappa=0.0,
+                rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0)) -> lbm_config:
+    """Build an lbm_config.  `shape` is the numpy shape (ny, nx) or (nz, ny, nx).  `body` is
+    ("ball", center, radius) or ("plane", wall_y) or None."""
+    if len(shape) == 2:
+        nz, (ny, nx) = 1, shape
+    else:
+        nz, ny, nx = shape
+    cfg = lbm_config()
+    cfg.lattice = {"D2Q9": LBM_D2Q9, "D3Q19": LBM_D3Q19}[lattice]
+    cfg.precision = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV}[precision]
+    cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+    cfg.eos = eos
+    cfg.G, cfg.sigma = G, sigma
+    cfg.s_rho, cfg.s_e, cfg.s_eps, cfg.s_j, cfg.s_q, cfg.s_nu, cfg.s_pi, cfg.s_m = s_rho, s_e, s_eps, s_j, s_q, s_nu, s_pi, s_m
+    cfg.rho_l, cfg.rho_g, cfg.rho_ref = rho_l, rho_g, rho_ref
+    for i in range(3):
+        cfg.body_force[i] = body_force[i] if i < len(body_force) else 0.0
+        cfg.drop_hint[i] = drop_hint[i] if i < len(drop_hint) else 0.0
+    cfg.wall_kind = {"IVD": LBM_WALL_IVD, "VD": LBM_WALL_VD}[wall]
+    cfg.kappa = kappa
+    cfg.rho_w_const = rho_w_const
+    cfg.body_kind = LBM_BODY_NONE
+    if body is not None:
+        if body[0] == "ball":
+            cfg.body_kind = LBM_BODY_BALL
+            for i, c in enumerate(body[1]):
+                cfg.body_center[i] = c
+            cfg.body_radius = body[2]
+        else:
+            cfg.body_kind = LBM_BODY_PLANE
+            cfg.body_center[1] = body[1]
+    return cfg
+
+
+class Simulation:
+    """Owns one lbm_handle.  Thin convenience over the entry points above."""
+
+    def __init__(self, cfg: lbm_config, solid_mask, rho0=None, u0=None, kappa_per_wall=None, stream=None):
+        self.cfg = cfg
+        self.q = 9 if cfg.lattice == LBM_D2Q9 else 19
+        self.d = 2 if cfg.lattice == LBM_D2Q9 else 3
+        self.n = cfg.nx * cfg.ny * cfg.nz
+        self.shape = (cfg.ny, cfg.nx) if self.d == 2 else (cfg.nz, cfg.ny, cfg.nx)
+        self.h = lbm_init(cfg, solid_mask, rho0, u0, kappa_per_wall, stream)
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n)
+
+    def enqueue(self, n: int = 1):
+        lbm_enqueue_steps(self.h, n)
+
+    def check(self):
+        lbm_check(self.h)
+
+    def observables(self, fields: bool = False):
+        if not fields:
+            return lbm_observables(self.h), None, None
+        rho = np.zeros(self.n)
+        u = np.zeros(self.d * self.n)
+        o = lbm_observables(self.h, rho, u)
+        return o, rho.reshape(self.shape), u.reshape((self.d,) + self.shape)
+
+    def get_state(self) -> np.ndarray:
+        return lbm_get_state(self.h, self.q, self.n).reshape((self.q,) + self.shape)
+
+    def set_state(self, f_post, step: int = 0):
+        lbm_set_state(self.h, f_post, step)
+
+    def wall_nodes(self) -> np.ndarray:
+        return lbm_wall_nodes(self.h)
+
+    def limiter_bounds(self):
+        return lbm_limiter_bounds(self.h)
+
+    def launches(self) -> int:
+        return lbm_kernel_launches(self.h)
+
+    def close(self):
+        if self.h is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

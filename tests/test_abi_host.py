@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry point that
+include/lbmwet.h declares, its host-only thermodynamics agree with the oracle, and invalid
+configurations are rejected with LBM_ERR_ARG before any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1908_04443_gb300 import lbmwet as L
+from oracle import eos as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "lbmwet.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|void|int64_t|const char\*)\s+(lbm_\w+)\s*\(", text, re.M)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert len(names) >= 19
+    lib = L.library()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.EXPORTED)
+
+
+def test_struct_layout_matches_header_order():
+    # the ctypes mirror must list the C struct members in declaration order
+    text = open(os.path.join(ROOT, "include", "lbmwet.h")).read()
+    body = re.search(r"typedef struct \{((?:(?!typedef).)*?)\} lbm_config;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    members = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1]
+        for nm in names.split(","):
+            members.append(nm.strip().split("[")[0])
+    assert members == [f[0] for f in L.lbm_config._fields_]
+
+
+@pytest.mark.parametrize("kind,tr", [("PR", 0.86), ("CS", 0.7), ("CS", 0.6)])
+def test_coexistence_matches_oracle(kind, tr):
+    o = E.pr_paper() if kind == "PR" else E.cs_config()
+    tc_o = o.tc()
+    e = L.make_eos(kind, o.a, o.b, o.R, 0.0, o.omega)
+    tc = L.lbm_critical_temperature(e)
+    assert abs(tc / tc_o - 1) < 1e-9
+    o = o.at_reduced_temperature(tr)
+    e.T = tr * tc
+    g, l = L.lbm_coexistence(e)
+    go, lo = E.maxwell(o)
+    assert abs(g / go - 1) < 1e-8
+    assert abs(l / lo - 1) < 1e-10
+
+
+def test_coexistence_rejects_supercritical():
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 1.0)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_coexistence(e)
+    assert ei.value.status == L.LBM_ERR_ARG
+
+
+def _cfg(**kw):
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    e.T = 0.7 * L.lbm_critical_temperature(e)
+    return L.make_config("D2Q9", "fp64", (8, 8), e, **kw)
+
+
+@pytest.mark.parametrize("bad", [dict(s_e=0.0), dict(s_nu=2.0), dict(s_q=-1.0), dict(G=0.0), dict(wall="VD")])
+def test_init_rejects_bad_config(bad):
+    wall_ok = bad.pop("wall", None)
+    cfg = _cfg(**bad)
+    if wall_ok:
+        cfg.wall_kind = 7
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_init(cfg, np.zeros((8, 8), np.uint8))
+    assert ei.value.status == L.LBM_ERR_ARG
+
+
+def test_init_rejects_bad_grid():
+    cfg = _cfg()
+    cfg.nz = 2          # D2Q9 with nz != 1
+    with pytest.raises(L.LbmError):
+        L.lbm_init(cfg, np.zeros(128, np.uint8))
+    cfg = _cfg()
+    cfg.eos.T = 10.0    # above the critical temperature
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_init(cfg, np.zeros((8, 8), np.uint8))
+    assert ei.value.status == L.LBM_ERR_ARG

@@ -1,0 +1,162 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 storage: within 1e-10 max-abs in density after the 1000 steps of the 100x100 cylinder
+workload, within 1e-13 after one step on assorted small grids (ragged tiles, tiny grids, all-fluid,
+per-wall-node kappa, VD walls, body force, PR and C-S).  FP32 deviation storage: within 1e-4
+relative in density.  Observables (mass, density extremes, max |u|, contact angle) are compared with
+the oracle's on the same state.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lbm, contact_angle as CA
+from tests.harness import Case, c1_case, drop_on_cylinder
+
+pytestmark = pytest.mark.gpu
+
+
+def _one_step_case(case: Case, precision="fp64", steps_before=0):
+    geo, p, f0 = case.oracle()
+    with case.gpu(precision) as sim:
+        if steps_before:
+            sim.step(steps_before)
+        f_gpu0 = sim.get_state()
+        sim.step(1)
+        f_gpu1 = sim.get_state()
+    f_ref1 = lbm.step(f_gpu0, geo, p)
+    return f_gpu0, f_gpu1, f_ref1, geo
+
+
+@pytest.mark.parametrize("shape,center,R,dc,r", [
+    ((100, 100), (50.0, 50.0), 20.0, (50.0, 95.0), 25.0),     # several full tiles, wrapping drop
+    ((37, 53), (20.3, 17.1), 9.5, (21.0, 30.0), 10.0),         # ragged tiles in x and y
+    ((8, 8), (3.0, 4.0), 1.5, (5.0, 4.0), 2.5),                # grid smaller than one tile
+    ((5, 70), (30.0, 2.0), 1.0, (40.0, 2.0), 3.0),             # thin strip
+])
+def test_one_step_fp64(shape, center, R, dc, r):
+    case = drop_on_cylinder(shape, center, R, dc, r, kappa=0.15)
+    f0, f1, ref, geo = _one_step_case(case, steps_before=3)
+    assert np.max(np.abs(f1 - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("kw", [
+    dict(kappa=-0.02),                                        # hydrophobic branch
+    dict(wall="VD", rho_w_const=0.1),                         # constant virtual density
+    dict(body_force=(1e-5, -3e-6, 0.0)),
+    dict(eos_kind="PR", t_over_tc=0.86, sigma=0.11),          # the paper's equation of state
+    dict(rates=dict(s_e=0.6, s_eps=1.5, s_q=1.2, s_nu=1.7)),
+])
+def test_one_step_variants(kw):
+    shape = (48, 40)
+    case = drop_on_cylinder(shape, (20.0, 15.0), 7.0, (20.0, 28.0), 9.0, **kw)
+    f0, f1, ref, geo = _one_step_case(case, steps_before=2)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.max(np.abs(f1 - ref)) < 1e-13 * scale
+
+
+def test_per_wall_node_kappa():
+    shape = (40, 44)
+    base = drop_on_cylinder(shape, (22.0, 15.0), 8.0, (22.0, 28.0), 8.0)
+    geo = lbm.Geometry(base.mask, "D2Q9")
+    rng = np.random.default_rng(3)
+    base.kappa = rng.uniform(-0.02, 0.4, len(geo.wall_flat))
+    with base.gpu() as sim:
+        assert np.array_equal(sim.wall_nodes(), geo.wall_flat)
+    f0, f1, ref, _ = _one_step_case(base, steps_before=2)
+    assert np.max(np.abs(f1 - ref)) < 1e-13
+
+
+def test_all_fluid_and_flat_interface():
+    shape = (64, 6)
+    g_l = Case("D2Q9", shape, np.zeros(shape, np.uint8), np.zeros(shape)).bounds()
+    rho = W.slab_density(shape, 16, 48, g_l[1], g_l[0])
+    case = Case("D2Q9", shape, np.zeros(shape, np.uint8), rho)
+    f0, f1, ref, _ = _one_step_case(case, steps_before=5)
+    assert np.max(np.abs(f1 - ref)) < 1e-13
+
+
+def test_c1_fp64_1000_steps():
+    """The 100x100 cylinder workload: FP64 GPU vs FP64 oracle after 1000 steps, 1e-10 in density."""
+    case = c1_case()
+    geo, p, f0 = case.oracle()
+    f = lbm.run(f0, geo, p, 1000)
+    o_ref, rho_ref, u_ref = lbm.observables(f, geo, p)
+    with case.gpu("fp64") as sim:
+        sim.step(1000)
+        o, rho, u = sim.observables(fields=True)
+    fl = geo.fluid
+    assert np.max(np.abs(rho[fl] - rho_ref[fl])) < 1e-10
+    assert np.max(np.abs(u[:, fl] - u_ref[:, fl])) < 1e-10
+    assert abs(o.mass - o_ref.mass) < 1e-10 * o_ref.mass
+    assert abs(o.rho_max - o_ref.rho_max) < 1e-10 and abs(o.rho_min - o_ref.rho_min) < 1e-10
+    assert abs(o.u_max - o_ref.u_max) < 1e-10
+    g, l = case.bounds()
+    th, c, r, npts = CA.contact_angle(rho_ref, case.mask, l, g, case.drop_hint, case.body[1], case.body[2])
+    assert o.n_interface == npts
+    assert abs(o.theta_deg - th) < 1e-6
+    assert abs(o.drop_radius - r) < 1e-8
+    assert o.step == 1000
+
+
+def test_c1_fp32_deviation_storage():
+    """FP32 deviation storage vs the FP64 oracle: 1e-4 relative in density after 1000 steps."""
+    case = c1_case()
+    g, l = case.bounds()
+    case.rho_ref = g
+    geo, p, f0 = case.oracle()
+    f = lbm.run(f0, geo, p, 1000)
+    o_ref, rho_ref, _ = lbm.observables(f, geo, p)
+    with case.gpu("fp32") as sim:
+        sim.step(1000)
+        o, rho, _ = sim.observables(fields=True)
+    fl = geo.fluid
+    rel = np.max(np.abs(rho[fl] - rho_ref[fl]) / rho_ref[fl])
+    assert rel < 1e-4
+    th, *_ = CA.contact_angle(rho_ref, case.mask, l, g, case.drop_hint, case.body[1], case.body[2])
+    assert abs(o.theta_deg - th) < 0.5
+
+
+def test_mass_conservation_gpu_fp64():
+    case = c1_case()
+    with case.gpu("fp64") as sim:
+        m0 = sim.observables()[0].mass
+        sim.step(500)
+        m1 = sim.observables()[0].mass
+    assert abs(m1 / m0 - 1) < 1e-12
+
+
+def test_state_round_trips():
+    case = drop_on_cylinder((30, 34), (17.0, 12.0), 6.0, (17.0, 22.0), 6.0)
+    geo, p, f0 = case.oracle()
+    with case.gpu("fp64") as sim:
+        s0 = sim.get_state()
+        assert np.max(np.abs(s0 - f0)) < 1e-15          # the initial state is f^eq(rho0, 0)
+        sim.step(7)
+        from paper_1908_04443_gb300 import lbmwet as L
+        blob = L.lbm_save_state(sim.h)
+        s7 = sim.get_state()
+        sim.step(5)
+        L.lbm_load_state(sim.h, blob)
+        assert np.array_equal(sim.get_state(), s7)
+        sim.set_state(s7, step=7)
+        assert np.max(np.abs(sim.get_state() - s7)) == 0.0
+        o = sim.observables()[0]
+        assert o.step == 7
+
+
+def test_unstable_state_is_reported():
+    """G > 0 makes the square-root argument of Eq. 6 negative: the device flags it, the call fails
+    with LBM_ERR_UNSTABLE, and the context stays usable."""
+    from paper_1908_04443_gb300 import lbmwet as L
+    case = drop_on_cylinder((16, 16), (8.0, 5.0), 2.0, (8.0, 10.0), 3.0)
+    sim = case.gpu("fp64")
+    sim.cfg.G = 1.0
+    sim.close()
+    sim = L.Simulation(sim.cfg, case.mask, case.rho0)
+    with pytest.raises(L.LbmError) as ei:
+        sim.step(2)
+    assert ei.value.status == L.LBM_ERR_UNSTABLE
+    sim.close()
+    with case.gpu("fp64") as ok:       # a fresh handle on the same context still works
+        ok.step(3)
