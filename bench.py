@@ -238,6 +238,9 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         with torch.cuda.stream(stream):
+            # a bounded spin (torch's sleep kernel) holds the stream while the host enqueues every
+            # timed step, so that no event interval includes host launch latency
+            torch.cuda._sleep(int(2e6 + 4e5 * args.steps))
             for k in range(args.steps):
                 flush.zero_()                      # evict the state from L2 (outside the events)
                 starts[k].record(stream)
