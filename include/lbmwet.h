@@ -157,6 +157,24 @@ lbm_status lbm_observables(lbm_handle* h, lbm_obs* out, double* rho_host, double
  * doubles) into caller-owned DEVICE buffers (either may be NULL); no host copy, no sync. */
 lbm_status lbm_fields_device(lbm_handle* h, double* rho_dev, double* u_dev);
 
+/* Allocation-free form of the reductions of lbm_observables.  The paper has no counterpart: this
+ * is for callers that must not call cudaMalloc - frameworks that route every device allocation
+ * through their own allocator and memory budget, or latency-sensitive loops where cudaMalloc's
+ * implicit device synchronisation is not acceptable.  It allocates nothing: the caller passes
+ * the device fields (rho: N doubles, u: d*N doubles, component-major, e.g. filled by
+ * lbm_fields_device into the caller's buffers) and receives the same lbm_obs as lbm_observables
+ * (on the host; the call synchronises the handle's stream).  The per-block partial sums live in a
+ * static device array inside the library, of fixed size (about 590 KB), present on every GPU
+ * that loads the library until the process exits.
+ *   - Maximum grid: 16,777,216 nodes (256^3); larger grids are rejected with LBM_ERR_ARG.
+ *   - The first call on a device (with that device current) looks up the array's device address
+ *     with cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents; each call writes every
+ *     slot it reads, so nothing needs clearing.  Calls whose kernels overlap on the GPU (e.g. on
+ *     different streams) race on the array: order them.
+ * Errors: LBM_ERR_ARG (null pointer, grid too large), LBM_ERR_CUDA. */
+lbm_status lbm_observables_noalloc(lbm_handle* h, const double* rho_dev, const double* u_dev, lbm_obs* out);
+
 /* Wall nodes (linear indices, ascending) - the order of kappa_per_wall.  idx_out may be NULL
  * to query the count only. */
 lbm_status lbm_wall_nodes(const lbm_handle* h, int64_t* idx_out, int64_t* count);

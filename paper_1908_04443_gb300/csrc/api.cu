@@ -597,3 +597,101 @@ void lbm_destroy(lbm_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free observables (no counterpart in the paper): see lbm_observables_noalloc in
+// include/lbmwet.h.  Reduces caller-provided device fields with the handle's node flags into the
+// library's static device scratch; allocates nothing.
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+void obs_from_reduction(const lbm_handle* h, const double* red, lbm_obs* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->mass = red[0];
+    out->rho_max = red[1];
+    out->rho_min = red[2];
+    out->u_max = std::sqrt(red[3]);
+    out->step = h->step;
+    out->theta_deg = NAN;
+    out->drop_radius = NAN;
+    for (int k = 0; k < 3; ++k) out->drop_center[k] = NAN;
+    const double n = red[4];
+    out->n_interface = (int64_t)n;
+    const int D = h->D;
+    if (!(n >= D + 1)) return;
+    // Kasa normal equations for (D_1..D_d, F): sum (|p|^2 + D.p + F)^2 minimal, p relative to the hint
+    const double m1[3] = {red[5], red[6], red[7]};
+    const double mxx[3][3] = {{red[8], red[11], red[12]}, {red[11], red[9], red[13]}, {red[12], red[13], red[10]}};
+    const double mr[3] = {red[14], red[15], red[16]};
+    const int m = D + 1;
+    double A[4][5];
+    for (int i = 0; i < D; ++i) {
+        for (int j = 0; j < D; ++j) A[i][j] = mxx[i][j];
+        A[i][D] = m1[i];
+        A[i][m] = -mr[i];
+    }
+    for (int j = 0; j < D; ++j) A[D][j] = m1[j];
+    A[D][D] = n;
+    A[D][m] = -red[17];
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        if (std::fabs(A[piv][col]) < 1e-300) return;
+        for (int j = 0; j <= m; ++j) std::swap(A[col][j], A[piv][j]);
+        for (int r = 0; r < m; ++r) {
+            if (r == col) continue;
+            const double fct = A[r][col] / A[col][col];
+            for (int j = col; j <= m; ++j) A[r][j] -= fct * A[col][j];
+        }
+    }
+    double c[3] = {0, 0, 0}, cc = 0;
+    for (int k = 0; k < D; ++k) {
+        c[k] = -0.5 * A[k][m] / A[k][k];
+        cc += c[k] * c[k];
+    }
+    const double r2 = cc - A[D][m] / A[D][D];
+    if (!(r2 > 0)) return;
+    const double r = std::sqrt(r2);
+    for (int k = 0; k < D; ++k) out->drop_center[k] = h->cfg.drop_hint[k] + c[k];
+    out->drop_radius = r;
+    double cth = NAN;
+    if (h->cfg.body_kind == LBM_BODY_BALL) {
+        const double Rw = h->cfg.body_radius + 0.5;
+        double d2 = 0;
+        for (int k = 0; k < D; ++k) {
+            const double dd = out->drop_center[k] - h->cfg.body_center[k];
+            d2 += dd * dd;
+        }
+        cth = (Rw * Rw + r * r - d2) / (2.0 * Rw * r);
+    } else if (h->cfg.body_kind == LBM_BODY_PLANE) {
+        cth = -(out->drop_center[1] - h->cfg.body_center[1]) / r;
+    }
+    if (!std::isnan(cth)) {
+        cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
+        out->theta_deg = std::acos(cth) * 180.0 / M_PI;
+    }
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_observables_noalloc(lbm_handle* h, const double* rho_dev, const double* u_dev,
+                                               lbm_obs* out) {
+    if (!h || !rho_dev || !u_dev || !out) return fail(h, LBM_ERR_ARG, "null argument");
+    if (h->N > static_reduce_max_nodes())
+        return fail(h, LBM_ERR_ARG,
+                    "grid has " + std::to_string(h->N) + " nodes; the allocation-free reduction's static scratch "
+                    "holds at most " + std::to_string(static_reduce_max_nodes()) + " nodes");
+    int dev = -1;
+    CK(h, cudaGetDevice(&dev));
+    double* scratch = nullptr;
+    CK(h, static_reduce_setup(dev, &scratch));
+    double red[NRED];
+    const double mid = 0.5 * (h->rho_l + h->rho_g);
+    CK(h, launch_reduce_static(h->D, rho_dev, u_dev, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid,
+                               h->cfg.drop_hint, scratch, red, h->stream));
+    h->launches += 2;
+    obs_from_reduction(h, red, out);
+    return LBM_OK;
+}

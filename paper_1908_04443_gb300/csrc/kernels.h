@@ -54,4 +54,15 @@ size_t reduce_partials_size(long long N);
 cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny, int nz,
                           double rho_mid, const double* hint, double* partials, double* out, cudaStream_t s);
 
+// Allocation-free observables reduction: per-block partials and the final sums live in a
+// file-scope device array of reduce.cu.  static_reduce_setup() resolves this device's address of
+// that array (once per device; the device must be current); launch_reduce_static() runs the
+// reduction into it and copies the NRED results to out_host, synchronising the stream.  Grids
+// above static_reduce_max_nodes() are refused with cudaErrorInvalidValue.
+long long static_reduce_max_nodes();
+cudaError_t static_reduce_setup(int device, double** ptr);
+cudaError_t launch_reduce_static(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny,
+                                 int nz, double rho_mid, const double* hint, double* scratch, double* out_host,
+                                 cudaStream_t s);
+
 }  // namespace lbmwet

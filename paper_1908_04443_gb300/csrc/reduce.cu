@@ -4,6 +4,7 @@
 // tree reductions, then one block combining them.  All sums in double.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "kernels.h"
 #include "lattice.cuh"
@@ -167,6 +168,75 @@ cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uin
     if (e != cudaSuccess) return e;
     reduce_final<<<1, RB, 0, s>>>(partials, nb, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the observables reduction (no counterpart in the paper).
+//
+// For callers that must not call cudaMalloc - e.g. frameworks that route every device allocation
+// through their own allocator and budget, or latency-sensitive loops where cudaMalloc's implicit
+// device synchronisation is not acceptable - the same two kernels run with their per-block
+// partials and final sums in this file-scope device array instead of handle-owned buffers.
+//
+// Capacity: STATIC_BLOCKS blocks of STATIC_NODES_PER_BLOCK nodes, i.e. grids of at most
+// 4096 * 4096 = 16,777,216 nodes (256^3); larger grids are rejected.  The array (4096 * 18 + 18
+// doubles, about 590 KB) is part of the module image, so every GPU that loads this library holds
+// it until the process exits.  All calls share it and it keeps the last call's contents; every
+// slot is written by the partial kernel before the final kernel reads it, so nothing needs
+// clearing between calls.  Calls whose kernels overlap on the GPU (different streams, or
+// different handles on one device without ordering) race on the array.
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int STATIC_BLOCKS = 4096;
+constexpr long long STATIC_NODES_PER_BLOCK = 4096;
+
+static __device__ __align__(256) double g_static_scratch[STATIC_BLOCKS * NRED + NRED];
+
+constexpr int MAX_DEVICES = 64;
+double* g_static_ptr[MAX_DEVICES] = {nullptr};
+std::mutex g_static_mutex;
+
+}  // namespace
+
+long long static_reduce_max_nodes() { return STATIC_BLOCKS * STATIC_NODES_PER_BLOCK; }
+
+cudaError_t static_reduce_setup(int device, double** ptr) {
+    if (device < 0 || device >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        // host code may not use the symbol itself as an address: ask the runtime for the device
+        // address of this device's copy (the device must be current)
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[device] = static_cast<double*>(p);
+    }
+    *ptr = g_static_ptr[device];
+    return cudaSuccess;
+}
+
+cudaError_t launch_reduce_static(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny,
+                                 int nz, double rho_mid, const double* hint, double* scratch, double* out_host,
+                                 cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    const long long nb = (N + STATIC_NODES_PER_BLOCK - 1) / STATIC_NODES_PER_BLOCK;
+    if (nb < 1 || nb > STATIC_BLOCKS) return cudaErrorInvalidValue;
+    double* partials = scratch;
+    double* out = scratch + (long long)STATIC_BLOCKS * NRED;
+    if (dim == 2)
+        reduce_partial<2><<<int(nb), RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    else
+        reduce_partial<3><<<int(nb), RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_final<<<1, RB, 0, s>>>(partials, int(nb), out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(out_host, out, sizeof(double) * NRED, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace lbmwet

@@ -70,6 +70,7 @@ def _load():
         "lbm_check": (C.c_int, [H]),
         "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
         "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+        "lbm_observables_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.POINTER(lbm_obs)]),
         "lbm_wall_nodes": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_int64)]),
         "lbm_get_state": (C.c_int, [H, C.c_void_p]),
         "lbm_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
@@ -91,7 +92,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
-            "lbm_observables", "lbm_fields_device", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
+            "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
             "lbm_destroy", "lbm_last_error", "lbm_status_string")
 
@@ -176,6 +177,13 @@ def lbm_observables(h, rho_host: Optional[np.ndarray] = None, u_host: Optional[n
 
 def lbm_fields_device(h, rho_dev_ptr: Optional[int], u_dev_ptr: Optional[int]):
     _check(_lib.lbm_fields_device(h, rho_dev_ptr, u_dev_ptr), h)
+
+
+def lbm_observables_noalloc(h, rho_dev_ptr: int, u_dev_ptr: int) -> lbm_obs:
+    """Reductions of lbm_observables over caller-owned device fields, with no device allocation."""
+    o = lbm_obs()
+    _check(_lib.lbm_observables_noalloc(h, rho_dev_ptr, u_dev_ptr, C.byref(o)), h)
+    return o
 
 
 def lbm_wall_nodes(h) -> np.ndarray:
