@@ -1,11 +1,13 @@
 """Benchmark of the fused pseudopotential MRT-LB step with improved virtual-density walls.
 
 Default workload: the 600 x 400 D2Q9 droplet-on-cylinder (cylinder R = 60, drop r = 70, C-S EOS at
-0.6 Tc, improved virtual-density walls), FP32 deviation storage.  One bench step is one lattice
-Boltzmann time step over the whole grid.  Metric: MLUPS (million lattice-node updates per second,
-all nodes counted).
+0.6 Tc, improved virtual-density walls, FP32 deviation storage) over its sweep of seven wall
+parameters from hydrophilic to hydrophobic, stepped as one batch (one persistent kernel launch per
+time step).  One bench step is one lattice Boltzmann time step of every grid.  Metric: MLUPS
+(million lattice-node updates per second, all nodes counted).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2|c1|c3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c2single|c1|c3|c4] [--precision fp32|fp64]
 
 Timing: W untimed steps, then K steps, each bracketed by CUDA events on the stream the step kernel
 is launched on; the L2 cache is flushed (a 2 x L2-sized buffer is rewritten) before every timed
@@ -49,12 +51,26 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+WORKLOADS = ("c2", "c2single", "c1", "c3", "c4")
+
+
 def workload(name: str):
+    """(list of instances, precision, label).  c2: the 600 x 400 cylinder workload over its sweep of
+    seven wall parameters (hydrophilic to hydrophobic), run as one batch; c2single: one of them;
+    c1: the 100 x 100 FP64 parity grid; c3: the 256^3 D3Q19 sphere; c4: 96 uneven 2D instances."""
     if name == "c1":
-        return W.c1_parity_cylinder(), "fp64"
+        return [W.c1_parity_cylinder()], "fp64", "c1_d2q9_fp64_100x100"
     if name == "c3":
-        return W.c3_sphere_256(), "fp32"
-    return W.c2_cylinder_600x400(kappa=0.15), "fp32"
+        return [W.c3_sphere_256()], "fp32", "c3_d3q19_256cube_fp32"
+    if name == "c4":
+        return W.c4_batch(96), "fp32", "c4_batch96_d2q9_128to512_fp32"
+    if name == "c2single":
+        return [W.c2_cylinder_600x400(kappa=0.15)], "fp32", "c2_d2q9_600x400_fp32_single"
+    return None, "fp32", "c2_d2q9_600x400_fp32_sweep7"
+
+
+def c2_sweep(rho_l, rho_g):
+    return [W.c2_cylinder_600x400(kappa=k) for k in W.c2_cylinder_sweep_kappas(rho_l, rho_g)]
 
 
 def sigma_for(wl) -> float:
@@ -152,9 +168,9 @@ print(json.dumps({{"times": times, "nodes": wl.nodes}}))
 
 
 def run_oracle(wl_name: str, steps: int, warmup: int):
-    ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()"}.get(wl_name, "c2_cylinder_600x400(kappa=0.15)")
-    wl, _ = workload(wl_name)
-    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=sigma_for(wl), warmup=warmup, steps=steps)
+    ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()", "c4": "c4_batch(96)[0]"}.get(
+        wl_name, "c2_cylinder_600x400(kappa=0.15)")
+    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -164,14 +180,13 @@ def run_oracle(wl_name: str, steps: int, warmup: int):
 
 
 def cpu_baseline(wl_name: str, target_s: float = 15.0):
-    wl, _ = workload(wl_name)
     # estimate the step time from one step, then take a sample of about target_s seconds
     t1, nodes = run_oracle(wl_name, 1, 0)
     n = max(1, min(2000, int(target_s / max(t1[0], 1e-4))))
     times, nodes = run_oracle(wl_name, n, 0)
     total = sum(times)
     return {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 oracle steps of the {wl.name} workload ({nodes} nodes), one thread"}
+            "sample": f"{n} FP64 oracle steps of one {nodes}-node grid of the workload, one thread"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -185,13 +200,48 @@ def dist_setup():
     return world, rank, local
 
 
-def make_sim(L, wl, precision, stream, rho_g, rho_l):
+def make_cfg(L, wl, precision, rho_g, rho_l):
     e = L.make_eos(wl.eos, 0.25, 4.0, 1.0, 0.0)
     e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
-    cfg = L.make_config(wl.lattice, precision, wl.shape, e, sigma=sigma_for(wl), rho_l=rho_l, rho_g=rho_g,
-                        kappa=wl.kappa, rho_ref=rho_g, body=("ball", wl.body_center, wl.body_radius),
-                        drop_hint=wl.drop_center)
-    return cfg
+    return L.make_config(wl.lattice, precision, wl.shape, e, sigma=sigma_for(wl), rho_l=rho_l, rho_g=rho_g,
+                         kappa=wl.kappa, rho_ref=rho_g, body=("ball", wl.body_center, wl.body_radius),
+                         drop_hint=wl.drop_center)
+
+
+class Runner:
+    """One grid (lbm_handle) or several (lbm_batch) behind the same few calls."""
+
+    def __init__(self, L, cfgs, masks, rho0s, stream):
+        self.L = L
+        self.batch = len(cfgs) > 1
+        if self.batch:
+            self.b = L.lbm_batch_init(cfgs, masks, rho0s, None, stream)
+            self.handles = [L.lbm_batch_handle(self.b, i) for i in range(len(cfgs))]
+        else:
+            self.b = None
+            self.h = L.lbm_init(cfgs[0], masks[0], rho0s[0], None, None, stream)
+            self.handles = [self.h]
+
+    def enqueue(self, n):
+        if self.batch:
+            self.L.lbm_batch_enqueue_steps(self.b, n)
+        else:
+            self.L.lbm_enqueue_steps(self.h, n)
+
+    def step(self, n):
+        if self.batch:
+            self.L.lbm_batch_step(self.b, n)
+        else:
+            self.L.lbm_step(self.h, n)
+
+    def launches(self):
+        return self.L.lbm_batch_kernel_launches(self.b) if self.batch else self.L.lbm_kernel_launches(self.h)
+
+    def close(self):
+        if self.batch:
+            self.L.lbm_batch_destroy(self.b)
+        else:
+            self.L.lbm_destroy(self.h)
 
 
 def run_ours(args):
@@ -209,28 +259,38 @@ def run_ours(args):
         dist.barrier()
     from paper_1908_04443_gb300 import lbmwet as L
 
-    wl, precision = workload(args.workload)
+    wls, precision, label = workload(args.workload)
     if args.precision:
         precision = args.precision
-    e = L.make_eos(wl.eos, 0.25, 4.0, 1.0, 0.0)
-    e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    tc = L.lbm_critical_temperature(e)
+    t_over_tc = 0.6 if args.workload in ("c2", "c2single") else (wls[0].t_over_tc)
+    e.T = t_over_tc * tc
     rho_g, rho_l = L.lbm_coexistence(e)
-    mask = wl.mask()
-    rho0 = wl.rho0(rho_l, rho_g)
+    if wls is None:
+        wls = c2_sweep(rho_l, rho_g)
+    if args.workload == "c4":
+        # negative draws are drho in units of (rho_l - rho_g)
+        for wl in wls:
+            if wl.kappa < 0:
+                wl.kappa *= (rho_l - rho_g)
+    lattice = wls[0].lattice
+    cfgs = [make_cfg(L, wl, precision, rho_g, rho_l) for wl in wls]
+    masks = [wl.mask() for wl in wls]
+    rho0s = [wl.rho0(rho_l, rho_g) for wl in wls]
+    nodes = sum(wl.nodes for wl in wls)
     stream = torch.cuda.Stream()
-    cfg = make_sim(L, wl, precision, stream, rho_g, rho_l)
-    sim = L.Simulation(cfg, mask, rho0, None, None, stream)
+    run = Runner(L, cfgs, masks, rho0s, stream)
 
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device="cuda")
 
-    # warm-up
     with torch.cuda.stream(stream):
-        sim.enqueue(args.warmup)
-        sim.check()
+        run.enqueue(args.warmup)
+    run.step(0)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches0 = sim.launches()
+    launches0 = run.launches()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -244,26 +304,25 @@ def run_ours(args):
             for k in range(args.steps):
                 flush.zero_()                      # evict the state from L2 (outside the events)
                 starts[k].record(stream)
-                sim.enqueue(1)
+                run.enqueue(1)
                 ends[k].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
-    sim.check()
+    run.step(0)                                    # reads the device error flag
     if dist is not None:
         dist.barrier()
-    step_ms = [s.elapsed_time(e_) for s, e_ in zip(starts, ends)]
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     total_ms = sum(step_ms)
-    launches = sim.launches() - launches0
+    launches = run.launches() - launches0
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    nodes = wl.nodes
     value = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
     ms_per_step = total_ms / args.steps
 
     # roofline of the step kernel: algorithmic bytes (read + write of every distribution once)
-    bpl = bytes_per_lu(wl.lattice, precision)
+    bpl = bytes_per_lu(lattice, precision)
     alg_bytes = bpl * nodes
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
     peaks = {}
@@ -276,45 +335,76 @@ def run_ours(args):
     traffic = NCU_TRAFFIC.get((args.workload, precision, khash))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes}
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel": "fused_step" + ("_batched" if run.batch else "")}
 
-    # end to end through the public API with host buffers: lbm_init from host arrays, K calls of
-    # lbm_step(h, 1) (each reads back the 4-byte device status), lbm_observables with the host
-    # density and velocity fields, lbm_destroy
+    # batched launch vs one launch per instance (no L2 flush: back-to-back steps)
+    batched_vs_separate = None
+    if run.batch and not args.no_extras:
+        seps = [L.lbm_init(c, m, r, None, None, stream) for c, m, r in zip(cfgs, masks, rho0s)]
+        kk = max(16, args.steps // 2)
+        def timed(fn):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                fn(2)
+                torch.cuda._sleep(int(2e6 + 4e5 * kk))
+                ev0.record(stream)
+                fn(kk)
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1) / kk
+        def sep(n):
+            for _ in range(n):
+                for h in seps:
+                    L.lbm_enqueue_steps(h, 1)
+        ms_b = timed(run.enqueue)
+        ms_s = timed(sep)
+        for h in seps:
+            L.lbm_destroy(h)
+        batched_vs_separate = {"instances": len(cfgs), "steps": kk, "batched_ms_per_step": round(ms_b, 5),
+                               "separate_ms_per_step": round(ms_s, 5), "speedup": round(ms_s / ms_b, 3),
+                               "note": "one batched launch per step vs one launch per instance per step; "
+                                       "L2 not flushed"}
+    run.close()
+
+    # end to end through the public API with host buffers: init from host arrays, K calls of the
+    # stepping entry point with one step each (each reads back the 4-byte device status), then the
+    # observables with the host density and velocity fields of every instance
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = L.lbm_init(cfg, mask, rho0, None, None, stream)
+    r2 = Runner(L, cfgs, masks, rho0s, stream)
     for _ in range(args.steps):
-        L.lbm_step(h, 1)
-    rho_h = np.empty(nodes)
-    u_h = np.empty(nodes * (2 if wl.lattice == "D2Q9" else 3))
-    obs = L.lbm_observables(h, rho_h, u_h)
-    L.lbm_destroy(h)
+        r2.step(1)
+    d2h = 4 * args.steps
+    dim = 2 if lattice == "D2Q9" else 3
+    for h, wl in zip(r2.handles, wls):
+        rho_h = np.empty(wl.nodes)
+        u_h = np.empty(wl.nodes * dim)
+        L.lbm_observables(h, rho_h, u_h)
+        d2h += rho_h.nbytes + u_h.nbytes + 8 * 18
+    r2.close()
     e2e_s = time.perf_counter() - t0
-    h2d = mask.size + rho0.size * 8
-    d2h = 4 * args.steps + 8 * 18 + rho_h.nbytes + u_h.nbytes
+    h2d = sum(m.size + r.size * 8 for m, r in zip(masks, rho0s))
     e2e = {"value": round(world * nodes * args.steps / e2e_s / 1e6, 2), "unit": UNIT,
            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
-           "definition": "lbm_init(host mask, host rho0) + K x lbm_step(h,1) + lbm_observables(host rho,u)"}
-    o_final = sim.observables()[0]
-    sim.close()
+           "definition": "init from host mask/rho0 + K x step(1) (4-byte status read each) + observables "
+                         "with host rho and u of every instance"}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 6), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64",
-            "data": "synthetic (seeded droplet-on-cylinder geometry of the paper's Sec. IV.A shape)",
-            "config": {"workload": wl.name, "lattice": wl.lattice, "grid": list(wl.shape[::-1]),
-                       "nodes": nodes, "precision": "fp32-deviation" if precision == "fp32" else "fp64",
-                       "eos": f"{wl.eos} T={wl.t_over_tc}Tc", "wall": f"IVD kappa={wl.kappa}",
+            "data": "synthetic (seeded drop-on-cylinder/sphere geometries shaped like the paper's Sec. IV)",
+            "config": {"workload": label, "lattice": lattice, "instances": len(wls),
+                       "grids": sorted(set(tuple(wl.shape[::-1]) for wl in wls))[:4], "nodes": nodes,
+                       "precision": "fp32-deviation" if precision == "fp32" else "fp64",
+                       "eos": f"C-S T={t_over_tc}Tc", "wall": "IVD", "kappas": [round(wl.kappa, 5) for wl in wls][:8],
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed before every timed step (2 x L2 buffer rewrite, outside the events)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "wall_s_timed_region": round(t_wall, 4),
-            "observables_after": {"mass": o_final.mass, "rho_max": o_final.rho_max, "rho_min": o_final.rho_min,
-                                  "u_max": o_final.u_max, "theta_deg": o_final.theta_deg,
-                                  "step": o_final.step},
             "kernel_hash": khash}
+    if batched_vs_separate:
+        line["batched_vs_separate"] = batched_vs_separate
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -331,7 +421,7 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return
-    wl, precision = workload(args.workload)
+    wls, precision, label = workload(args.workload)
     times, nodes = run_oracle(args.workload, args.steps, args.warmup)
     total = sum(times)
     value = nodes * args.steps / total / 1e6
@@ -339,9 +429,10 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": wl.name, "lattice": wl.lattice, "grid": list(wl.shape[::-1]), "nodes": nodes},
+            "config": {"workload": label, "per_step_sample": f"one {nodes}-node grid of the workload"},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} FP64 oracle steps of {wl.name} after {args.warmup} warm-up"},
+                             "sample": f"{args.steps} FP64 oracle steps of one {nodes}-node grid of {label} "
+                                       f"after {args.warmup} warm-up"},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -352,9 +443,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-vs-separate comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -204,6 +204,34 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
+/* ---- Batches (no counterpart in the paper: many independent grids of one physics) ----------
+ * A batch steps n grids with one persistent kernel launch per time step: a grid of CTAs sized to
+ * the GPU walks a work list of (instance, tile) items covering every instance; the launches of
+ * lbm_batch_step are captured in CUDA graphs of 16 steps like lbm_step's.  Instances share
+ * lattice, precision and physics (EOS, G, sigma, rates, limiter bounds, rho_ref, body force,
+ * wall scheme); grid size, kappa, per-wall-node kappa, body and drop hint may differ. */
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch of n >= 1 instances: cfgs[i], masks[i], rho0s[i] (array may be NULL, entries may
+ * be NULL) and kappas_per_wall[i] (array or entries may be NULL) as in lbm_init.  Errors as
+ * lbm_init, plus LBM_ERR_ARG if the instances' physics differ. */
+lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* const* masks, const double* const* rho0s,
+                          const double* const* kappas_per_wall, void* stream, lbm_batch** out);
+/* Advance every instance n steps; reads the batch's device error flag once at the end. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
+/* Enqueue n steps without reading the error flag (checked by the next lbm_batch_step). */
+lbm_status lbm_batch_enqueue_steps(lbm_batch* b, int64_t n);
+/* Observables of every instance (out_n has lbm_batch_size() entries). */
+lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n);
+/* Handle of instance i, owned by the batch: valid for lbm_observables, lbm_fields_device,
+ * lbm_get_state, lbm_set_state, lbm_save_state/lbm_load_state, lbm_wall_nodes; lbm_step and
+ * lbm_enqueue_steps on it return LBM_ERR_STATE and lbm_destroy ignores it.  NULL if i is out of range. */
+lbm_handle* lbm_batch_handle(lbm_batch* b, int32_t i);
+int32_t lbm_batch_size(const lbm_batch* b);
+int64_t lbm_batch_kernel_launches(const lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
 void lbm_destroy(lbm_handle* h);
 
 /* Message of the last failing call on h (or of the last failing lbm_init when h is NULL). */

@@ -45,6 +45,7 @@ struct lbm_handle {
     cudaStream_t cap_stream = nullptr;
     DevParams dp{};
     std::string err;
+    bool batch_member = false;   // owned and stepped by an lbm_batch
 };
 
 namespace {
@@ -379,6 +380,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
 
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
     if (!h) return LBM_ERR_ARG;
+    if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_step");
     lbm_status st = enqueue_steps(h, n);
     if (st != LBM_OK) return st;
     CK(h, cudaGetLastError());
@@ -387,6 +389,7 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
 
 lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n) {
     if (!h) return LBM_ERR_ARG;
+    if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_enqueue_steps");
     return enqueue_steps(h, n);
 }
 
@@ -589,7 +592,7 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
 
 void lbm_destroy(lbm_handle* h) {
-    if (!h) return;
+    if (!h || h->batch_member) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     free_all(h);
@@ -695,3 +698,244 @@ extern "C" lbm_status lbm_observables_noalloc(lbm_handle* h, const double* rho_d
     obs_from_reduction(h, red, out);
     return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Batches: many grids of one physics stepped by one persistent kernel per time step.
+// ---------------------------------------------------------------------------------------------
+
+struct lbm_batch {
+    std::vector<lbm_handle*> inst;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int lat = 0, prec = 0;
+    DevParams phys{};
+    unsigned* d_err = nullptr;
+    BatchInstance* d_insts = nullptr;
+    BatchItem* d_items = nullptr;
+    int n_items = 0, ctas = 1, cur = 0;
+    int64_t step = 0, launches = 0, nodes = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_init_error = msg;
+    return s;
+}
+
+#define CKB(b, call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,             \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    } while (0)
+
+bool same_physics(const lbm_config& a, const lbm_config& b) {
+    return a.lattice == b.lattice && a.precision == b.precision && a.eos.kind == b.eos.kind && a.eos.a == b.eos.a &&
+           a.eos.b == b.eos.b && a.eos.R == b.eos.R && a.eos.T == b.eos.T && a.eos.omega == b.eos.omega &&
+           a.G == b.G && a.sigma == b.sigma && a.s_rho == b.s_rho && a.s_e == b.s_e && a.s_eps == b.s_eps &&
+           a.s_j == b.s_j && a.s_q == b.s_q && a.s_nu == b.s_nu && a.s_pi == b.s_pi && a.s_m == b.s_m &&
+           a.rho_l == b.rho_l && a.rho_g == b.rho_g && a.rho_ref == b.rho_ref && a.body_force[0] == b.body_force[0] &&
+           a.body_force[1] == b.body_force[1] && a.body_force[2] == b.body_force[2] && a.wall_kind == b.wall_kind &&
+           a.rho_w_const == b.rho_w_const;
+}
+
+void batch_free(lbm_batch* b) {
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_err);
+    cudaFree(b->d_insts);
+    cudaFree(b->d_items);
+    for (lbm_handle* h : b->inst) {
+        h->batch_member = false;
+        lbm_destroy(h);
+    }
+    b->inst.clear();
+}
+
+lbm_status batch_launch(lbm_batch* b, cudaStream_t s, int parity) {
+    cudaError_t e = launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status batch_graph(lbm_batch* b, int parity) {
+    if (!b->cap_stream) CKB(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CKB(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int par = parity;
+    for (int i = 0; i < GRAPH_STEPS; ++i) {
+        cudaError_t e = launch_step_batched(b->lat, b->prec, par, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas,
+                                            b->cap_stream);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(b->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        par ^= 1;
+    }
+    CKB(b, cudaStreamEndCapture(b->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status batch_enqueue(lbm_batch* b, int64_t n) {
+    if (n < 0) return bfail(b, LBM_ERR_ARG, "negative step count");
+    while (n > 0) {
+        if (n >= GRAPH_STEPS) {
+            if (!b->graph[b->cur]) {
+                lbm_status st = batch_graph(b, b->cur);
+                if (st != LBM_OK) return st;
+            }
+            CKB(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+            n -= GRAPH_STEPS;
+            b->step += GRAPH_STEPS;
+            b->launches += GRAPH_STEPS;
+        } else {
+            lbm_status st = batch_launch(b, b->stream, b->cur);
+            if (st != LBM_OK) return st;
+            b->cur ^= 1;
+            n -= 1;
+            b->step += 1;
+            b->launches += 1;
+        }
+    }
+    for (lbm_handle* h : b->inst) {
+        h->cur = b->cur;
+        h->step = b->step;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* const* masks, const double* const* rho0s,
+                          const double* const* kappas_per_wall, void* stream, lbm_batch** out) {
+    if (n < 1 || !cfgs || !masks || !out) return bfail(nullptr, LBM_ERR_ARG, "null argument or empty batch");
+    *out = nullptr;
+    for (int i = 1; i < n; ++i)
+        if (!same_physics(cfgs[0], cfgs[i]))
+            return bfail(nullptr, LBM_ERR_ARG, "instance " + std::to_string(i) + " differs from instance 0 in lattice, "
+                                                "precision or physics (only grid, kappa, body and hint may differ)");
+    lbm_batch* b = new lbm_batch();
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->lat = cfgs[0].lattice;
+    b->prec = cfgs[0].precision;
+    for (int i = 0; i < n; ++i) {
+        lbm_handle* h = nullptr;
+        lbm_status st = lbm_init(&cfgs[i], masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
+                                 kappas_per_wall ? kappas_per_wall[i] : nullptr, stream, &h);
+        if (st != LBM_OK) {
+            const std::string m = "instance " + std::to_string(i) + ": " + g_init_error;
+            batch_free(b);
+            delete b;
+            return bfail(nullptr, st, m);
+        }
+        h->batch_member = true;
+        b->inst.push_back(h);
+        b->nodes += h->N;
+    }
+    int tx, ty, tz;
+    step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
+    std::vector<BatchInstance> insts(n);
+    std::vector<BatchItem> items;
+    for (int i = 0; i < n; ++i) {
+        lbm_handle* h = b->inst[i];
+        BatchInstance& d = insts[i];
+        d.nx = h->cfg.nx;
+        d.ny = h->cfg.ny;
+        d.nz = h->cfg.nz;
+        d.N = int(h->N);
+        d.f[0] = h->f[0];
+        d.f[1] = h->f[1];
+        d.type = h->d_type;
+        d.wall_id = h->d_wall_id;
+        d.kappa_w = h->dp.kappa_w;
+        d.kappa = h->dp.kappa;
+        for (int z = 0; z < d.nz; z += tz)
+            for (int y = 0; y < d.ny; y += ty)
+                for (int x = 0; x < d.nx; x += tx) items.push_back(BatchItem{i, x, y, z});
+    }
+    b->n_items = int(items.size());
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long cap = (long long)sms * batched_ctas_per_sm(b->lat, b->prec);
+    b->ctas = int(b->n_items < cap ? b->n_items : cap);
+    b->phys = b->inst[0]->dp;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        const std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+    }
+    b->phys.err = b->d_err;
+    (void)st;
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_enqueue_steps(lbm_batch* b, int64_t n) {
+    if (!b) return LBM_ERR_ARG;
+    return batch_enqueue(b, n);
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+    if (!b) return LBM_ERR_ARG;
+    lbm_status st = batch_enqueue(b, n);
+    if (st != LBM_OK) return st;
+    unsigned flags = 0;
+    CKB(b, cudaMemcpyAsync(&flags, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    CKB(b, cudaStreamSynchronize(b->stream));
+    if (flags) return bfail(b, LBM_ERR_UNSTABLE, "device flagged a non-positive square-root argument or density");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n) {
+    if (!b || !out_n) return LBM_ERR_ARG;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        lbm_status st = lbm_observables(b->inst[i], &out_n[i], nullptr, nullptr);
+        if (st != LBM_OK) return bfail(b, st, "instance " + std::to_string(i) + ": " + b->inst[i]->err);
+    }
+    return LBM_OK;
+}
+
+lbm_handle* lbm_batch_handle(lbm_batch* b, int32_t i) {
+    if (!b || i < 0 || i >= (int32_t)b->inst.size()) return nullptr;
+    return b->inst[i];
+}
+
+int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->inst.size() : 0; }
+
+int64_t lbm_batch_kernel_launches(const lbm_batch* b) { return b ? b->launches : 0; }
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+}  // extern "C"

@@ -26,6 +26,21 @@ struct DevParams {
     unsigned* err;               // sticky device error flags
 };
 
+// One instance of a batch: its own grid, buffers and wall parameter; the physics (EOS, rates,
+// sigma, limiter bounds, body force, wall scheme) is shared by the batch.
+struct BatchInstance {
+    int nx, ny, nz, N;
+    void* f[2];                // the instance's two distribution buffers
+    const uint8_t* type;
+    const int* wall_id;
+    const double* kappa_w;     // per wall node or null (scalar kappa)
+    double kappa;
+};
+// One work item of the batched step: a tile of an instance.
+struct BatchItem {
+    int inst, x0, y0, z0;
+};
+
 enum Lat { LAT_D2Q9 = 0, LAT_D3Q19 = 1 };
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1 };
 
@@ -42,8 +57,16 @@ cudaError_t launch_init(int lat, int prec, void* fout, const DevParams& p, const
 cudaError_t launch_get_state(int lat, int prec, const void* fin, const DevParams& p, double* fpost, cudaStream_t s);
 // Stored state from post-streaming doubles [q][N].
 cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, const double* fpost, cudaStream_t s);
-// Node-type flags from the solid mask: T_SOLID, T_WALL (solid with a fluid lattice neighbour) and
-// T_NEARWALL (within Euclidean distance 3 of a solid node).
+// Batched step: a persistent grid of `ctas` CTAs walks the work list (instance, tile) of every
+// instance of the batch; each instance reads f[parity] and writes f[parity ^ 1].
+cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& phys, const BatchInstance* insts,
+                                const BatchItem* items, int n_items, int ctas, cudaStream_t s);
+// Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
+void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);
+int batched_ctas_per_sm(int lat, int prec);
+// Node-type flags from the solid mask: T_SOLID, T_WALL (solid with a fluid lattice neighbour),
+// T_NEARWALL (within Euclidean distance 3 of a solid node) and T_BULK (fluid with every lattice
+// neighbour fluid).
 cudaError_t launch_classify(int lat, const uint8_t* mask, uint8_t* type, int nx, int ny, int nz, cudaStream_t s);
 
 // Observables reduction over rho/u/type: out[0..3] = mass, rho_max, rho_min, max |u|^2;

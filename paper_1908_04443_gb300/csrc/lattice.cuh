@@ -17,7 +17,7 @@
 
 namespace lbmwet {
 
-enum : uint8_t { T_SOLID = 1, T_WALL = 2, T_NEARWALL = 4 };
+enum : uint8_t { T_SOLID = 1, T_WALL = 2, T_NEARWALL = 4, T_BULK = 8 };  // BULK: fluid, all neighbours fluid
 enum : unsigned { ERR_PSI = 1u, ERR_RHO = 2u, ERR_NONFINITE = 4u };
 
 struct D2Q9 {

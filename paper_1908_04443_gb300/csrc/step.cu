@@ -1,17 +1,20 @@
 // Fused time-step kernels of the pseudopotential MRT-LB method with improved virtual-density walls.
 //
-// One CTA owns a TX x TY (x TZ) tile of nodes.  The state in global memory is the post-collision
-// f* of the previous step (structure of arrays, [a][node]); a step is
+// One CTA owns a TX x TY (x TZ) tile of nodes, one thread per node.  The state in global memory is
+// the post-collision f* of the previous step (structure of arrays, [a][node]); a step is
 //   0. node-type flags of the tile + 3-node halo into shared memory;
-//   1. pull-streaming (Eq. 3) with halfway bounce-back (Fig. 3) of every node of the tile + 2-node
-//      halo, and its density (Eq. 4) into shared memory (the tile's own pulled f stay in registers);
-//   2. psi (Eq. 6) on the tile + 1-node halo: from rho at fluid nodes, and at wall nodes from the
-//      virtual density of Eqs. 16-17 (improved scheme with limiter, Sec. III.B) or the constant one
-//      (Sec. II.B), itself averaged from the shared-memory densities of its fluid neighbours;
+//   1. pull-streaming (Eq. 3) with halfway bounce-back (Fig. 3) and the density (Eq. 4) of every
+//      node of the tile + 1-node halo (the tile's own pulled f stay in registers), and psi (Eq. 6)
+//      of its fluid nodes; wall nodes are queued; tiles that contain a wall node also pull their
+//      2-node halo ring, whose densities Eq. 17 needs;
+//   2. at the queued wall nodes: the virtual density of Eqs. 16-17 (improved scheme with limiter,
+//      Sec. III.B) or the constant one (Sec. II.B), averaged from the shared-memory densities of
+//      their fluid neighbours, and its psi;
 //   3. at the tile's fluid nodes: F_m (Eq. 5) from shared psi, F = F_m + body force, u (Eq. 4), the
 //      MRT collision with the consistency source (Eqs. 2, 7), and a coalesced store of f*.
-// Steps 1-2 need neighbour values of the same time level, hence the halo recomputation: nothing
-// but f* is written to global memory per step.
+// Neighbour values of the same time level come from the halo recomputation: nothing but f* is
+// written to global memory per step.  The same tile body serves a single grid (tiles from the
+// CUDA grid) and a batch of grids (a persistent grid walking a work list of (instance, tile)).
 #include <cmath>
 
 #include "kernels.h"
@@ -19,27 +22,69 @@
 
 namespace lbmwet {
 
+// physics constants in compute precision
 template <class C>
-struct EosC {
-    int kind;
-    C RT, a, b, b4, aphi, two_over_G;
+struct Phys {
+    int eos_kind, wall_kind;
+    C RT, a, b, b4, aphi, two_over_G, G;
+    C rho_l, rho_g, rho_ref, fx, fy, fz, rho_w_const;
+    Rates<C> r;
 };
 
 template <class C>
-__device__ __forceinline__ C psi_arg(C rho, const EosC<C>& e) {
+Phys<C> make_phys(const DevParams& p) {
+    Phys<C> h;
+    h.eos_kind = p.eos_kind;
+    h.wall_kind = p.wall_kind;
+    h.RT = C(p.RT);
+    h.a = C(p.a);
+    h.b = C(p.b);
+    h.b4 = C(0.25 * p.b);
+    h.aphi = C(p.aphi);
+    h.two_over_G = C(p.two_over_G);
+    h.G = C(p.G);
+    h.rho_l = C(p.rho_l);
+    h.rho_g = C(p.rho_g);
+    h.rho_ref = C(p.rho_ref);
+    h.fx = C(p.fx);
+    h.fy = C(p.fy);
+    h.fz = C(p.fz);
+    h.rho_w_const = C(p.rho_w_const);
+    h.r.s_e = C(p.s_e);
+    h.r.s_eps = C(p.s_eps);
+    h.r.s_q = C(p.s_q);
+    h.r.s_nu = C(p.s_nu);
+    h.r.s_pi = C(p.s_pi);
+    h.r.s_m = C(p.s_m);
+    h.r.c_e = C(p.c_e);
+    h.r.c_eps = C(p.c_eps);
+    return h;
+}
+
+// geometry of one grid
+struct Geo {
+    int nx, ny, nz, N;
+    const uint8_t* type;
+    const int* wall_id;
+    const double* kappa_w;   // per wall node or null
+    double kappa;
+};
+
+template <class C>
+__device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
     C p;
-    if (e.kind == 1) {  // Carnahan-Starling
+    if (e.eos_kind == 1) {  // Carnahan-Starling
         const C eta = e.b4 * rho;
         const C om = C(1) - eta;
         p = rho * e.RT * (C(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) - e.a * rho * rho;
-    } else {            // Peng-Robinson, Eq. 18
+    } else {                // Peng-Robinson, Eq. 18
         p = rho * e.RT / (C(1) - e.b * rho) - e.aphi * rho * rho / (C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho);
     }
     return e.two_over_G * (p - rho * C(1.0 / 3.0));   // Eq. 6 argument: 2 (p - rho c_s^2) / (G c^2)
 }
 
 template <class C>
-__device__ __forceinline__ C psi_checked(C rho, const EosC<C>& e, unsigned* err) {
+__device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err) {
     const C arg = psi_arg(rho, e);
     if (!(arg > C(0))) {
         atomicOr(err, ERR_PSI);
@@ -54,235 +99,302 @@ __device__ __forceinline__ int wrap_full(int v, int n) {
 }
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-template <class L, class S, class C, int TX, int TY, int TZ, int BY, int MODE>
-__global__ void __launch_bounds__(TX* BY) fused_step(const S* __restrict__ fin, S* __restrict__ fout, DevParams p,
-                                                     double* __restrict__ rho_out, double* __restrict__ u_out) {
+template <class L, class C, int TX, int TY, int TZ>
+struct TileSmem {
+    static constexpr int D = L::D;
+    static constexpr int HZ = (D == 3) ? 2 : 0, PZH = (D == 3) ? 1 : 0, YZH = (D == 3) ? 3 : 0;
+    static constexpr int RX = TX + 4, RY = TY + 4, RZ = TZ + 2 * HZ;    // density tile (2-node halo)
+    static constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2 * PZH;   // psi tile (1-node halo)
+    static constexpr int YX = TX + 6, YY = TY + 6, YZ = TZ + 2 * YZH;   // type tile (3-node halo)
+    uint8_t type[YZ * YY * YX];
+    C rho[RZ * RY * RX];
+    C psi[PZ * PY * PX];
+    short wall[PZ * PY * PX];    // queued wall cells (psi-tile indices)
+    int nwall;
+};
+
+// One tile: x0, y0, z0 is its first node.  All threads of the CTA call this together.
+template <class L, class S, class C, int TX, int TY, int TZ, int MODE>
+__device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
+                                          const Phys<C>& ph, int x0, int y0, int z0, unsigned* err,
+                                          double* __restrict__ rho_out, double* __restrict__ u_out,
+                                          TileSmem<L, C, TX, TY, TZ>& sm) {
+    using T = TileSmem<L, C, TX, TY, TZ>;
     constexpr int D = L::D, Q = L::Q;
-    constexpr int HZ = (D == 3) ? 2 : 0;        // rho halo along z
-    constexpr int PZH = (D == 3) ? 1 : 0;       // psi halo along z
-    constexpr int YZH = (D == 3) ? 3 : 0;       // type halo along z
-    constexpr int RX = TX + 4, RY = TY + 4, RZ = TZ + 2 * HZ;
-    constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2 * PZH;
-    constexpr int YX = TX + 6, YY = TY + 6, YZ = TZ + 2 * YZH;
-    constexpr int NT = TX * BY;
-    constexpr int RPT = (TY * TZ) / BY;
-    static_assert((TY * TZ) % BY == 0, "rows per thread");
+    constexpr int NT = TX * TY * TZ;
+    constexpr int RX = T::RX, RY = T::RY, RZ = T::RZ, PX = T::PX, PY = T::PY, PZ = T::PZ;
+    constexpr int YX = T::YX, YY = T::YY, YZ = T::YZ, HZ = T::HZ, PZH = T::PZH, YZH = T::YZH;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
+    const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    // grids narrower than a tile plus its halo wrap more than once: use the full modulo there
+    const bool small = nx < TX + 8 || ny < TY + 8 || (D == 3 && nz < TZ + 8);
+    auto wx = [&](int v) { return small ? wrap_full(v, nx) : wrap1(v, nx); };
+    auto wy = [&](int v) { return small ? wrap_full(v, ny) : wrap1(v, ny); };
+    auto wz = [&](int v) { return (D == 3) ? (small ? wrap_full(v, nz) : wrap1(v, nz)) : 0; };
+    auto tix = [](int lx, int ly, int lz) { return (lz * YY + ly) * YX + lx; };
+    auto rix = [](int lx, int ly, int lz) { return (lz * RY + ly) * RX + lx; };
+    auto pix = [](int lx, int ly, int lz) { return (lz * PY + ly) * PX + lx; };
 
-    __shared__ uint8_t s_type[YZ * YY * YX];
-    __shared__ C s_rho[RZ * RY * RX];
-    __shared__ C s_psi[PZ * PY * PX];
-
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long N = p.N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-
-    EosC<C> eos;
-    eos.kind = p.eos_kind;
-    eos.RT = C(p.RT);
-    eos.a = C(p.a);
-    eos.b = C(p.b);
-    eos.b4 = C(p.b * 0.25);
-    eos.aphi = C(p.aphi);
-    eos.two_over_G = C(p.two_over_G);
-    const C rho_ref = C(p.rho_ref);
-
-    auto tidx = [&](int lx, int ly, int lz) { return (lz * YY + ly) * YX + lx; };
-    auto ridx = [&](int lx, int ly, int lz) { return (lz * RY + ly) * RX + lx; };
-    auto pidx = [&](int lx, int ly, int lz) { return (lz * PY + ly) * PX + lx; };
-
-    // 0. node types of the tile + 3-node halo
+    // 0. node types of the tile + 3-node halo; does the 1-node halo region hold a wall node?
+    if (tid == 0) sm.nwall = 0;
+    int wall_seen = 0;
     for (int i = tid; i < YX * YY * YZ; i += NT) {
         const int lx = i % YX, t = i / YX, ly = t % YY, lz = t / YY;
-        const int gx = wrap_full(x0 + lx - 3, nx), gy = wrap_full(y0 + ly - 3, ny);
-        const int gz = (D == 3) ? wrap_full(z0 + lz - YZH, nz) : 0;
-        s_type[i] = p.type[((long long)gz * ny + gy) * nx + gx];
+        const int gx = wx(x0 + lx - 3), gy = wy(y0 + ly - 3), gz = wz(z0 + lz - YZH);
+        const uint8_t ty = g.type[(gz * ny + gy) * nx + gx];
+        sm.type[i] = ty;
+        const bool in_p = lx >= 2 && lx < TX + 4 && ly >= 2 && ly < TY + 4 &&
+                          (D == 2 || (lz >= YZH - PZH && lz < TZ + YZH + PZH));
+        if (in_p && (ty & T_WALL)) wall_seen = 1;
     }
-    __syncthreads();
+    const bool tile_has_wall = __syncthreads_or(wall_seen);
 
-    // pull of one node: f_a(x) = f*_a(x - e_a) if x - e_a is fluid, else f*_abar(x)
-    auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int tx, int ty, int tz) {
-        const long long g = ((long long)gz * ny + gy) * nx + gx;
+    // pull of one node at global (gx, gy, gz) whose type-tile cell is ti
+    auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int ti, uint8_t self) {
+        const int xm = wrap1(gx - 1, nx), xp = wrap1(gx + 1, nx);
+        const int ym = wrap1(gy - 1, ny), yp = wrap1(gy + 1, ny);
+        const int cx[3] = {xm, gx, xp};
+        const int ry[3] = {ym * nx, gy * nx, yp * nx};
+        int pz[3];
+        if (D == 3) {
+            const int nxy = nx * ny;
+            pz[0] = wrap1(gz - 1, nz) * nxy;
+            pz[1] = gz * nxy;
+            pz[2] = wrap1(gz + 1, nz) * nxy;
+        } else {
+            pz[0] = pz[1] = pz[2] = 0;
+        }
+        const int gi = pz[1] + ry[1] + cx[1];
+        if (self & T_BULK) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            if (s_type[tidx(tx - ex, ty - ey, tz - ez)] & T_SOLID) {
-                f[a] = C(fin[(long long)L::opp(a) * N + g]);
-            } else {
-                const int sx = ex ? wrap1(gx - ex, nx) : gx;
-                const int sy = ey ? wrap1(gy - ey, ny) : gy;
-                const int sz = ez ? wrap1(gz - ez, nz) : gz;
-                f[a] = C(fin[(long long)a * N + ((long long)sz * ny + sy) * nx + sx]);
+            for (int a = 0; a < Q; ++a) {
+                const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                f[a] = C(fin[a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                const int up = ti - ex - ey * YX - ez * YX * YY;
+                if (sm.type[up] & T_SOLID) f[a] = C(fin[L::opp(a) * N + gi]);
+                else f[a] = C(fin[a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
             }
         }
     };
 
-    // 1a. the tile's own nodes: pull into registers, density into shared memory
-    C f[RPT][Q];
-    int gxs[RPT], gys[RPT], gzs[RPT];
-    bool fluid[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int j = threadIdx.y + r * BY;
-        const int lx = threadIdx.x, ly = j % TY, lz = j / TY;
-        const int gx = wrap_full(x0 + lx, nx), gy = wrap_full(y0 + ly, ny);
-        const int gz = (D == 3) ? wrap_full(z0 + lz, nz) : 0;
-        gxs[r] = gx;
-        gys[r] = gy;
-        gzs[r] = gz;
-        const int tx = lx + 3, ty = ly + 3, tz = lz + YZH;
-        fluid[r] = !(s_type[tidx(tx, ty, tz)] & T_SOLID);
-        C drho = C(0);
-        if (fluid[r]) {
-            pull(f[r], gx, gy, gz, tx, ty, tz);
-#pragma unroll
-            for (int a = 0; a < Q; ++a) drho += f[r][a];
-        } else {
-#pragma unroll
-            for (int a = 0; a < Q; ++a) f[r][a] = C(0);
-        }
-        s_rho[ridx(lx + 2, ly + 2, lz + HZ)] = fluid[r] ? rho_ref + drho : C(0);
-    }
-    // 1b. the 2-node halo ring: density only
-    for (int i = tid; i < RX * RY * RZ; i += NT) {
-        const int lx = i % RX, t = i / RX, ly = t % RY, lz = t / RY;
-        if (lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && lz >= HZ && lz < TZ + HZ) continue;
-        const int gx = wrap_full(x0 + lx - 2, nx), gy = wrap_full(y0 + ly - 2, ny);
-        const int gz = (D == 3) ? wrap_full(z0 + lz - HZ, nz) : 0;
-        const int tx = lx + 1, ty = ly + 1, tz = lz + (YZH - HZ);
+    // 1a. the tile's own node
+    const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
+    const int gx = wx(x0 + lx), gy = wy(y0 + ly), gz = wz(z0 + lz);
+    const int gi = (gz * ny + gy) * nx + gx;
+    const int my_ti = tix(lx + 3, ly + 3, lz + YZH);
+    const uint8_t my_type = sm.type[my_ti];
+    const bool my_fluid = !(my_type & T_SOLID);
+    C f[Q];
+    {
         C rho = C(0);
-        if (!(s_type[tidx(tx, ty, tz)] & T_SOLID)) {
-            C g[Q];
-            pull(g, gx, gy, gz, tx, ty, tz);
+        if (my_fluid) {
+            pull(f, gx, gy, gz, my_ti, my_type);
             C drho = C(0);
 #pragma unroll
-            for (int a = 0; a < Q; ++a) drho += g[a];
-            rho = rho_ref + drho;
+            for (int a = 0; a < Q; ++a) drho += f[a];
+            rho = ph.rho_ref + drho;
+            sm.psi[pix(lx + 1, ly + 1, lz + PZH)] = psi_checked(rho, ph, err);
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) f[a] = C(0);
+            const int pi = pix(lx + 1, ly + 1, lz + PZH);
+            sm.psi[pi] = C(0);
+            if (my_type & T_WALL) sm.wall[atomicAdd(&sm.nwall, 1)] = short(pi);
         }
-        s_rho[i] = rho;
+        sm.rho[rix(lx + 2, ly + 2, lz + HZ)] = rho;
+    }
+    // 1b. the 1-node halo ring: density and psi (fluid) or queue (wall)
+    for (int i = tid; i < PX * PY * PZ; i += NT) {
+        const int px = i % PX, t = i / PX, py = t % PY, pz = t / PY;
+        if (px >= 1 && px <= TX && py >= 1 && py <= TY && (D == 2 || (pz >= 1 && pz <= TZ))) continue;
+        const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
+        const int ti = tix(px + 2, py + 2, pz + (YZH - PZH));
+        const uint8_t ty = sm.type[ti];
+        C rho = C(0), psi = C(0);
+        if (!(ty & T_SOLID)) {
+            C h[Q];
+            pull(h, cgx, cgy, cgz, ti, ty);
+            C drho = C(0);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) drho += h[a];
+            rho = ph.rho_ref + drho;
+            psi = psi_checked(rho, ph, err);
+        } else if (ty & T_WALL) {
+            sm.wall[atomicAdd(&sm.nwall, 1)] = short(i);
+        }
+        sm.rho[rix(px + 1, py + 1, pz + (HZ - PZH))] = rho;
+        sm.psi[i] = psi;
+    }
+    // 1c. the 2-node halo ring, only where Eq. 17 will need it
+    if (tile_has_wall) {
+        for (int i = tid; i < RX * RY * RZ; i += NT) {
+            const int rx = i % RX, t = i / RX, ry = t % RY, rz = t / RY;
+            if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && (D == 2 || (rz >= 1 && rz <= TZ + 2))) continue;
+            const int cgx = wx(x0 + rx - 2), cgy = wy(y0 + ry - 2), cgz = wz(z0 + rz - HZ);
+            const int ti = tix(rx + 1, ry + 1, rz + (YZH - HZ));
+            const uint8_t ty = sm.type[ti];
+            C rho = C(0);
+            if (!(ty & T_SOLID)) {
+                C h[Q];
+                pull(h, cgx, cgy, cgz, ti, ty);
+                C drho = C(0);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) drho += h[a];
+                rho = ph.rho_ref + drho;
+            }
+            sm.rho[i] = rho;
+        }
     }
     __syncthreads();
 
-    // 2. psi on the tile + 1-node halo
-    const C rho_g = C(p.rho_g), rho_l = C(p.rho_l);
-    for (int i = tid; i < PX * PY * PZ; i += NT) {
-        const int lx = i % PX, t = i / PX, ly = t % PY, lz = t / PY;
-        const int rx = lx + 1, ry = ly + 1, rz = lz + (HZ - PZH);
-        const int tx = lx + 2, ty = ly + 2, tz = lz + (YZH - PZH);
-        const uint8_t ty_ = s_type[tidx(tx, ty, tz)];
-        C psi = C(0);
-        if (!(ty_ & T_SOLID)) {
-            psi = psi_checked(s_rho[ridx(rx, ry, rz)], eos, p.err);
-        } else if (ty_ & T_WALL) {
+    // 2. wall nodes of the tile + 1-node halo: virtual density and its psi
+    const int nwall = sm.nwall;
+    if (nwall > 0) {
+        for (int k = tid; k < nwall; k += NT) {
+            const int i = sm.wall[k];
+            const int px = i % PX, t = i / PX, py = t % PY, pz = t / PY;
+            const int rx = px + 1, ry = py + 1, rz = pz + (HZ - PZH);
+            const int ti = tix(px + 2, py + 2, pz + (YZH - PZH));
             C rw;
-            if (p.wall_kind == 1) {
-                rw = C(p.rho_w_const);
+            if (ph.wall_kind == 1) {
+                rw = ph.rho_w_const;
             } else {
                 // Eq. 17: weighted mean of the fluid neighbours' densities
                 C num = C(0), den = C(0);
 #pragma unroll
                 for (int a = 1; a < Q; ++a) {
                     const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-                    if (!(s_type[tidx(tx + ex, ty + ey, tz + ez)] & T_SOLID)) {
-                        num += C(L::wf(a)) * s_rho[ridx(rx + ex, ry + ey, rz + ez)];
+                    if (!(sm.type[ti + ex + ey * YX + ez * YX * YY] & T_SOLID)) {
+                        num += C(L::wf(a)) * sm.rho[rix(rx + ex, ry + ey, rz + ez)];
                         den += C(L::wf(a));
                     }
                 }
                 const C rho_ave = num / den;
                 C kap;
-                if (p.kappa_w) {
-                    const int gx = wrap_full(x0 + lx - 1, nx), gy = wrap_full(y0 + ly - 1, ny);
-                    const int gz = (D == 3) ? wrap_full(z0 + lz - PZH, nz) : 0;
-                    kap = C(p.kappa_w[p.wall_id[((long long)gz * ny + gy) * nx + gx]]);
+                if (g.kappa_w) {
+                    const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
+                    kap = C(g.kappa_w[g.wall_id[(cgz * ny + cgy) * nx + cgx]]);
                 } else {
-                    kap = C(p.kappa);
+                    kap = C(g.kappa);
                 }
                 // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
                 rw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
-                rw = rw > rho_l ? rho_l : rw;
-                rw = rw < rho_g ? rho_g : rw;
+                rw = rw > ph.rho_l ? ph.rho_l : rw;
+                rw = rw < ph.rho_g ? ph.rho_g : rw;
             }
-            psi = psi_checked(rw, eos, p.err);
+            sm.psi[i] = psi_checked(rw, ph, err);
         }
-        s_psi[i] = psi;
+        __syncthreads();
     }
-    __syncthreads();
 
-    // 3. force, velocity and collision of the tile's fluid nodes
-    Rates<C> rates;
-    rates.s_e = C(p.s_e);
-    rates.s_eps = C(p.s_eps);
-    rates.s_q = C(p.s_q);
-    rates.s_nu = C(p.s_nu);
-    rates.s_pi = C(p.s_pi);
-    rates.s_m = C(p.s_m);
-    rates.c_e = C(p.c_e);
-    rates.c_eps = C(p.c_eps);
-    const C G = C(p.G);
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int j = threadIdx.y + r * BY;
-        const int lx = threadIdx.x, ly = j % TY, lz = j / TY;
-        const bool valid = (x0 + lx < nx) && (y0 + ly < ny) && (D == 2 || z0 + lz < nz);
-        if (!valid) continue;
-        const long long g = ((long long)gzs[r] * ny + gys[r]) * nx + gxs[r];
-        if (!fluid[r]) {
-            if (MODE == 1) {
-                if (rho_out) rho_out[g] = 0.0;
-                if (u_out) {
-                    for (int c = 0; c < D; ++c) u_out[(long long)c * N + g] = 0.0;
-                }
-            }
-            continue;
-        }
-        const int px = lx + 1, py = ly + 1, pz = lz + PZH;
-        const C psi_c = s_psi[pidx(px, py, pz)];
-        // sum_a w_a psi(x + e_a) e_a, taken over opposite pairs: w_a e_a (psi(x + e_a) - psi(x - e_a))
-        // (nearly equal values cancel exactly in the difference, which keeps FP32 accurate in bulk)
-        C sx = C(0), sy = C(0), sz = C(0);
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            if (L::opp(a) < a) continue;
-            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            const C dpsi = s_psi[pidx(px + ex, py + ey, pz + ez)] - s_psi[pidx(px - ex, py - ey, pz - ez)];
-            const C wd = C(L::wf(a)) * dpsi;
-            if (ex) sx += C(ex) * wd;
-            if (ey) sy += C(ey) * wd;
-            if (D == 3 && ez) sz += C(ez) * wd;
-        }
-        // Eq. 5
-        const C Fmx = -G * psi_c * sx, Fmy = -G * psi_c * sy, Fmz = -G * psi_c * sz;
-        const C Fx = Fmx + C(p.fx), Fy = Fmy + C(p.fy), Fz = Fmz + C(p.fz);
-        C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            drho += f[r][a];
-            if (L::ex(a)) jx += C(L::ex(a)) * f[r][a];
-            if (L::ey(a)) jy += C(L::ey(a)) * f[r][a];
-            if (D == 3 && L::ez(a)) jz += C(L::ez(a)) * f[r][a];
-        }
-        const C rho = rho_ref + drho;
-        if (!(rho > C(0))) atomicOr(p.err, ERR_RHO);
-        // Eq. 4: rho u = sum e f + F/2
-        const C inv = C(1) / rho;
-        const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv, uz = (jz + C(0.5) * Fz) * inv;
+    // 3. force, velocity and collision of the tile's fluid node
+    const bool valid = (x0 + lx < nx) && (y0 + ly < ny) && (D == 2 || z0 + lz < nz);
+    if (!valid) return;
+    if (!my_fluid) {
         if (MODE == 1) {
-            if (rho_out) rho_out[g] = double(rho);
-            if (u_out) {
-                u_out[g] = double(ux);
-                u_out[N + g] = double(uy);
-                if (D == 3) u_out[2 * N + g] = double(uz);
-            }
-            continue;
+            if (rho_out) rho_out[gi] = 0.0;
+            if (u_out)
+                for (int c = 0; c < D; ++c) u_out[c * N + gi] = 0.0;
         }
-        const C X = (Fmx * Fmx + Fmy * Fmy + Fmz * Fmz) / (psi_c * psi_c);
-        if constexpr (D == 2) {
-            collide_d2q9<C>(f[r], drho, rho, ux, uy, Fx, Fy, X, rates);
-        } else {
-            collide_d3q19<C>(f[r], drho, rho, ux, uy, uz, Fx, Fy, Fz, X, rates);
-        }
+        return;
+    }
+    const int pc = pix(lx + 1, ly + 1, lz + PZH);
+    const C psi_c = sm.psi[pc];
+    // sum_a w_a psi(x + e_a) e_a, taken over opposite pairs: w_a e_a (psi(x + e_a) - psi(x - e_a))
+    // (nearly equal values cancel exactly in the difference, which keeps FP32 accurate in bulk)
+    C sx = C(0), sy = C(0), sz = C(0);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) fout[(long long)a * N + g] = S(f[r][a]);
+    for (int a = 1; a < Q; ++a) {
+        if (L::opp(a) < a) continue;
+        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+        const int off = ex + ey * PX + ez * PX * PY;
+        const C wd = C(L::wf(a)) * (sm.psi[pc + off] - sm.psi[pc - off]);
+        if (ex) sx += C(ex) * wd;
+        if (ey) sy += C(ey) * wd;
+        if (D == 3 && ez) sz += C(ez) * wd;
+    }
+    // Eq. 5
+    const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy, Fmz = -ph.G * psi_c * sz;
+    const C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
+    C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        drho += f[a];
+        if (L::ex(a)) jx += C(L::ex(a)) * f[a];
+        if (L::ey(a)) jy += C(L::ey(a)) * f[a];
+        if (D == 3 && L::ez(a)) jz += C(L::ez(a)) * f[a];
+    }
+    const C rho = ph.rho_ref + drho;
+    if (!(rho > C(0))) atomicOr(err, ERR_RHO);
+    // Eq. 4: rho u = sum e f + F/2
+    const C inv = C(1) / rho;
+    const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv, uz = (jz + C(0.5) * Fz) * inv;
+    if (MODE == 1) {
+        if (rho_out) rho_out[gi] = double(rho);
+        if (u_out) {
+            u_out[gi] = double(ux);
+            u_out[N + gi] = double(uy);
+            if (D == 3) u_out[2 * N + gi] = double(uz);
+        }
+        return;
+    }
+    const C X = (Fmx * Fmx + Fmy * Fmy + Fmz * Fmz) / (psi_c * psi_c);
+    if constexpr (D == 2) {
+        collide_d2q9<C>(f, drho, rho, ux, uy, Fx, Fy, X, ph.r);
+    } else {
+        collide_d3q19<C>(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, ph.r);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fout[a * N + gi] = S(f[a]);
+}
+
+// Tile shapes per lattice and precision (one thread per node).
+template <class L, class S>
+struct TileShape;
+template <> struct TileShape<D2Q9, float> { static constexpr int X = 32, Y = 16, Z = 1, MINB = 2; };
+template <> struct TileShape<D2Q9, double> { static constexpr int X = 32, Y = 8, Z = 1, MINB = 2; };
+template <> struct TileShape<D3Q19, float> { static constexpr int X = 32, Y = 4, Z = 4, MINB = 1; };
+template <> struct TileShape<D3Q19, double> { static constexpr int X = 32, Y = 4, Z = 2, MINB = 1; };
+
+template <class L, class S, class C, int MODE>
+__global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileShape<L, S>::Z, TileShape<L, S>::MINB)
+    fused_step(const S* __restrict__ fin, S* __restrict__ fout, Geo g, Phys<C> ph, unsigned* err,
+               double* __restrict__ rho_out, double* __restrict__ u_out) {
+    using TS = TileShape<L, S>;
+    __shared__ TileSmem<L, C, TS::X, TS::Y, TS::Z> sm;
+    tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                  blockIdx.z * TS::Z, err, rho_out, u_out, sm);
+}
+
+// Batched step: CTAs walk the work list; each item is one tile of one instance.
+template <class L, class S, class C>
+__global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileShape<L, S>::Z, TileShape<L, S>::MINB)
+    fused_step_batched(int parity, const BatchInstance* __restrict__ insts, const BatchItem* __restrict__ items,
+                       int n_items, Phys<C> ph, unsigned* err) {
+    using TS = TileShape<L, S>;
+    __shared__ TileSmem<L, C, TS::X, TS::Y, TS::Z> sm;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const BatchInstance& in = insts[item.inst];
+        Geo g;
+        g.nx = in.nx;
+        g.ny = in.ny;
+        g.nz = in.nz;
+        g.N = in.N;
+        g.type = in.type;
+        g.wall_id = in.wall_id;
+        g.kappa_w = in.kappa_w;
+        g.kappa = in.kappa;
+        const S* fin = static_cast<const S*>(in.f[parity]);
+        S* fout = static_cast<S*>(in.f[parity ^ 1]);
+        __syncthreads();   // the previous item's threads are done with shared memory
+        tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0>(fin, fout, g, ph, item.x0, item.y0, item.z0, err, nullptr, nullptr,
+                                                   sm);
     }
 }
 
@@ -401,6 +513,15 @@ __global__ void classify_kernel(const uint8_t* __restrict__ mask, uint8_t* __res
                     if (mask[((long long)sz * ny + sy) * nx + sx]) near = true;
                 }
         if (near) t |= T_NEARWALL;
+        if (!solid) {
+            bool bulk = true;
+            for (int a = 1; a < L::Q; ++a) {
+                const int sx = wrap1(x + L::ex(a), nx), sy = wrap1(y + L::ey(a), ny);
+                const int sz = (L::D == 3) ? wrap1(z + L::ez(a), nz) : 0;
+                if (mask[((long long)sz * ny + sy) * nx + sx]) bulk = false;
+            }
+            if (bulk) t |= T_BULK;
+        }
         type[g] = t;
     }
 }
@@ -409,25 +530,38 @@ __global__ void classify_kernel(const uint8_t* __restrict__ mask, uint8_t* __res
 // Launchers
 // ---------------------------------------------------------------------------------------------
 
-template <class L, class S, class C, int TX, int TY, int TZ, int BY, int MODE>
+static Geo geo_of(const DevParams& p) {
+    Geo g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.nz = p.nz;
+    g.N = int(p.N);
+    g.type = p.type;
+    g.wall_id = p.wall_id;
+    g.kappa_w = p.kappa_w;
+    g.kappa = p.kappa;
+    return g;
+}
+
+template <class L, class S, int MODE>
 static cudaError_t launch_tile(const void* fin, void* fout, const DevParams& p, double* rho, double* u, cudaStream_t s) {
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + TZ - 1) / TZ);
-    dim3 block(TX, BY, 1);
-    fused_step<L, S, C, TX, TY, TZ, BY, MODE>
-        <<<grid, block, 0, s>>>(static_cast<const S*>(fin), static_cast<S*>(fout), p, rho, u);
+    using TS = TileShape<L, S>;
+    dim3 grid((p.nx + TS::X - 1) / TS::X, (p.ny + TS::Y - 1) / TS::Y, (p.nz + TS::Z - 1) / TS::Z);
+    dim3 block(TS::X, TS::Y, TS::Z);
+    fused_step<L, S, S, MODE><<<grid, block, 0, s>>>(static_cast<const S*>(fin), static_cast<S*>(fout), geo_of(p),
+                                                     make_phys<S>(p), p.err, rho, u);
     return cudaGetLastError();
 }
 
-// Tile shapes: 2D 32x16 tiles with 256 threads (2 nodes per thread); 3D 32x4x4 tiles, 256 threads.
 template <int MODE>
 static cudaError_t dispatch(int lat, int prec, const void* fin, void* fout, const DevParams& p, double* rho, double* u,
                             cudaStream_t s) {
     if (lat == LAT_D2Q9) {
-        if (prec == PREC_FP64) return launch_tile<D2Q9, double, double, 32, 16, 1, 8, MODE>(fin, fout, p, rho, u, s);
-        return launch_tile<D2Q9, float, float, 32, 16, 1, 8, MODE>(fin, fout, p, rho, u, s);
+        if (prec == PREC_FP64) return launch_tile<D2Q9, double, MODE>(fin, fout, p, rho, u, s);
+        return launch_tile<D2Q9, float, MODE>(fin, fout, p, rho, u, s);
     }
-    if (prec == PREC_FP64) return launch_tile<D3Q19, double, double, 32, 4, 4, 16, MODE>(fin, fout, p, rho, u, s);
-    return launch_tile<D3Q19, float, float, 32, 4, 4, 8, MODE>(fin, fout, p, rho, u, s);
+    if (prec == PREC_FP64) return launch_tile<D3Q19, double, MODE>(fin, fout, p, rho, u, s);
+    return launch_tile<D3Q19, float, MODE>(fin, fout, p, rho, u, s);
 }
 
 cudaError_t launch_step(int lat, int prec, const void* fin, void* fout, const DevParams& p, cudaStream_t s) {
@@ -437,6 +571,50 @@ cudaError_t launch_step(int lat, int prec, const void* fin, void* fout, const De
 cudaError_t launch_fields(int lat, int prec, const void* fin, const DevParams& p, double* rho, double* u,
                           cudaStream_t s) {
     return dispatch<1>(lat, prec, fin, nullptr, p, rho, u, s);
+}
+
+template <class L, class S>
+static cudaError_t batched_l(int parity, const DevParams& p, const BatchInstance* insts, const BatchItem* items,
+                             int n_items, int ctas, cudaStream_t s) {
+    using TS = TileShape<L, S>;
+    dim3 block(TS::X, TS::Y, TS::Z);
+    fused_step_batched<L, S, S><<<ctas, block, 0, s>>>(parity, insts, items, n_items, make_phys<S>(p), p.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& p, const BatchInstance* insts,
+                                const BatchItem* items, int n_items, int ctas, cudaStream_t s) {
+    if (lat == LAT_D2Q9) {
+        if (prec == PREC_FP64) return batched_l<D2Q9, double>(parity, p, insts, items, n_items, ctas, s);
+        return batched_l<D2Q9, float>(parity, p, insts, items, n_items, ctas, s);
+    }
+    if (prec == PREC_FP64) return batched_l<D3Q19, double>(parity, p, insts, items, n_items, ctas, s);
+    return batched_l<D3Q19, float>(parity, p, insts, items, n_items, ctas, s);
+}
+
+void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz) {
+    if (lat == LAT_D2Q9) {
+        if (prec == PREC_FP64) { *tx = TileShape<D2Q9, double>::X; *ty = TileShape<D2Q9, double>::Y; *tz = 1; }
+        else { *tx = TileShape<D2Q9, float>::X; *ty = TileShape<D2Q9, float>::Y; *tz = 1; }
+    } else {
+        if (prec == PREC_FP64) { *tx = TileShape<D3Q19, double>::X; *ty = TileShape<D3Q19, double>::Y; *tz = TileShape<D3Q19, double>::Z; }
+        else { *tx = TileShape<D3Q19, float>::X; *ty = TileShape<D3Q19, float>::Y; *tz = TileShape<D3Q19, float>::Z; }
+    }
+}
+
+template <class L, class S>
+static int occ() {
+    using TS = TileShape<L, S>;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_batched<L, S, S>, TS::X * TS::Y * TS::Z, 0) !=
+        cudaSuccess)
+        n = 1;
+    return n < 1 ? 1 : n;
+}
+
+int batched_ctas_per_sm(int lat, int prec) {
+    if (lat == LAT_D2Q9) return prec == PREC_FP64 ? occ<D2Q9, double>() : occ<D2Q9, float>();
+    return prec == PREC_FP64 ? occ<D3Q19, double>() : occ<D3Q19, float>();
 }
 
 static unsigned grid_for(long long n) {

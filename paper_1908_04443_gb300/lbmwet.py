@@ -82,6 +82,16 @@ def _load():
         "lbm_destroy": (None, [H]),
         "lbm_last_error": (C.c_char_p, [H]),
         "lbm_status_string": (C.c_char_p, [C.c_int]),
+        "lbm_batch_init": (C.c_int, [C.c_int32, C.POINTER(lbm_config), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
+        "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+        "lbm_batch_enqueue_steps": (C.c_int, [C.c_void_p, C.c_int64]),
+        "lbm_batch_observables": (C.c_int, [C.c_void_p, C.POINTER(lbm_obs)]),
+        "lbm_batch_handle": (C.c_void_p, [C.c_void_p, C.c_int32]),
+        "lbm_batch_size": (C.c_int32, [C.c_void_p]),
+        "lbm_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
+        "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
+        "lbm_batch_destroy": (None, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -94,7 +104,9 @@ _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
-            "lbm_destroy", "lbm_last_error", "lbm_status_string")
+            "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_batch_init", "lbm_batch_step",
+            "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_handle", "lbm_batch_size",
+            "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
 def library():
@@ -235,6 +247,72 @@ def lbm_kernel_launches(h) -> int:
 
 def lbm_destroy(h):
     _lib.lbm_destroy(h)
+
+
+def _bcheck(status: int, b=None):
+    if status != LBM_OK:
+        msg = _lib.lbm_batch_last_error(b)
+        raise LbmError(status, (msg or b"").decode() or _lib.lbm_status_string(status).decode())
+
+
+def lbm_batch_init(cfgs, masks, rho0s=None, kappas_per_wall=None, stream=None):
+    n = len(cfgs)
+    arr = (lbm_config * n)(*cfgs)
+    keep = []
+
+    def ptrs(items, dtype):
+        if items is None:
+            return None
+        out = (C.c_void_p * n)()
+        for i, a in enumerate(items):
+            if a is None:
+                out[i] = None
+            else:
+                x = np.ascontiguousarray(np.asarray(a).reshape(-1), dtype=dtype)
+                keep.append(x)
+                out[i] = x.ctypes.data
+        return out
+
+    pm = ptrs([np.asarray(m).reshape(-1) != 0 for m in masks], np.uint8)
+    pr = ptrs(rho0s, np.float64)
+    pk = ptrs(kappas_per_wall, np.float64)
+    b = C.c_void_p()
+    _bcheck(_lib.lbm_batch_init(n, arr, pm, pr, pk, _stream_ptr(stream), C.byref(b)), None)
+    return b
+
+
+def lbm_batch_step(b, n: int):
+    _bcheck(_lib.lbm_batch_step(b, int(n)), b)
+
+
+def lbm_batch_enqueue_steps(b, n: int):
+    _bcheck(_lib.lbm_batch_enqueue_steps(b, int(n)), b)
+
+
+def lbm_batch_observables(b):
+    n = _lib.lbm_batch_size(b)
+    out = (lbm_obs * n)()
+    _bcheck(_lib.lbm_batch_observables(b, out), b)
+    return list(out)
+
+
+def lbm_batch_handle(b, i: int):
+    h = _lib.lbm_batch_handle(b, int(i))
+    if not h:
+        raise IndexError(i)
+    return C.c_void_p(h)
+
+
+def lbm_batch_size(b) -> int:
+    return int(_lib.lbm_batch_size(b))
+
+
+def lbm_batch_kernel_launches(b) -> int:
+    return int(_lib.lbm_batch_kernel_launches(b))
+
+
+def lbm_batch_destroy(b):
+    _lib.lbm_batch_destroy(b)
 
 
 # ---- configuration helpers ----------------------------------------------------------------------

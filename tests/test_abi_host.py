@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "lbmwet.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:lbm_status|void|int64_t|const char\*)\s+(lbm_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|void|int64_t|int32_t|lbm_handle\*|const char\*)\s+(lbm_\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported():
@@ -92,3 +92,13 @@ def test_init_rejects_bad_grid():
     with pytest.raises(L.LbmError) as ei:
         L.lbm_init(cfg, np.zeros((8, 8), np.uint8))
     assert ei.value.status == L.LBM_ERR_ARG
+
+
+def test_batch_rejects_mixed_physics_before_device_work():
+    a = _cfg()
+    b = _cfg(sigma=0.2)
+    m = np.zeros((8, 8), np.uint8)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_batch_init([a, b], [m, m])
+    assert ei.value.status == L.LBM_ERR_ARG
+    assert "differs" in str(ei.value)
