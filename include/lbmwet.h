@@ -204,6 +204,28 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
+/* ---- Adjoint (D2Q9, IVD walls) -------------------------------------------------------------
+ * Gradient of a loss of the final density, L(rho_T), with respect to the per-wall-node IVD
+ * parameter kappa_j (Eq. 16 in the unified form of lbm_config.kappa), by the discrete adjoint of
+ * the time step (Eqs. 1-7, 16-17, halfway bounce-back): reverse of the collision, of the force
+ * of Eq. 5 through psi (Eq. 6), of the virtual wall density with its limiter (zero derivative
+ * where the limiter clamps), and of the streaming.  The paper has no adjoint; this serves the
+ * inverse problem of fitting wall wettability to an observed density field. */
+
+/* Advance n_steps >= 1 steps from the current state, keeping a device checkpoint of the stored
+ * state every ckpt_every steps (ceil(n_steps/ckpt_every) copies of the distributions).  Switches
+ * the handle to per-wall-node kappa if it was using the scalar one.  Errors: LBM_ERR_ARG (D3Q19,
+ * VD walls, bad counts), LBM_ERR_OOM, LBM_ERR_UNSTABLE. */
+lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_every);
+
+/* dL/dkappa for the trajectory of the last lbm_record, whose final state must still be the
+ * handle's state (else LBM_ERR_STATE).  drho_final_dev: DEVICE array of N doubles, dL/drho_T at
+ * every node (ignored at solid nodes).  dkappa_host: host array, one double per wall node in
+ * lbm_wall_nodes() order.  Recomputes each checkpoint segment's states, then runs the reverse
+ * sweep; allocates (ckpt_every - 1) + 2 distribution buffers and 19 N scalars of scratch for the
+ * call.  Synchronises the stream. */
+lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, double* dkappa_host);
+
 /* ---- Batches (no counterpart in the paper: many independent grids of one physics) ----------
  * A batch steps n grids with one persistent kernel launch per time step: a grid of CTAs sized to
  * the GPU walks a work list of (instance, tile) items covering every instance; the launches of

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/lbmwet.h"
+#include "adjoint.h"
 #include "eos_host.h"
 #include "kernels.h"
 #include "lattice.cuh"
@@ -30,6 +31,10 @@ struct lbm_handle {
     int cur = 0;
     size_t fbytes = 0;   // bytes of one distribution buffer
     uint8_t* d_type = nullptr;
+    uint8_t* d_tile_solid = nullptr;
+    std::vector<uint8_t> tile_solid;   // per step-kernel tile: a solid node within the tile + 3-node halo
+    int tiles[3] = {1, 1, 1};
+    int int_tile[3] = {1, 1, 1};
     int* d_wall_id = nullptr;
     double* d_kappa = nullptr;
     unsigned* d_err = nullptr;
@@ -46,6 +51,10 @@ struct lbm_handle {
     DevParams dp{};
     std::string err;
     bool batch_member = false;   // owned and stepped by an lbm_batch
+    // recorded trajectory for the adjoint: checkpoints of the stored state every rec_every steps
+    std::vector<void*> ckpt;
+    int64_t rec_steps = 0, rec_every = 0, rec_end_step = -1;
+    int rec_end_cur = 0;
 };
 
 namespace {
@@ -78,6 +87,7 @@ void free_all(lbm_handle* h) {
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_type);
+    cudaFree(h->d_tile_solid);
     cudaFree(h->d_wall_id);
     cudaFree(h->d_kappa);
     cudaFree(h->d_err);
@@ -85,6 +95,8 @@ void free_all(lbm_handle* h) {
     cudaFree(h->d_u);
     cudaFree(h->d_partials);
     cudaFree(h->d_red);
+    for (void* c : h->ckpt) cudaFree(c);
+    h->ckpt.clear();
 }
 
 lbm_status check_device_error(lbm_handle* h) {
@@ -268,6 +280,41 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "the grid has no fluid node");
     }
+    // per tile of the step kernel: does a solid node lie within the box of cells the tile touches
+    // (the full tile, including cells of a ragged tile that wrap past the grid edge, plus a 3-node
+    // halo)?  Tiles without one skip the node-type staging.
+    {
+        int t[3];
+        step_tile_shape(c.lattice, c.precision, &t[0], &t[1], &t[2]);
+        const int n3[3] = {nx, ny, nz};
+        for (int k = 0; k < 3; ++k) {
+            h->int_tile[k] = t[k];
+            h->tiles[k] = (n3[k] + t[k] - 1) / t[k];
+        }
+        const int hz = h->D == 3 ? 3 : 0;
+        h->tile_solid.assign((size_t)h->tiles[0] * h->tiles[1] * h->tiles[2], 0);
+        if (nfluid < N) {
+            for (int tz = 0; tz < h->tiles[2]; ++tz)
+                for (int ty = 0; ty < h->tiles[1]; ++ty)
+                    for (int tx = 0; tx < h->tiles[0]; ++tx) {
+                        bool found = false;
+                        for (int dz = -hz; dz < (h->D == 3 ? t[2] + hz : 1) && !found; ++dz) {
+                            const int z = ((tz * t[2] + dz) % nz + nz) % nz;
+                            for (int dy = -3; dy < t[1] + 3 && !found; ++dy) {
+                                const int y = ((ty * t[1] + dy) % ny + ny) % ny;
+                                const uint8_t* row = solid_mask + ((long long)z * ny + y) * nx;
+                                for (int dx = -3; dx < t[0] + 3; ++dx) {
+                                    if (row[((tx * t[0] + dx) % nx + nx) % nx]) {
+                                        found = true;
+                                        break;
+                                    }
+                                }
+                            }
+                        }
+                        h->tile_solid[((size_t)tz * h->tiles[1] + ty) * h->tiles[0] + tx] = found ? 1 : 0;
+                    }
+        }
+    }
 
     const size_t ssize = c.precision == LBM_FP64 ? sizeof(double) : sizeof(float);
     h->fbytes = ssize * h->Q * (size_t)N;
@@ -283,6 +330,9 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     CKI(cudaMalloc(&h->f[0], h->fbytes), "cudaMalloc f");
     CKI(cudaMalloc(&h->f[1], h->fbytes), "cudaMalloc f");
     CKI(cudaMalloc(&h->d_type, N), "cudaMalloc type");
+    CKI(cudaMalloc(&h->d_tile_solid, h->tile_solid.size()), "cudaMalloc tile flags");
+    CKI(cudaMemcpyAsync(h->d_tile_solid, h->tile_solid.data(), h->tile_solid.size(), cudaMemcpyHostToDevice, h->stream),
+        "copy tile flags");
     CKI(cudaMalloc(&h->d_wall_id, sizeof(int) * N), "cudaMalloc wall_id");
     CKI(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc err");
     const size_t nw = h->wall_nodes.size();
@@ -345,6 +395,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.kappa_w = kappa_per_wall ? h->d_kappa : nullptr;
     p.wall_id = h->d_wall_id;
     p.type = h->d_type;
+    p.tile_solid = h->d_tile_solid;
     p.err = h->d_err;
 
     // initial state f = f^eq(rho0, u0), stored so that the first pull yields it
@@ -863,7 +914,10 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         d.kappa = h->dp.kappa;
         for (int z = 0; z < d.nz; z += tz)
             for (int y = 0; y < d.ny; y += ty)
-                for (int x = 0; x < d.nx; x += tx) items.push_back(BatchItem{i, x, y, z});
+                for (int x = 0; x < d.nx; x += tx) {
+                    const size_t t = ((size_t)(z / tz) * h->tiles[1] + y / ty) * h->tiles[0] + x / tx;
+                    items.push_back(BatchItem{i, x, y, z, int(h->tile_solid[t])});
+                }
     }
     b->n_items = int(items.size());
     int dev = 0, sms = 152;
@@ -872,7 +926,6 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     const long long cap = (long long)sms * batched_ctas_per_sm(b->lat, b->prec);
     b->ctas = int(b->n_items < cap ? b->n_items : cap);
     b->phys = b->inst[0]->dp;
-    lbm_status st = LBM_OK;
     cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
@@ -889,7 +942,6 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
     }
     b->phys.err = b->d_err;
-    (void)st;
     *out = b;
     return LBM_OK;
 }
@@ -939,3 +991,91 @@ void lbm_batch_destroy(lbm_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint (D2Q9): gradient of a loss of the final density with respect to per-wall-node kappa.
+// ---------------------------------------------------------------------------------------------
+
+extern "C" lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_every) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_step");
+    if (h->D != 2) return fail(h, LBM_ERR_ARG, "the adjoint is implemented for D2Q9");
+    if (n_steps < 1 || ckpt_every < 1) return fail(h, LBM_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+    if (h->cfg.wall_kind != LBM_WALL_IVD) return fail(h, LBM_ERR_ARG, "the adjoint differentiates the IVD scheme");
+    if (!h->dp.kappa_w) {
+        // switch to per-wall-node kappa (d_kappa already holds the scalar value at every wall node)
+        h->dp.kappa_w = h->d_kappa;
+        for (int i = 0; i < 2; ++i)
+            if (h->graph[i]) {
+                cudaGraphExecDestroy(h->graph[i]);
+                h->graph[i] = nullptr;
+            }
+    }
+    for (void* c : h->ckpt) cudaFree(c);
+    h->ckpt.clear();
+    h->rec_steps = 0;
+    const int64_t nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    for (int64_t c = 0; c < nck; ++c) {
+        void* buf = nullptr;
+        CK(h, cudaMalloc(&buf, h->fbytes));
+        h->ckpt.push_back(buf);
+        CK(h, cudaMemcpyAsync(buf, h->f[h->cur], h->fbytes, cudaMemcpyDeviceToDevice, h->stream));
+        const int64_t len = std::min(ckpt_every, n_steps - c * ckpt_every);
+        lbm_status st = enqueue_steps(h, len);
+        if (st != LBM_OK) return st;
+    }
+    h->rec_steps = n_steps;
+    h->rec_every = ckpt_every;
+    h->rec_end_step = h->step;
+    h->rec_end_cur = h->cur;
+    return check_device_error(h);
+}
+
+extern "C" lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, double* dkappa_host) {
+    if (!h || !drho_final_dev || !dkappa_host) return fail(h, LBM_ERR_ARG, "null argument");
+    if (h->rec_steps < 1 || h->step != h->rec_end_step || h->cur != h->rec_end_cur)
+        return fail(h, LBM_ERR_STATE, "lbm_adjoint needs an lbm_record whose final state is the current one");
+    const size_t nw = h->wall_nodes.size();
+    const int64_t every = h->rec_every, n = h->rec_steps;
+    const int64_t nck = (int64_t)h->ckpt.size();
+    const size_t es = h->prec == LBM_FP64 ? sizeof(double) : sizeof(float);
+    void* seg = nullptr;
+    void* mu[2] = {nullptr, nullptr};
+    void* scratch = nullptr;
+    double* dk = nullptr;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaMalloc(&seg, h->fbytes * (size_t)(every > 1 ? every - 1 : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&mu[0], h->fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&mu[1], h->fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, es * adjoint_scratch_elems(h->N));
+    if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(double) * (nw ? nw : 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double) * (nw ? nw : 1), h->stream);
+    AdjointScratch w{scratch};
+    int cur = 0;
+    if (e == cudaSuccess) e = launch_adjoint_final(h->prec, drho_final_dev, mu[cur], h->dp, h->stream);
+    std::vector<void*> sp((size_t)every);
+    for (int64_t c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
+        const int64_t len = std::min(every, n - c * every);
+        sp[0] = h->ckpt[c];
+        for (int64_t i = 1; i < len; ++i) sp[i] = static_cast<char*>(seg) + (size_t)(i - 1) * h->fbytes;
+        // recompute the segment's stored states f*_{k0 + 1} .. f*_{k0 + len - 1}
+        for (int64_t i = 0; i + 1 < len && e == cudaSuccess; ++i)
+            e = launch_step(h->lat, h->prec, sp[i], sp[i + 1], h->dp, h->stream);
+        for (int64_t i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+            e = launch_adjoint_step(h->prec, sp[i], mu[cur], mu[cur ^ 1], h->dp, w, dk, h->stream);
+            cur ^= 1;
+        }
+        h->launches += (len - 1) + 5 * len;
+    }
+    if (e == cudaSuccess && nw)
+        e = cudaMemcpyAsync(dkappa_host, dk, sizeof(double) * nw, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "adjoint");
+    cudaFree(seg);
+    cudaFree(mu[0]);
+    cudaFree(mu[1]);
+    cudaFree(scratch);
+    cudaFree(dk);
+    if (st != LBM_OK) return st;
+    return check_device_error(h);
+}

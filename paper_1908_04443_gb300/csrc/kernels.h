@@ -22,7 +22,8 @@ struct DevParams {
     double kappa, rho_w_const;
     const double* kappa_w;       // per wall node (device) or null
     const int* wall_id;          // per node: index into kappa_w (valid at wall nodes)
-    const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL
+    const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL | T_BULK
+    const uint8_t* tile_solid;   // per tile of the step kernel's grid: a solid node within the tile + 3-node halo
     unsigned* err;               // sticky device error flags
 };
 
@@ -39,6 +40,7 @@ struct BatchInstance {
 // One work item of the batched step: a tile of an instance.
 struct BatchItem {
     int inst, x0, y0, z0;
+    int solid;   // a solid node lies within the tile + 3-node halo
 };
 
 enum Lat { LAT_D2Q9 = 0, LAT_D3Q19 = 1 };

@@ -270,4 +270,84 @@ __host__ __device__ __forceinline__ void collide_d3q19(C (&f)[19], C drho, C rho
     f[18] = eyz0 - (a5 + a6) + (a7 + a8) - a14 - (a17 + a18);
 }
 
+// Reverse of collide_d2q9: given mu = dL/df* at one node, the adjoints of its inputs.  f holds the
+// post-streaming deviations, F = F_m + F_body the total force and psi_c the node's psi; on return
+// fbar[a] = dL/df_a (through the moments, u, rho and the equilibria), Fmbar = dL/dF_m (through F and
+// the consistency term X = |F_m|^2/psi_c^2) and psibar = dL/dpsi_c (through X only; F_m's own
+// dependence on psi is handled by the caller).
+template <class C>
+__host__ __device__ __forceinline__ void collide_d2q9_adjoint(const C (&f)[9], const C (&mu)[9], C rho, C ux, C uy,
+                                                              C Fx, C Fy, C Fmx, C Fmy, C psi_c, const Rates<C>& r,
+                                                              C (&fbar)[9], C& Fmbar_x, C& Fmbar_y, C& psibar) {
+    (void)f;
+    // dL/dm* = diag(1/|row|^2) M mu
+    const C u14 = mu[1] + mu[2] + mu[3] + mu[4];
+    const C u58 = mu[5] + mu[6] + mu[7] + mu[8];
+    const C ms0 = (mu[0] + u14 + u58) * C(1.0 / 9);
+    const C ms1 = (-C(4) * mu[0] - u14 + C(2) * u58) * C(1.0 / 36);
+    const C ms2 = (C(4) * mu[0] - C(2) * u14 + u58) * C(1.0 / 36);
+    const C ms3 = (mu[1] - mu[3] + mu[5] - mu[6] - mu[7] + mu[8]) * C(1.0 / 6);
+    const C ms4 = (-C(2) * mu[1] + C(2) * mu[3] + mu[5] - mu[6] - mu[7] + mu[8]) * C(1.0 / 12);
+    const C ms5 = (mu[2] - mu[4] + mu[5] + mu[6] - mu[7] - mu[8]) * C(1.0 / 6);
+    const C ms6 = (-C(2) * mu[2] + C(2) * mu[4] + mu[5] + mu[6] - mu[7] - mu[8]) * C(1.0 / 12);
+    const C ms7 = (mu[1] - mu[2] + mu[3] - mu[4]) * C(0.25);
+    const C ms8 = (mu[5] - mu[6] + mu[7] - mu[8]) * C(0.25);
+    const C h_e = C(1) - C(0.5) * r.s_e, h_eps = C(1) - C(0.5) * r.s_eps;
+    const C h_q = C(1) - C(0.5) * r.s_q, h_nu = C(1) - C(0.5) * r.s_nu;
+    const C u2 = ux * ux + uy * uy;
+    // adjoints of rho (= rho_ref + sum f), j, u and F
+    C Rb = ms0, jbx = ms3, jby = ms5, Fbx = ms3, Fby = ms5, ubx = C(0), uby = C(0);
+    // rows e, eps: relaxation towards -2 drho + 3 rho u^2 and drho - 3 rho u^2, source 6 u.F +- c X
+    const C a_e = r.s_e * ms1, a_eps = r.s_eps * ms2;
+    Rb += -C(2) * a_e + a_eps + C(3) * u2 * (a_e - a_eps);
+    ubx += C(6) * rho * ux * (a_e - a_eps);
+    uby += C(6) * rho * uy * (a_e - a_eps);
+    const C t_uF = C(6) * (h_e * ms1 - h_eps * ms2);
+    ubx += t_uF * Fx;
+    uby += t_uF * Fy;
+    Fbx += t_uF * ux;
+    Fby += t_uF * uy;
+    const C Xb = h_e * r.c_e * ms1 - h_eps * r.c_eps * ms2;
+    // rows qx, qy: relaxation towards -rho u, source -F
+    Rb += -r.s_q * (ms4 * ux + ms6 * uy);
+    ubx += -r.s_q * ms4 * rho;
+    uby += -r.s_q * ms6 * rho;
+    Fbx += -h_q * ms4;
+    Fby += -h_q * ms6;
+    // pxx: rho (ux^2 - uy^2), source 2 (ux Fx - uy Fy); pxy: rho ux uy, source ux Fy + uy Fx
+    const C a7 = r.s_nu * ms7, b7 = C(2) * h_nu * ms7, a8 = r.s_nu * ms8, b8 = h_nu * ms8;
+    Rb += a7 * (ux * ux - uy * uy) + a8 * ux * uy;
+    ubx += C(2) * a7 * rho * ux + b7 * Fx + a8 * rho * uy + b8 * Fy;
+    uby += -C(2) * a7 * rho * uy - b7 * Fy + a8 * rho * ux + b8 * Fx;
+    Fbx += b7 * ux + b8 * uy;
+    Fby += -b7 * uy + b8 * ux;
+    // u = (j + F/2) / rho
+    const C inv = C(1) / rho;
+    jbx += ubx * inv;
+    jby += uby * inv;
+    Fbx += C(0.5) * ubx * inv;
+    Fby += C(0.5) * uby * inv;
+    Rb += -(ubx * ux + uby * uy) * inv;
+    // X = |F_m|^2 / psi_c^2;  F = F_m + F_body
+    const C ip2 = C(1) / (psi_c * psi_c);
+    const C X = (Fmx * Fmx + Fmy * Fmy) * ip2;
+    Fmbar_x = Fbx + C(2) * Xb * Fmx * ip2;
+    Fmbar_y = Fby + C(2) * Xb * Fmy * ip2;
+    psibar = -C(2) * Xb * X / psi_c;
+    // f: rows e, eps, qx, qy, pxx, pxy of M (m-bar = (1 - s) m*-bar), plus rho and j
+    const C mb1 = (C(1) - r.s_e) * ms1, mb2 = (C(1) - r.s_eps) * ms2, mb4 = (C(1) - r.s_q) * ms4;
+    const C mb6 = (C(1) - r.s_q) * ms6, mb7 = (C(1) - r.s_nu) * ms7, mb8 = (C(1) - r.s_nu) * ms8;
+    const C b = -mb1 - C(2) * mb2 + Rb;
+    const C c = C(2) * mb1 + mb2 + Rb;
+    fbar[0] = -C(4) * mb1 + C(4) * mb2 + Rb;
+    fbar[1] = b - C(2) * mb4 + mb7 + jbx;
+    fbar[2] = b - C(2) * mb6 - mb7 + jby;
+    fbar[3] = b + C(2) * mb4 + mb7 - jbx;
+    fbar[4] = b + C(2) * mb6 - mb7 - jby;
+    fbar[5] = c + mb4 + mb6 + mb8 + jbx + jby;
+    fbar[6] = c - mb4 + mb6 - mb8 - jbx + jby;
+    fbar[7] = c - mb4 - mb6 + mb8 - jbx - jby;
+    fbar[8] = c + mb4 - mb6 - mb8 + jbx - jby;
+}
+
 }  // namespace lbmwet

@@ -65,10 +65,17 @@ Phys<C> make_phys(const DevParams& p) {
 struct Geo {
     int nx, ny, nz, N;
     const uint8_t* type;
+    const uint8_t* tile_solid;   // per tile (single-grid kernel) or null
     const int* wall_id;
     const double* kappa_w;   // per wall node or null
     double kappa;
 };
+
+// Division in compute precision: FP64 keeps IEEE division (parity with the FP64 oracle); the FP32
+// path uses the fast hardware approximation (relative error of a few ulp, below the rounding of the
+// FP32 state).
+__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 
 template <class C>
 __device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
@@ -76,9 +83,9 @@ __device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
     if (e.eos_kind == 1) {  // Carnahan-Starling
         const C eta = e.b4 * rho;
         const C om = C(1) - eta;
-        p = rho * e.RT * (C(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) - e.a * rho * rho;
+        p = cdiv(rho * e.RT * (C(1) + eta + eta * eta - eta * eta * eta), om * om * om) - e.a * rho * rho;
     } else {                // Peng-Robinson, Eq. 18
-        p = rho * e.RT / (C(1) - e.b * rho) - e.aphi * rho * rho / (C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho);
+        p = cdiv(rho * e.RT, C(1) - e.b * rho) - cdiv(e.aphi * rho * rho, C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho);
     }
     return e.two_over_G * (p - rho * C(1.0 / 3.0));   // Eq. 6 argument: 2 (p - rho c_s^2) / (G c^2)
 }
@@ -92,6 +99,46 @@ __device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err)
     }
     return sqrt(arg);
 }
+
+// The k-th cell of the one-cell-thick shell of an AX x AY (x AZ) box, enumerated so that
+// consecutive k are neighbouring cells (warps stay coherent).
+template <int AX, int AY, int AZ, int D>
+struct Shell {
+    static constexpr int COUNT = D == 2 ? 2 * AX + 2 * (AY - 2) : 2 * AX * AY + (AZ - 2) * (2 * AX + 2 * (AY - 2));
+    __device__ static __forceinline__ void cell(int k, int& x, int& y, int& z) {
+        if (D == 2) {
+            z = 0;
+            if (k < 2 * AX) {
+                y = k < AX ? 0 : AY - 1;
+                x = k < AX ? k : k - AX;
+            } else {
+                const int j = k - 2 * AX;
+                y = 1 + (j >> 1);
+                x = (j & 1) ? AX - 1 : 0;
+            }
+        } else {
+            constexpr int plane = AX * AY, per = 2 * AX + 2 * (AY - 2);
+            if (k < 2 * plane) {
+                z = k < plane ? 0 : AZ - 1;
+                const int r = k < plane ? k : k - plane;
+                x = r % AX;
+                y = r / AX;
+            } else {
+                const int j = k - 2 * plane;
+                z = 1 + j / per;
+                const int r = j % per;
+                if (r < 2 * AX) {
+                    y = r < AX ? 0 : AY - 1;
+                    x = r < AX ? r : r - AX;
+                } else {
+                    const int t = r - 2 * AX;
+                    y = 1 + (t >> 1);
+                    x = (t & 1) ? AX - 1 : 0;
+                }
+            }
+        }
+    }
+};
 
 __device__ __forceinline__ int wrap_full(int v, int n) {
     v %= n;
@@ -116,8 +163,8 @@ struct TileSmem {
 // One tile: x0, y0, z0 is its first node.  All threads of the CTA call this together.
 template <class L, class S, class C, int TX, int TY, int TZ, int MODE>
 __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
-                                          const Phys<C>& ph, int x0, int y0, int z0, unsigned* err,
-                                          double* __restrict__ rho_out, double* __restrict__ u_out,
+                                          const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid,
+                                          unsigned* err, double* __restrict__ rho_out, double* __restrict__ u_out,
                                           TileSmem<L, C, TX, TY, TZ>& sm) {
     using T = TileSmem<L, C, TX, TY, TZ>;
     constexpr int D = L::D, Q = L::Q;
@@ -135,10 +182,11 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     auto rix = [](int lx, int ly, int lz) { return (lz * RY + ly) * RX + lx; };
     auto pix = [](int lx, int ly, int lz) { return (lz * PY + ly) * PX + lx; };
 
-    // 0. node types of the tile + 3-node halo; does the 1-node halo region hold a wall node?
+    // 0. node types of the tile + 3-node halo (skipped when no solid node lies within it: then
+    //    every cell is a bulk fluid node); does the 1-node halo region hold a wall node?
     if (tid == 0) sm.nwall = 0;
     int wall_seen = 0;
-    for (int i = tid; i < YX * YY * YZ; i += NT) {
+    for (int i = tid; tile_solid && i < YX * YY * YZ; i += NT) {
         const int lx = i % YX, t = i / YX, ly = t % YY, lz = t / YY;
         const int gx = wx(x0 + lx - 3), gy = wy(y0 + ly - 3), gz = wz(z0 + lz - YZH);
         const uint8_t ty = g.type[(gz * ny + gy) * nx + gx];
@@ -148,6 +196,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         if (in_p && (ty & T_WALL)) wall_seen = 1;
     }
     const bool tile_has_wall = __syncthreads_or(wall_seen);
+    auto type_at = [&](int ti) -> uint8_t { return tile_solid ? sm.type[ti] : uint8_t(T_BULK); };
 
     // pull of one node at global (gx, gy, gz) whose type-tile cell is ti
     auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int ti, uint8_t self) {
@@ -187,7 +236,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     const int gx = wx(x0 + lx), gy = wy(y0 + ly), gz = wz(z0 + lz);
     const int gi = (gz * ny + gy) * nx + gx;
     const int my_ti = tix(lx + 3, ly + 3, lz + YZH);
-    const uint8_t my_type = sm.type[my_ti];
+    const uint8_t my_type = type_at(my_ti);
     const bool my_fluid = !(my_type & T_SOLID);
     C f[Q];
     {
@@ -209,12 +258,14 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         sm.rho[rix(lx + 2, ly + 2, lz + HZ)] = rho;
     }
     // 1b. the 1-node halo ring: density and psi (fluid) or queue (wall)
-    for (int i = tid; i < PX * PY * PZ; i += NT) {
-        const int px = i % PX, t = i / PX, py = t % PY, pz = t / PY;
-        if (px >= 1 && px <= TX && py >= 1 && py <= TY && (D == 2 || (pz >= 1 && pz <= TZ))) continue;
+    using ShellP = Shell<PX, PY, PZ, D>;
+    for (int k = tid; k < ShellP::COUNT; k += NT) {
+        int px, py, pz;
+        ShellP::cell(k, px, py, pz);
+        const int i = pix(px, py, pz);
         const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
         const int ti = tix(px + 2, py + 2, pz + (YZH - PZH));
-        const uint8_t ty = sm.type[ti];
+        const uint8_t ty = type_at(ti);
         C rho = C(0), psi = C(0);
         if (!(ty & T_SOLID)) {
             C h[Q];
@@ -232,9 +283,10 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     }
     // 1c. the 2-node halo ring, only where Eq. 17 will need it
     if (tile_has_wall) {
-        for (int i = tid; i < RX * RY * RZ; i += NT) {
-            const int rx = i % RX, t = i / RX, ry = t % RY, rz = t / RY;
-            if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && (D == 2 || (rz >= 1 && rz <= TZ + 2))) continue;
+        using ShellR = Shell<RX, RY, RZ, D>;
+        for (int k = tid; k < ShellR::COUNT; k += NT) {
+            int rx, ry, rz;
+            ShellR::cell(k, rx, ry, rz);
             const int cgx = wx(x0 + rx - 2), cgy = wy(y0 + ry - 2), cgz = wz(z0 + rz - HZ);
             const int ti = tix(rx + 1, ry + 1, rz + (YZH - HZ));
             const uint8_t ty = sm.type[ti];
@@ -247,7 +299,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                 for (int a = 0; a < Q; ++a) drho += h[a];
                 rho = ph.rho_ref + drho;
             }
-            sm.rho[i] = rho;
+            sm.rho[rix(rx, ry, rz)] = rho;
         }
     }
     __syncthreads();
@@ -274,7 +326,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                         den += C(L::wf(a));
                     }
                 }
-                const C rho_ave = num / den;
+                const C rho_ave = cdiv(num, den);
                 C kap;
                 if (g.kappa_w) {
                     const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
@@ -332,7 +384,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     const C rho = ph.rho_ref + drho;
     if (!(rho > C(0))) atomicOr(err, ERR_RHO);
     // Eq. 4: rho u = sum e f + F/2
-    const C inv = C(1) / rho;
+    const C inv = cdiv(C(1), rho);
     const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv, uz = (jz + C(0.5) * Fz) * inv;
     if (MODE == 1) {
         if (rho_out) rho_out[gi] = double(rho);
@@ -343,7 +395,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         }
         return;
     }
-    const C X = (Fmx * Fmx + Fmy * Fmy + Fmz * Fmz) / (psi_c * psi_c);
+    const C X = cdiv(Fmx * Fmx + Fmy * Fmy + Fmz * Fmz, psi_c * psi_c);
     if constexpr (D == 2) {
         collide_d2q9<C>(f, drho, rho, ux, uy, Fx, Fy, X, ph.r);
     } else {
@@ -367,8 +419,10 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
                double* __restrict__ rho_out, double* __restrict__ u_out) {
     using TS = TileShape<L, S>;
     __shared__ TileSmem<L, C, TS::X, TS::Y, TS::Z> sm;
+    const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
     tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
-                                                  blockIdx.z * TS::Z, err, rho_out, u_out, sm);
+                                                  blockIdx.z * TS::Z, solid, err, rho_out, u_out, sm);
 }
 
 // Batched step: CTAs walk the work list; each item is one tile of one instance.
@@ -387,14 +441,15 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
         g.nz = in.nz;
         g.N = in.N;
         g.type = in.type;
+        g.tile_solid = nullptr;
         g.wall_id = in.wall_id;
         g.kappa_w = in.kappa_w;
         g.kappa = in.kappa;
         const S* fin = static_cast<const S*>(in.f[parity]);
         S* fout = static_cast<S*>(in.f[parity ^ 1]);
         __syncthreads();   // the previous item's threads are done with shared memory
-        tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0>(fin, fout, g, ph, item.x0, item.y0, item.z0, err, nullptr, nullptr,
-                                                   sm);
+        tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0>(fin, fout, g, ph, item.x0, item.y0, item.z0, item.solid != 0, err,
+                                                   nullptr, nullptr, sm);
     }
 }
 
@@ -537,6 +592,7 @@ static Geo geo_of(const DevParams& p) {
     g.nz = p.nz;
     g.N = int(p.N);
     g.type = p.type;
+    g.tile_solid = p.tile_solid;
     g.wall_id = p.wall_id;
     g.kappa_w = p.kappa_w;
     g.kappa = p.kappa;

@@ -82,6 +82,8 @@ def _load():
         "lbm_destroy": (None, [H]),
         "lbm_last_error": (C.c_char_p, [H]),
         "lbm_status_string": (C.c_char_p, [C.c_int]),
+        "lbm_record": (C.c_int, [H, C.c_int64, C.c_int64]),
+        "lbm_adjoint": (C.c_int, [H, C.c_void_p, C.c_void_p]),
         "lbm_batch_init": (C.c_int, [C.c_int32, C.POINTER(lbm_config), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
         "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -104,7 +106,7 @@ _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
-            "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_batch_init", "lbm_batch_step",
+            "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_record", "lbm_adjoint", "lbm_batch_init", "lbm_batch_step",
             "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_handle", "lbm_batch_size",
             "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
 
@@ -247,6 +249,17 @@ def lbm_kernel_launches(h) -> int:
 
 def lbm_destroy(h):
     _lib.lbm_destroy(h)
+
+
+def lbm_record(h, n_steps: int, ckpt_every: int):
+    _check(_lib.lbm_record(h, int(n_steps), int(ckpt_every)), h)
+
+
+def lbm_adjoint(h, drho_final_dev_ptr: int, n_wall: int) -> np.ndarray:
+    """dL/dkappa per wall node; drho_final_dev_ptr is a device pointer to N doubles."""
+    out = np.zeros(max(n_wall, 1), dtype=np.float64)
+    _check(_lib.lbm_adjoint(h, drho_final_dev_ptr, out.ctypes.data_as(C.c_void_p)), h)
+    return out[:n_wall]
 
 
 def _bcheck(status: int, b=None):
