@@ -244,6 +244,48 @@ class Runner:
             self.L.lbm_destroy(self.h)
 
 
+def adjoint_ratio(L, torch, stream, steps=2000, ckpt=100):
+    """The 256 x 256 adjoint workload: per-wall-node kappa on a cylinder of radius 40, FP32, loss
+    sum (rho_T - rho_target)^2.  Times the forward pass with checkpoints (lbm_record) and the
+    gradient (lbm_adjoint: segment recomputation + reverse sweep) with CUDA events."""
+    wl = W.c5_adjoint_256()
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
+    rho_g, rho_l = L.lbm_coexistence(e)
+    cfg = make_cfg(L, wl, "fp32", rho_g, rho_l)
+    mask = wl.mask()
+    h = L.lbm_init(cfg, mask, wl.rho0(rho_l, rho_g), None, None, stream)
+    nw = len(L.lbm_wall_nodes(h))
+    cx, cy = wl.body_center
+    idx = L.lbm_wall_nodes(h)
+    ang = np.arctan2(idx // wl.shape[1] - cy, idx % wl.shape[1] - cx)
+    kappa = 0.1 + W.smooth_polar_field(ang)
+    L.lbm_set_kappa(h, kappa)
+    f0 = L.lbm_get_state(h, 9, wl.nodes)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        L.lbm_record(h, steps, ckpt)
+        ev[1].record(stream)
+    rho = torch.empty(wl.nodes, dtype=torch.float64, device="cuda")
+    L.lbm_fields_device(h, rho.data_ptr(), None)
+    torch.cuda.synchronize()
+    drho = 2.0 * (rho - rho.mean()) * torch.as_tensor(mask.reshape(-1) == 0, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[2].record(stream)
+        g = L.lbm_adjoint(h, drho.data_ptr(), nw)
+        ev[3].record(stream)
+    torch.cuda.synchronize()
+    fwd = ev[0].elapsed_time(ev[1])
+    adj = ev[2].elapsed_time(ev[3])
+    L.lbm_destroy(h)
+    return {"workload": f"c5_adjoint_256x256_fp32 ({steps} steps, checkpoint every {ckpt})", "wall_nodes": nw,
+            "forward_ms": round(fwd, 3), "adjoint_ms": round(adj, 3), "ratio": round(adj / fwd, 3),
+            "note": "adjoint = recomputation of each checkpoint segment + the reverse sweep; forward = "
+                    "the checkpointed forward pass", "grad_norm": float(np.linalg.norm(g))}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -367,6 +409,10 @@ def run_ours(args):
                                        "L2 not flushed"}
     run.close()
 
+    adjoint = None
+    if not args.no_extras and args.workload in ("c2", "c5"):
+        adjoint = adjoint_ratio(L, torch, stream, steps=args.adjoint_steps)
+
     # end to end through the public API with host buffers: init from host arrays, K calls of the
     # stepping entry point with one step each (each reads back the 4-byte device status), then the
     # observables with the host density and velocity fields of every instance
@@ -405,6 +451,8 @@ def run_ours(args):
             "kernel_hash": khash}
     if batched_vs_separate:
         line["batched_vs_separate"] = batched_vs_separate
+    if adjoint:
+        line["adjoint_vs_forward"] = adjoint
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -446,7 +494,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched-vs-separate comparison")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint side measurements")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
