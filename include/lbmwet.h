@@ -222,7 +222,8 @@ lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_every);
  * handle's state (else LBM_ERR_STATE).  drho_final_dev: DEVICE array of N doubles, dL/drho_T at
  * every node (ignored at solid nodes).  dkappa_host: host array, one double per wall node in
  * lbm_wall_nodes() order.  Recomputes each checkpoint segment's states, then runs the reverse
- * sweep; allocates (ckpt_every - 1) + 2 distribution buffers and 19 N scalars of scratch for the
+ * sweep (each segment replayed as a CUDA graph); allocates ckpt_every + 2 distribution buffers and 19 N
+ * scalars of scratch for the
  * call.  Synchronises the stream. */
 lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, double* dkappa_host);
 

@@ -17,6 +17,7 @@ LIB = os.path.join(HERE, "liblbmwet.so")
 OBJ = os.path.join(ROOT, "_build")
 SOURCES = ["step.cu", "reduce.cu", "adjoint.cu", "api.cu", "eos_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+EXTRA_FLAGS = os.environ.get("LBMWET_NVCC_FLAGS", "").split()   # e.g. tile-shape macros for measurements
 
 
 def nvcc() -> str:
@@ -29,7 +30,7 @@ def nvcc() -> str:
 def _compile(src: str, verbose_ptxas: bool) -> str:
     out = os.path.join(OBJ, os.path.basename(src) + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", out, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-lineinfo", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + ARCH
+           "-lineinfo", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + ARCH + EXTRA_FLAGS
     if verbose_ptxas and src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

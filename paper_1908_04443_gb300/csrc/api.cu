@@ -1039,38 +1039,66 @@ extern "C" lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, d
     const int64_t every = h->rec_every, n = h->rec_steps;
     const int64_t nck = (int64_t)h->ckpt.size();
     const size_t es = h->prec == LBM_FP64 ? sizeof(double) : sizeof(float);
+    // segment buffers: slot 0 receives a copy of the segment's checkpoint, slots 1.. the recomputed
+    // states; one CUDA graph per (segment length, adjoint-buffer parity) replays a whole segment
     void* seg = nullptr;
     void* mu[2] = {nullptr, nullptr};
     void* scratch = nullptr;
     double* dk = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<std::pair<std::pair<int64_t, int>, cudaGraphExec_t>> graphs;
     lbm_status st = LBM_OK;
-    cudaError_t e = cudaMalloc(&seg, h->fbytes * (size_t)(every > 1 ? every - 1 : 1));
+    cudaError_t e = cudaMalloc(&seg, h->fbytes * (size_t)every);
     if (e == cudaSuccess) e = cudaMalloc(&mu[0], h->fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&mu[1], h->fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&scratch, es * adjoint_scratch_elems(h->N));
     if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(double) * (nw ? nw : 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double) * (nw ? nw : 1), h->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     AdjointScratch w{scratch};
     int cur = 0;
     if (e == cudaSuccess) e = launch_adjoint_final(h->prec, drho_final_dev, mu[cur], h->dp, h->stream);
-    std::vector<void*> sp((size_t)every);
+    auto slot = [&](int64_t i) { return static_cast<void*>(static_cast<char*>(seg) + (size_t)i * h->fbytes); };
+    auto enqueue_segment = [&](int64_t len, int par, cudaStream_t s) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        for (int64_t i = 0; i + 1 < len && r == cudaSuccess; ++i)
+            r = launch_step(h->lat, h->prec, slot(i), slot(i + 1), h->dp, s);
+        int c2 = par;
+        for (int64_t i = len - 1; i >= 0 && r == cudaSuccess; --i) {
+            r = launch_adjoint_step(h->prec, slot(i), mu[c2], mu[c2 ^ 1], h->dp, w, dk, s);
+            c2 ^= 1;
+        }
+        return r;
+    };
     for (int64_t c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
         const int64_t len = std::min(every, n - c * every);
-        sp[0] = h->ckpt[c];
-        for (int64_t i = 1; i < len; ++i) sp[i] = static_cast<char*>(seg) + (size_t)(i - 1) * h->fbytes;
-        // recompute the segment's stored states f*_{k0 + 1} .. f*_{k0 + len - 1}
-        for (int64_t i = 0; i + 1 < len && e == cudaSuccess; ++i)
-            e = launch_step(h->lat, h->prec, sp[i], sp[i + 1], h->dp, h->stream);
-        for (int64_t i = len - 1; i >= 0 && e == cudaSuccess; --i) {
-            e = launch_adjoint_step(h->prec, sp[i], mu[cur], mu[cur ^ 1], h->dp, w, dk, h->stream);
-            cur ^= 1;
+        e = cudaMemcpyAsync(slot(0), h->ckpt[c], h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) break;
+        cudaGraphExec_t ex = nullptr;
+        for (auto& kv : graphs)
+            if (kv.first.first == len && kv.first.second == cur) ex = kv.second;
+        if (!ex) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) break;
+            cudaError_t r = enqueue_segment(len, cur, cap);
+            e = cudaStreamEndCapture(cap, &g);
+            if (r != cudaSuccess) e = r;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) break;
+            graphs.push_back({{len, cur}, ex});
         }
+        e = cudaGraphLaunch(ex, h->stream);
+        if (len % 2) cur ^= 1;
         h->launches += (len - 1) + 5 * len;
     }
     if (e == cudaSuccess && nw)
         e = cudaMemcpyAsync(dkappa_host, dk, sizeof(double) * nw, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) st = cuda_fail(h, e, "adjoint");
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    if (cap) cudaStreamDestroy(cap);
     cudaFree(seg);
     cudaFree(mu[0]);
     cudaFree(mu[1]);

@@ -408,9 +408,24 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
 // Tile shapes per lattice and precision (one thread per node).
 template <class L, class S>
 struct TileShape;
-template <> struct TileShape<D2Q9, float> { static constexpr int X = 32, Y = 16, Z = 1, MINB = 2; };
+#ifndef LBMWET_T2F_X   // tile of the FP32 D2Q9 kernels (compile-time; chosen by measurement)
+#define LBMWET_T2F_X 32
+#define LBMWET_T2F_Y 16
+#define LBMWET_T2F_MINB 2
+#endif
+#ifndef LBMWET_T3F_X   // tile of the FP32 D3Q19 kernels
+#define LBMWET_T3F_X 32
+#define LBMWET_T3F_Y 4
+#define LBMWET_T3F_Z 4
+#define LBMWET_T3F_MINB 1
+#endif
+template <> struct TileShape<D2Q9, float> {
+    static constexpr int X = LBMWET_T2F_X, Y = LBMWET_T2F_Y, Z = 1, MINB = LBMWET_T2F_MINB;
+};
 template <> struct TileShape<D2Q9, double> { static constexpr int X = 32, Y = 8, Z = 1, MINB = 2; };
-template <> struct TileShape<D3Q19, float> { static constexpr int X = 32, Y = 4, Z = 4, MINB = 1; };
+template <> struct TileShape<D3Q19, float> {
+    static constexpr int X = LBMWET_T3F_X, Y = LBMWET_T3F_Y, Z = LBMWET_T3F_Z, MINB = LBMWET_T3F_MINB;
+};
 template <> struct TileShape<D3Q19, double> { static constexpr int X = 32, Y = 4, Z = 2, MINB = 1; };
 
 template <class L, class S, class C, int MODE>
