@@ -2,17 +2,17 @@
 //
 // Forward step k (GPU storage): stored post-collision f*_k --pull (Eq. 3, Fig. 3)--> f (post-
 // streaming) --rho, psi, rho_w (Eqs. 4, 6, 16-17), F_m (Eq. 5), collision (Eqs. 2, 7)--> f*_{k+1}.
-// Its adjoint maps mu_{k+1} = dL/df*_{k+1} to mu_k = dL/df*_k and adds dL/dkappa_j:
-//   1. rho of the recomputed state                                    (adj_density)
-//   2. psi, psi'(rho), and at wall nodes rho_w with d rho_w/d kappa and d rho_w/d rho_ave / den
-//      (zero where the limiter clamps)                                  (adj_psi)
-//   3. per fluid node, the reverse of the collision: lambda_loc = dL/df, Fmbar = dL/dF_m and the
-//      node's own psi-bar                                               (adj_local)
-//   4. per node, psi-bar gathered through Eq. 5 from the neighbours' Fmbar; fluid nodes turn it
-//      into rho-bar, wall nodes into kappa-bar (accumulated) and a rho_ave-bar weight  (adj_psibar)
-//   5. per fluid node, rho-bar from its own psi and from its wall neighbours' Eq. 17 averages,
-//      lambda = lambda_loc + rho-bar, and the transpose of the pull (a push) into mu_k  (adj_push)
+// Its adjoint maps mu_{k+1} = dL/df*_{k+1} to mu_k = dL/df*_k and adds dL/dkappa_j, in two kernels:
+//   A (the forward tile body in its adjoint mode, step.cu): recompute rho, psi and rho_w of the
+//     state pulled from f*_k; per fluid node the reverse of the collision, lambda_loc = dL/df,
+//     Fmbar = dL/dF_m and the node's own psi-bar; psi'(rho), and at wall nodes d rho_w/d kappa and
+//     d rho_w/d rho_ave / den (zero where the limiter clamps);
+//   B (adj_gather_push): psi-bar gathered through Eq. 5 from the neighbours' Fmbar; fluid nodes
+//     turn it into rho-bar, wall nodes into kappa-bar and an Eq. 17 weight; then per fluid node
+//     lambda = lambda_loc + rho-bar (own psi and wall neighbours' averages) and the transpose of the
+//     pull (a push) into mu_k.
 #include <cmath>
+#include <type_traits>
 
 #include "adjoint.h"
 #include "lattice.cuh"
@@ -21,295 +21,150 @@ namespace lbmwet {
 
 namespace {
 
-constexpr int AB = 256;
-
-__device__ __forceinline__ int wrapn(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-template <class C>
-struct EosA {
-    int kind;
-    C RT, a, b, b4, aphi, two_over_G, G;
-};
-
-template <class C>
-__host__ __device__ EosA<C> eos_of(const DevParams& p) {
-    EosA<C> e;
-    e.kind = p.eos_kind;
-    e.RT = C(p.RT);
-    e.a = C(p.a);
-    e.b = C(p.b);
-    e.b4 = C(0.25 * p.b);
-    e.aphi = C(p.aphi);
-    e.two_over_G = C(p.two_over_G);
-    e.G = C(p.G);
-    return e;
+__device__ __forceinline__ int wrap_any(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
 }
 
-// p(rho) and dp/drho
-template <class C>
-__device__ __forceinline__ void pressure_and_slope(C rho, const EosA<C>& e, C& p, C& dp) {
-    if (e.kind == 1) {
-        const C eta = e.b4 * rho, om = C(1) - eta;
-        const C om3 = om * om * om;
-        const C Z = (C(1) + eta + eta * eta - eta * eta * eta) / om3;
-        const C dZ = (C(4) + C(4) * eta - C(2) * eta * eta) / (om3 * om);
-        p = rho * e.RT * Z - e.a * rho * rho;
-        dp = e.RT * (Z + eta * dZ) - C(2) * e.a * rho;
-    } else {
-        const C den = C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho;
-        const C dden = C(2) * e.b - C(2) * e.b * e.b * rho;
-        const C om = C(1) - e.b * rho;
-        p = rho * e.RT / om - e.aphi * rho * rho / den;
-        dp = e.RT / (om * om) - e.aphi * (C(2) * rho * den - rho * rho * dden) / (den * den);
-    }
-}
-
-// psi (Eq. 6) and d psi / d rho = (p'(rho) - 1/3) / (G psi)
-template <class C>
-__device__ __forceinline__ void psi_and_slope(C rho, const EosA<C>& e, C& psi, C& dpsi) {
-    C p, dp;
-    pressure_and_slope(rho, e, p, dp);
-    const C arg = e.two_over_G * (p - rho * C(1.0 / 3.0));
-    psi = arg > C(0) ? sqrt(arg) : C(0);
-    dpsi = psi > C(0) ? (dp - C(1.0 / 3.0)) / (e.G * psi) : C(0);
-}
-
-template <class S, class C>
-__device__ __forceinline__ void pull9(const S* __restrict__ fin, const uint8_t* __restrict__ type, int x, int y,
-                                      int nx, int ny, int N, C (&f)[9]) {
-    const int g = y * nx + x;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int sx = wrapn(x - D2Q9::ex(a), nx), sy = wrapn(y - D2Q9::ey(a), ny);
-        const int s = sy * nx + sx;
-        f[a] = (type[s] & T_SOLID) ? C(fin[D2Q9::opp(a) * N + g]) : C(fin[a * N + s]);
-    }
-}
-
-template <class S, class C>
-__global__ void __launch_bounds__(AB) adj_density(const S* __restrict__ fin, DevParams p, C* __restrict__ rho_out) {
-    const int N = int(p.N), nx = p.nx, ny = p.ny;
-    const C rho_ref = C(p.rho_ref);
-    for (int g = blockIdx.x * AB + threadIdx.x; g < N; g += gridDim.x * AB) {
-        if (p.type[g] & T_SOLID) {
-            rho_out[g] = C(0);
-            continue;
-        }
-        C f[9];
-        pull9<S, C>(fin, p.type, g % nx, g / nx, nx, ny, N, f);
-        C d = C(0);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) d += f[a];
-        rho_out[g] = rho_ref + d;
-    }
-}
-
-template <class C>
-__global__ void __launch_bounds__(AB) adj_psi(DevParams p, const C* __restrict__ rho, C* __restrict__ psi,
-                                              C* __restrict__ dpsi, C* __restrict__ drw_k, C* __restrict__ drw_a) {
-    const int N = int(p.N), nx = p.nx, ny = p.ny;
-    const EosA<C> e = eos_of<C>(p);
-    const C rho_l = C(p.rho_l), rho_g = C(p.rho_g);
-    for (int g = blockIdx.x * AB + threadIdx.x; g < N; g += gridDim.x * AB) {
-        const uint8_t t = p.type[g];
-        C ps = C(0), dps = C(0), dk = C(0), da = C(0);
-        if (!(t & T_SOLID)) {
-            psi_and_slope(rho[g], e, ps, dps);
-        } else if (t & T_WALL) {
-            C rw;
-            if (p.wall_kind == 1) {
-                rw = C(p.rho_w_const);
-            } else {
-                const int x = g % nx, y = g / nx;
-                C num = C(0), den = C(0);
-#pragma unroll
-                for (int a = 1; a < 9; ++a) {
-                    const int s = wrapn(y + D2Q9::ey(a), ny) * nx + wrapn(x + D2Q9::ex(a), nx);
-                    if (!(p.type[s] & T_SOLID)) {
-                        num += C(D2Q9::wf(a)) * rho[s];
-                        den += C(D2Q9::wf(a));
-                    }
-                }
-                const C ra = num / den;
-                const C kap = p.kappa_w ? C(p.kappa_w[p.wall_id[g]]) : C(p.kappa);
-                const C raw = kap >= C(0) ? (C(1) + kap) * ra : ra + kap;
-                rw = raw > rho_l ? rho_l : (raw < rho_g ? rho_g : raw);
-                if (raw < rho_l && raw > rho_g) {   // the limiter is inactive
-                    dk = kap >= C(0) ? ra : C(1);
-                    da = (kap >= C(0) ? C(1) + kap : C(1)) / den;
-                }
-            }
-            psi_and_slope(rw, e, ps, dps);
-        }
-        psi[g] = ps;
-        dpsi[g] = dps;
-        drw_k[g] = dk;
-        drw_a[g] = da;
-    }
-}
-
-template <class S, class C>
-__global__ void __launch_bounds__(AB) adj_local(const S* __restrict__ fin, const C* __restrict__ mu, DevParams p,
-                                                const C* __restrict__ psi, C* __restrict__ lam, C* __restrict__ fmb_x,
-                                                C* __restrict__ fmb_y, C* __restrict__ psib) {
-    const int N = int(p.N), nx = p.nx, ny = p.ny;
-    Rates<C> r;
-    r.s_e = C(p.s_e);
-    r.s_eps = C(p.s_eps);
-    r.s_q = C(p.s_q);
-    r.s_nu = C(p.s_nu);
-    r.s_pi = C(p.s_pi);
-    r.s_m = C(p.s_m);
-    r.c_e = C(p.c_e);
-    r.c_eps = C(p.c_eps);
-    const C G = C(p.G), rho_ref = C(p.rho_ref);
-    for (int g = blockIdx.x * AB + threadIdx.x; g < N; g += gridDim.x * AB) {
-        if (p.type[g] & T_SOLID) {
-            fmb_x[g] = C(0);
-            fmb_y[g] = C(0);
-            psib[g] = C(0);
-            continue;
-        }
-        const int x = g % nx, y = g / nx;
-        C f[9];
-        pull9<S, C>(fin, p.type, x, y, nx, ny, N, f);
-        const C psi_c = psi[g];
-        C sx = C(0), sy = C(0);
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-            const C v = C(D2Q9::wf(a)) * psi[wrapn(y + D2Q9::ey(a), ny) * nx + wrapn(x + D2Q9::ex(a), nx)];
-            sx += C(D2Q9::ex(a)) * v;
-            sy += C(D2Q9::ey(a)) * v;
-        }
-        const C Fmx = -G * psi_c * sx, Fmy = -G * psi_c * sy;
-        const C Fx = Fmx + C(p.fx), Fy = Fmy + C(p.fy);
-        C drho = C(0), jx = C(0), jy = C(0);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            drho += f[a];
-            jx += C(D2Q9::ex(a)) * f[a];
-            jy += C(D2Q9::ey(a)) * f[a];
-        }
-        const C rho = rho_ref + drho;
-        const C ux = (jx + C(0.5) * Fx) / rho, uy = (jy + C(0.5) * Fy) / rho;
-        C m[9], fb[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) m[a] = mu[a * N + g];
-        C bx, by, pb;
-        collide_d2q9_adjoint<C>(f, m, rho, ux, uy, Fx, Fy, Fmx, Fmy, psi_c, r, fb, bx, by, pb);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) lam[a * N + g] = fb[a];
-        fmb_x[g] = bx;
-        fmb_y[g] = by;
-        // F_m = -G psi(x) sum w psi(x+e) e: its dependence on psi(x) is F_m / psi(x)
-        psib[g] = pb + (bx * Fmx + by * Fmy) / psi_c;
-    }
-}
-
-template <class C>
-__global__ void __launch_bounds__(AB) adj_psibar(DevParams p, const C* __restrict__ psi, const C* __restrict__ dpsi,
-                                                 const C* __restrict__ drw_k, const C* __restrict__ drw_a,
-                                                 const C* __restrict__ fmb_x, const C* __restrict__ fmb_y,
-                                                 const C* __restrict__ psib, C* __restrict__ rhob, C* __restrict__ wb,
-                                                 double* __restrict__ dkappa) {
-    const int N = int(p.N), nx = p.nx, ny = p.ny;
+// psi-bar gathered through Eq. 5, rho-bar / kappa-bar, and the push (transpose of the pull), for a
+// TX x TY tile.  psi-bar(y) = psib(y) + sum_a [x = y - e_a fluid] (-G psi(x) w_a e_a . Fmbar(x)).
+template <class C, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) adj_gather_push(DevParams p, const C* __restrict__ psi,
+                                                          const C* __restrict__ dpsi, const C* __restrict__ drw_k,
+                                                          const C* __restrict__ drw_a, const C* __restrict__ fmb_x,
+                                                          const C* __restrict__ fmb_y, const C* __restrict__ psib,
+                                                          const C* __restrict__ lam, double* __restrict__ dkappa,
+                                                          C* __restrict__ mu_out) {
+    constexpr int RX = TX + 4, RY = TY + 4, PX = TX + 2, PY = TY + 2, NT = TX * TY;
+    __shared__ uint8_t s_t[RY * RX];
+    __shared__ C s_psi[RY * RX], s_fx[RY * RX], s_fy[RY * RX];
+    __shared__ C s_rb[PY * PX], s_wb[PY * PX];
+    const int nx = p.nx, ny = p.ny, N = int(p.N);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
     const C G = C(p.G);
-    for (int g = blockIdx.x * AB + threadIdx.x; g < N; g += gridDim.x * AB) {
-        const uint8_t t = p.type[g];
+    // 0. types, psi and Fmbar on the tile + 2-node halo
+    for (int i = tid; i < RX * RY; i += NT) {
+        const int gx = wrap_any(x0 + i % RX - 2, nx), gy = wrap_any(y0 + i / RX - 2, ny);
+        const int g = gy * nx + gx;
+        s_t[i] = p.type[g];
+        s_psi[i] = psi[g];
+        s_fx[i] = fmb_x[g];
+        s_fy[i] = fmb_y[g];
+    }
+    __syncthreads();
+    // 1. psi-bar on the tile + 1-node halo; fluid -> rho-bar, wall -> kappa-bar and the Eq. 17 weight
+    for (int i = tid; i < PX * PY; i += NT) {
+        const int px = i % PX, py = i / PX;
+        const int r = (py + 1) * RX + px + 1;
+        const uint8_t t = s_t[r];
         const bool fluid = !(t & T_SOLID);
         if (!fluid && !(t & T_WALL)) {
-            rhob[g] = C(0);
-            wb[g] = C(0);
+            s_rb[i] = C(0);
+            s_wb[i] = C(0);
             continue;
         }
-        const int x = g % nx, y = g / nx;
-        // psi(y) enters F_m(x) of every fluid x = y - e_a with weight -G psi(x) w_a e_a
+        const int gx = wrap_any(x0 + px - 1, nx), gy = wrap_any(y0 + py - 1, ny);
+        const int g = gy * nx + gx;
         C pb = fluid ? psib[g] : C(0);
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
-            const int s = wrapn(y - D2Q9::ey(a), ny) * nx + wrapn(x - D2Q9::ex(a), nx);
-            if (p.type[s] & T_SOLID) continue;
-            const C proj = fmb_x[s] * C(D2Q9::ex(a)) + fmb_y[s] * C(D2Q9::ey(a));
-            pb += -G * psi[s] * C(D2Q9::wf(a)) * proj;
+            const int rs = r - D2Q9::ex(a) - D2Q9::ey(a) * RX;
+            if (s_t[rs] & T_SOLID) continue;
+            pb += -G * s_psi[rs] * C(D2Q9::wf(a)) * (s_fx[rs] * C(D2Q9::ex(a)) + s_fy[rs] * C(D2Q9::ey(a)));
         }
         const C rb = pb * dpsi[g];
         if (fluid) {
-            rhob[g] = rb;
-            wb[g] = C(0);
+            s_rb[i] = rb;
+            s_wb[i] = C(0);
         } else {
-            rhob[g] = C(0);
-            wb[g] = rb * drw_a[g];
-            if (p.kappa_w) dkappa[p.wall_id[g]] += double(rb * drw_k[g]);
+            s_rb[i] = C(0);
+            s_wb[i] = rb * drw_a[g];
+            const bool own = px >= 1 && px <= TX && py >= 1 && py <= TY && x0 + px - 1 < nx && y0 + py - 1 < ny;
+            if (own && p.kappa_w) dkappa[p.wall_id[g]] += double(rb * drw_k[g]);
+        }
+    }
+    __syncthreads();
+    // 2. lambda = lam + rho-bar at the tile's fluid nodes, pushed to mu (the transpose of the pull)
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    if (x0 + lx >= nx || y0 + ly >= ny) return;
+    const int r = (ly + 2) * RX + lx + 2;
+    if (s_t[r] & T_SOLID) return;
+    const int pi = (ly + 1) * PX + lx + 1;
+    C rb = s_rb[pi];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        if (s_t[r + D2Q9::ex(a) + D2Q9::ey(a) * RX] & T_WALL)
+            rb += C(D2Q9::wf(a)) * s_wb[pi + D2Q9::ex(a) + D2Q9::ey(a) * PX];
+    }
+    const int gx = x0 + lx, gy = y0 + ly, g = gy * nx + gx;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const C l = lam[a * N + g] + rb;
+        const int rs = r - D2Q9::ex(a) - D2Q9::ey(a) * RX;
+        if (s_t[rs] & T_SOLID) {
+            mu_out[D2Q9::opp(a) * N + g] = l;
+        } else {
+            const int sx = wrap_any(gx - D2Q9::ex(a), nx), sy = wrap_any(gy - D2Q9::ey(a), ny);
+            mu_out[a * N + sy * nx + sx] = l;
         }
     }
 }
 
-// lambda = lam + rho-bar (own psi and wall neighbours' averages); push: lambda_a(z) -> mu_a(z - e_a)
-// if z - e_a is fluid, else mu_abar(z)
-template <class C, bool FINAL>
-__global__ void __launch_bounds__(AB) adj_push(DevParams p, const C* __restrict__ lam, const C* __restrict__ rhob,
-                                               const C* __restrict__ wb, const double* __restrict__ drho_final,
-                                               C* __restrict__ mu_out) {
+// mu_n from dL/drho_T: every direction of a fluid node carries dL/drho_T, pushed like step 2 above
+template <class C>
+__global__ void __launch_bounds__(256) adj_final_push(DevParams p, const double* __restrict__ drho,
+                                                      C* __restrict__ mu_out) {
     const int N = int(p.N), nx = p.nx, ny = p.ny;
-    for (int g = blockIdx.x * AB + threadIdx.x; g < N; g += gridDim.x * AB) {
+    for (int g = blockIdx.x * 256 + threadIdx.x; g < N; g += gridDim.x * 256) {
         if (p.type[g] & T_SOLID) continue;
         const int x = g % nx, y = g / nx;
-        C rb;
-        if (FINAL) {
-            rb = C(drho_final[g]);
-        } else {
-            rb = rhob[g];
-#pragma unroll
-            for (int a = 1; a < 9; ++a) {
-                const int s = wrapn(y + D2Q9::ey(a), ny) * nx + wrapn(x + D2Q9::ex(a), nx);
-                if (p.type[s] & T_WALL) rb += C(D2Q9::wf(a)) * wb[s];
-            }
-        }
+        const C l = C(drho[g]);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const C l = FINAL ? rb : lam[a * N + g] + rb;
-            const int s = wrapn(y - D2Q9::ey(a), ny) * nx + wrapn(x - D2Q9::ex(a), nx);
+            const int s = wrap_any(y - D2Q9::ey(a), ny) * nx + wrap_any(x - D2Q9::ex(a), nx);
             if (p.type[s] & T_SOLID) mu_out[D2Q9::opp(a) * N + g] = l;
             else mu_out[a * N + s] = l;
         }
     }
 }
 
-unsigned grid_of(long long n) {
-    long long b = (n + AB - 1) / AB;
-    if (b > 152LL * 16) b = 152LL * 16;
-    return unsigned(b < 1 ? 1 : b);
-}
+constexpr int GX = 32, GY = 8;
 
 template <class S>
 cudaError_t adjoint_step_t(const void* fstar_k, const void* mu_next, void* mu_prev, const DevParams& p,
                            const AdjointScratch& w, double* dkappa, cudaStream_t s) {
-    using C = S;
-    const unsigned g = grid_of(p.N);
-    const int N = int(p.N);
-    C* rho = static_cast<C*>(w.buf) + 0 * (size_t)N;
-    C* psi = static_cast<C*>(w.buf) + 1 * (size_t)N;
-    C* dpsi = static_cast<C*>(w.buf) + 2 * (size_t)N;
-    C* drw_k = static_cast<C*>(w.buf) + 3 * (size_t)N;
-    C* drw_a = static_cast<C*>(w.buf) + 4 * (size_t)N;
-    C* fmb_x = static_cast<C*>(w.buf) + 5 * (size_t)N;
-    C* fmb_y = static_cast<C*>(w.buf) + 6 * (size_t)N;
-    C* psib = static_cast<C*>(w.buf) + 7 * (size_t)N;
-    C* rhob = static_cast<C*>(w.buf) + 8 * (size_t)N;
-    C* wb = static_cast<C*>(w.buf) + 9 * (size_t)N;
-    C* lam = static_cast<C*>(w.buf) + 10 * (size_t)N;   // 9 N values
-    const S* fin = static_cast<const S*>(fstar_k);
-    adj_density<S, C><<<g, AB, 0, s>>>(fin, p, rho);
-    adj_psi<C><<<g, AB, 0, s>>>(p, rho, psi, dpsi, drw_k, drw_a);
-    adj_local<S, C><<<g, AB, 0, s>>>(fin, static_cast<const C*>(mu_next), p, psi, lam, fmb_x, fmb_y, psib);
-    adj_psibar<C><<<g, AB, 0, s>>>(p, psi, dpsi, drw_k, drw_a, fmb_x, fmb_y, psib, rhob, wb, dkappa);
-    adj_push<C, false><<<g, AB, 0, s>>>(p, lam, rhob, wb, nullptr, static_cast<C*>(mu_prev));
+    const size_t N = size_t(p.N);
+    S* b = static_cast<S*>(w.buf);
+    AdjointFields f;
+    f.mu = mu_next;
+    f.lam = b;
+    f.fmb_x = b + 9 * N;
+    f.fmb_y = b + 10 * N;
+    f.psib = b + 11 * N;
+    f.psi = b + 12 * N;
+    f.dpsi = b + 13 * N;
+    f.drw_k = b + 14 * N;
+    f.drw_a = b + 15 * N;
+    cudaError_t e = launch_adjoint_local(std::is_same<S, double>::value ? PREC_FP64 : PREC_FP32, fstar_k, p, f, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.nx + GX - 1) / GX, (p.ny + GY - 1) / GY, 1);
+    adj_gather_push<S, GX, GY><<<grid, dim3(GX, GY, 1), 0, s>>>(
+        p, static_cast<const S*>(f.psi), static_cast<const S*>(f.dpsi), static_cast<const S*>(f.drw_k),
+        static_cast<const S*>(f.drw_a), static_cast<const S*>(f.fmb_x), static_cast<const S*>(f.fmb_y),
+        static_cast<const S*>(f.psib), static_cast<const S*>(f.lam), dkappa, static_cast<S*>(mu_prev));
     return cudaGetLastError();
+}
+
+unsigned grid_of(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return unsigned(b < 1 ? 1 : b);
 }
 
 }  // namespace
 
-size_t adjoint_scratch_elems(long long N) { return size_t(N) * 19; }
+size_t adjoint_scratch_elems(long long N) { return size_t(N) * 16; }
 
 cudaError_t launch_adjoint_step(int prec, const void* fstar_k, const void* mu_next, void* mu_prev, const DevParams& p,
                                 const AdjointScratch& w, double* dkappa, cudaStream_t s) {
@@ -319,10 +174,8 @@ cudaError_t launch_adjoint_step(int prec, const void* fstar_k, const void* mu_ne
 
 cudaError_t launch_adjoint_final(int prec, const double* drho_final, void* mu, const DevParams& p, cudaStream_t s) {
     const unsigned g = grid_of(p.N);
-    if (prec == PREC_FP64)
-        adj_push<double, true><<<g, AB, 0, s>>>(p, nullptr, nullptr, nullptr, drho_final, static_cast<double*>(mu));
-    else
-        adj_push<float, true><<<g, AB, 0, s>>>(p, nullptr, nullptr, nullptr, drho_final, static_cast<float*>(mu));
+    if (prec == PREC_FP64) adj_final_push<double><<<g, 256, 0, s>>>(p, drho_final, static_cast<double*>(mu));
+    else adj_final_push<float><<<g, 256, 0, s>>>(p, drho_final, static_cast<float*>(mu));
     return cudaGetLastError();
 }
 
