@@ -877,6 +877,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         if (!same_physics(cfgs[0], cfgs[i]))
             return bfail(nullptr, LBM_ERR_ARG, "instance " + std::to_string(i) + " differs from instance 0 in lattice, "
                                                 "precision or physics (only grid, kappa, body and hint may differ)");
+    if (cfgs[0].lattice != LBM_D2Q9) return bfail(nullptr, LBM_ERR_ARG, "batches are implemented for D2Q9");
     lbm_batch* b = new lbm_batch();
     b->stream = static_cast<cudaStream_t>(stream);
     b->lat = cfgs[0].lattice;

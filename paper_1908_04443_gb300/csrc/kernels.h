@@ -63,6 +63,11 @@ cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, 
 // instance of the batch; each instance reads f[parity] and writes f[parity ^ 1].
 cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& phys, const BatchInstance* insts,
                                 const BatchItem* items, int n_items, int ctas, cudaStream_t s);
+// D3Q19 z-march step (mode 0: time step, 1: fields) and its tile (x, y, z-chunk).
+struct Geo;
+cudaError_t launch_step3d(int prec, int mode, const void* fin, void* fout, const Geo& g, const DevParams& p,
+                          double* rho, double* u, cudaStream_t s);
+void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz);
 // Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);
 int batched_ctas_per_sm(int lat, int prec);

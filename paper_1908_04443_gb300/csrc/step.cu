@@ -17,136 +17,14 @@
 // CUDA grid) and a batch of grids (a persistent grid walking a work list of (instance, tile)).
 #include <cmath>
 
+#include "adjoint.h"
 #include "kernels.h"
 #include "lattice.cuh"
+#include "tile_common.cuh"
 
 namespace lbmwet {
 
-// physics constants in compute precision
-template <class C>
-struct Phys {
-    int eos_kind, wall_kind;
-    C RT, a, b, b4, aphi, two_over_G, G;
-    C rho_l, rho_g, rho_ref, fx, fy, fz, rho_w_const;
-    Rates<C> r;
-};
-
-template <class C>
-Phys<C> make_phys(const DevParams& p) {
-    Phys<C> h;
-    h.eos_kind = p.eos_kind;
-    h.wall_kind = p.wall_kind;
-    h.RT = C(p.RT);
-    h.a = C(p.a);
-    h.b = C(p.b);
-    h.b4 = C(0.25 * p.b);
-    h.aphi = C(p.aphi);
-    h.two_over_G = C(p.two_over_G);
-    h.G = C(p.G);
-    h.rho_l = C(p.rho_l);
-    h.rho_g = C(p.rho_g);
-    h.rho_ref = C(p.rho_ref);
-    h.fx = C(p.fx);
-    h.fy = C(p.fy);
-    h.fz = C(p.fz);
-    h.rho_w_const = C(p.rho_w_const);
-    h.r.s_e = C(p.s_e);
-    h.r.s_eps = C(p.s_eps);
-    h.r.s_q = C(p.s_q);
-    h.r.s_nu = C(p.s_nu);
-    h.r.s_pi = C(p.s_pi);
-    h.r.s_m = C(p.s_m);
-    h.r.c_e = C(p.c_e);
-    h.r.c_eps = C(p.c_eps);
-    return h;
-}
-
-// geometry of one grid
-struct Geo {
-    int nx, ny, nz, N;
-    const uint8_t* type;
-    const uint8_t* tile_solid;   // per tile (single-grid kernel) or null
-    const int* wall_id;
-    const double* kappa_w;   // per wall node or null
-    double kappa;
-};
-
-// Division in compute precision: FP64 keeps IEEE division (parity with the FP64 oracle); the FP32
-// path uses the fast hardware approximation (relative error of a few ulp, below the rounding of the
-// FP32 state).
-__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
-
-template <class C>
-__device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
-    C p;
-    if (e.eos_kind == 1) {  // Carnahan-Starling
-        const C eta = e.b4 * rho;
-        const C om = C(1) - eta;
-        p = cdiv(rho * e.RT * (C(1) + eta + eta * eta - eta * eta * eta), om * om * om) - e.a * rho * rho;
-    } else {                // Peng-Robinson, Eq. 18
-        p = cdiv(rho * e.RT, C(1) - e.b * rho) - cdiv(e.aphi * rho * rho, C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho);
-    }
-    return e.two_over_G * (p - rho * C(1.0 / 3.0));   // Eq. 6 argument: 2 (p - rho c_s^2) / (G c^2)
-}
-
-template <class C>
-__device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err) {
-    const C arg = psi_arg(rho, e);
-    if (!(arg > C(0))) {
-        atomicOr(err, ERR_PSI);
-        return C(0);
-    }
-    return sqrt(arg);
-}
-
-// The k-th cell of the one-cell-thick shell of an AX x AY (x AZ) box, enumerated so that
-// consecutive k are neighbouring cells (warps stay coherent).
-template <int AX, int AY, int AZ, int D>
-struct Shell {
-    static constexpr int COUNT = D == 2 ? 2 * AX + 2 * (AY - 2) : 2 * AX * AY + (AZ - 2) * (2 * AX + 2 * (AY - 2));
-    __device__ static __forceinline__ void cell(int k, int& x, int& y, int& z) {
-        if (D == 2) {
-            z = 0;
-            if (k < 2 * AX) {
-                y = k < AX ? 0 : AY - 1;
-                x = k < AX ? k : k - AX;
-            } else {
-                const int j = k - 2 * AX;
-                y = 1 + (j >> 1);
-                x = (j & 1) ? AX - 1 : 0;
-            }
-        } else {
-            constexpr int plane = AX * AY, per = 2 * AX + 2 * (AY - 2);
-            if (k < 2 * plane) {
-                z = k < plane ? 0 : AZ - 1;
-                const int r = k < plane ? k : k - plane;
-                x = r % AX;
-                y = r / AX;
-            } else {
-                const int j = k - 2 * plane;
-                z = 1 + j / per;
-                const int r = j % per;
-                if (r < 2 * AX) {
-                    y = r < AX ? 0 : AY - 1;
-                    x = r < AX ? r : r - AX;
-                } else {
-                    const int t = r - 2 * AX;
-                    y = 1 + (t >> 1);
-                    x = (t & 1) ? AX - 1 : 0;
-                }
-            }
-        }
-    }
-};
-
-__device__ __forceinline__ int wrap_full(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-template <class L, class C, int TX, int TY, int TZ>
+template <class L, class C, int TX, int TY, int TZ, bool ADJ = false>
 struct TileSmem {
     static constexpr int D = L::D;
     static constexpr int HZ = (D == 3) ? 2 : 0, PZH = (D == 3) ? 1 : 0, YZH = (D == 3) ? 3 : 0;
@@ -158,15 +36,51 @@ struct TileSmem {
     C psi[PZ * PY * PX];
     short wall[PZ * PY * PX];    // queued wall cells (psi-tile indices)
     int nwall;
+    // adjoint mode: at wall cells d rho_w/d kappa, d rho_w/d rho_ave / den and d psi/d rho at rho_w
+    C wdk[ADJ ? PZ * PY * PX : 1], wda[ADJ ? PZ * PY * PX : 1], wdpsi[ADJ ? PZ * PY * PX : 1];
 };
 
+// Outputs of the adjoint mode of the tile body (one value per node unless noted).
+template <class C>
+struct AdjIO {
+    const C* mu;      // dL/df* of the step's output, [a][node]
+    C* lam;           // dL/df through the collision, [a][node]
+    C* fmb_x;         // dL/dF_m
+    C* fmb_y;
+    C* psib;          // dL/dpsi(x) through the node's own collision (X term and F_m's psi(x) factor)
+    C* psi;           // psi (fluid) or psi(rho_w) (wall)
+    C* dpsi;          // d psi/d rho at rho or rho_w
+    C* drw_k;         // walls: d rho_w / d kappa (0 when the limiter clamps)
+    C* drw_a;         // walls: d rho_w / d rho_ave / den
+};
+
+// d psi / d rho = (p'(rho) - 1/3) / (G psi), with p' from the equation of state
+template <class C>
+__device__ __forceinline__ C psi_slope(C rho, C psi, const Phys<C>& e) {
+    C dp;
+    if (e.eos_kind == 1) {
+        const C eta = e.b4 * rho, om = C(1) - eta;
+        const C om3 = om * om * om;
+        const C Z = (C(1) + eta + eta * eta - eta * eta * eta) / om3;
+        const C dZ = (C(4) + C(4) * eta - C(2) * eta * eta) / (om3 * om);
+        dp = e.RT * (Z + eta * dZ) - C(2) * e.a * rho;
+    } else {
+        const C den = C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho;
+        const C dden = C(2) * e.b - C(2) * e.b * e.b * rho;
+        const C om = C(1) - e.b * rho;
+        dp = e.RT / (om * om) - e.aphi * (C(2) * rho * den - rho * rho * dden) / (den * den);
+    }
+    return psi > C(0) ? (dp - C(1.0 / 3.0)) / (e.G * psi) : C(0);
+}
+
 // One tile: x0, y0, z0 is its first node.  All threads of the CTA call this together.
+// MODE 0: time step (writes f*); 1: fields (writes rho, u); 2: adjoint local part (writes AdjIO).
 template <class L, class S, class C, int TX, int TY, int TZ, int MODE>
 __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
                                           const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid,
                                           unsigned* err, double* __restrict__ rho_out, double* __restrict__ u_out,
-                                          TileSmem<L, C, TX, TY, TZ>& sm) {
-    using T = TileSmem<L, C, TX, TY, TZ>;
+                                          TileSmem<L, C, TX, TY, TZ, MODE == 2>& sm, const AdjIO<C>* adj = nullptr) {
+    using T = TileSmem<L, C, TX, TY, TZ, MODE == 2>;
     constexpr int D = L::D, Q = L::Q;
     constexpr int NT = TX * TY * TZ;
     constexpr int RX = T::RX, RY = T::RY, RZ = T::RZ, PX = T::PX, PY = T::PY, PZ = T::PZ;
@@ -221,12 +135,12 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                 f[a] = C(fin[a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
             }
         } else {
+            // next to a solid: one load per direction, the bounce-back source chosen by address
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-                const int up = ti - ex - ey * YX - ez * YX * YY;
-                if (sm.type[up] & T_SOLID) f[a] = C(fin[L::opp(a) * N + gi]);
-                else f[a] = C(fin[a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
+                const bool bb = (sm.type[ti - ex - ey * YX - ez * YX * YY] & T_SOLID) != 0;
+                f[a] = C(fin[bb ? L::opp(a) * N + gi : a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
             }
         }
     };
@@ -335,11 +249,20 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                     kap = C(g.kappa);
                 }
                 // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
-                rw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
-                rw = rw > ph.rho_l ? ph.rho_l : rw;
+                const C raw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
+                rw = raw > ph.rho_l ? ph.rho_l : raw;
                 rw = rw < ph.rho_g ? ph.rho_g : rw;
+                if constexpr (MODE == 2) {
+                    const bool free = raw < ph.rho_l && raw > ph.rho_g;   // limiter inactive
+                    sm.wdk[i] = free ? (kap >= C(0) ? rho_ave : C(1)) : C(0);
+                    sm.wda[i] = free ? (kap >= C(0) ? C(1) + kap : C(1)) / den : C(0);
+                }
+            }
+            if constexpr (MODE == 2) {
+                if (ph.wall_kind == 1) sm.wdk[i] = sm.wda[i] = C(0);
             }
             sm.psi[i] = psi_checked(rw, ph, err);
+            if constexpr (MODE == 2) sm.wdpsi[i] = psi_slope(rw, sm.psi[i], ph);
         }
         __syncthreads();
     }
@@ -347,15 +270,25 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     // 3. force, velocity and collision of the tile's fluid node
     const bool valid = (x0 + lx < nx) && (y0 + ly < ny) && (D == 2 || z0 + lz < nz);
     if (!valid) return;
+    const int pc = pix(lx + 1, ly + 1, lz + PZH);
     if (!my_fluid) {
         if (MODE == 1) {
             if (rho_out) rho_out[gi] = 0.0;
             if (u_out)
                 for (int c = 0; c < D; ++c) u_out[c * N + gi] = 0.0;
         }
+        if constexpr (MODE == 2) {
+            const bool wall = (my_type & T_WALL) != 0;
+            adj->psi[gi] = wall ? sm.psi[pc] : C(0);
+            adj->dpsi[gi] = wall ? sm.wdpsi[pc] : C(0);
+            adj->drw_k[gi] = wall ? sm.wdk[pc] : C(0);
+            adj->drw_a[gi] = wall ? sm.wda[pc] : C(0);
+            adj->fmb_x[gi] = C(0);
+            adj->fmb_y[gi] = C(0);
+            adj->psib[gi] = C(0);
+        }
         return;
     }
-    const int pc = pix(lx + 1, ly + 1, lz + PZH);
     const C psi_c = sm.psi[pc];
     // sum_a w_a psi(x + e_a) e_a, taken over opposite pairs: w_a e_a (psi(x + e_a) - psi(x - e_a))
     // (nearly equal values cancel exactly in the difference, which keeps FP32 accurate in bulk)
@@ -395,6 +328,26 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         }
         return;
     }
+    if constexpr (MODE == 2) {
+        if constexpr (D == 2) {
+            C m[Q], fb[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) m[a] = adj->mu[a * N + gi];
+            C bx, by, pb;
+            collide_d2q9_adjoint<C>(f, m, rho, ux, uy, Fx, Fy, Fmx, Fmy, psi_c, ph.r, fb, bx, by, pb);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) adj->lam[a * N + gi] = fb[a];
+            adj->fmb_x[gi] = bx;
+            adj->fmb_y[gi] = by;
+            // F_m = -G psi(x) sum w psi(x+e) e: its dependence on psi(x) is F_m / psi(x)
+            adj->psib[gi] = pb + (bx * Fmx + by * Fmy) / psi_c;
+            adj->psi[gi] = psi_c;
+            adj->dpsi[gi] = psi_slope(rho, psi_c, ph);
+            adj->drw_k[gi] = C(0);
+            adj->drw_a[gi] = C(0);
+        }
+        return;
+    }
     const C X = cdiv(Fmx * Fmx + Fmy * Fmy + Fmz * Fmz, psi_c * psi_c);
     if constexpr (D == 2) {
         collide_d2q9<C>(f, drho, rho, ux, uy, Fx, Fy, X, ph.r);
@@ -410,23 +363,14 @@ template <class L, class S>
 struct TileShape;
 #ifndef LBMWET_T2F_X   // tile of the FP32 D2Q9 kernels (compile-time; chosen by measurement)
 #define LBMWET_T2F_X 32
-#define LBMWET_T2F_Y 16
-#define LBMWET_T2F_MINB 2
-#endif
-#ifndef LBMWET_T3F_X   // tile of the FP32 D3Q19 kernels
-#define LBMWET_T3F_X 32
-#define LBMWET_T3F_Y 4
-#define LBMWET_T3F_Z 4
-#define LBMWET_T3F_MINB 1
+#define LBMWET_T2F_Y 8
+#define LBMWET_T2F_MINB 4
 #endif
 template <> struct TileShape<D2Q9, float> {
     static constexpr int X = LBMWET_T2F_X, Y = LBMWET_T2F_Y, Z = 1, MINB = LBMWET_T2F_MINB;
 };
 template <> struct TileShape<D2Q9, double> { static constexpr int X = 32, Y = 8, Z = 1, MINB = 2; };
-template <> struct TileShape<D3Q19, float> {
-    static constexpr int X = LBMWET_T3F_X, Y = LBMWET_T3F_Y, Z = LBMWET_T3F_Z, MINB = LBMWET_T3F_MINB;
-};
-template <> struct TileShape<D3Q19, double> { static constexpr int X = 32, Y = 4, Z = 2, MINB = 1; };
+
 
 template <class L, class S, class C, int MODE>
 __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileShape<L, S>::Z, TileShape<L, S>::MINB)
@@ -438,6 +382,19 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
     tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
                                                   blockIdx.z * TS::Z, solid, err, rho_out, u_out, sm);
+}
+
+// Adjoint local part (D2Q9): the forward tile machinery recomputes rho, psi and rho_w of the state
+// pulled from f*_k, then each node writes the reverse of its collision and its psi data.
+template <class S>
+__global__ void __launch_bounds__(TileShape<D2Q9, S>::X* TileShape<D2Q9, S>::Y, TileShape<D2Q9, S>::MINB)
+    adjoint_local_tile(const S* __restrict__ fin, Geo g, Phys<S> ph, unsigned* err, AdjIO<S> io) {
+    using TS = TileShape<D2Q9, S>;
+    __shared__ TileSmem<D2Q9, S, TS::X, TS::Y, 1, true> sm;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
+    tile_body<D2Q9, S, S, TS::X, TS::Y, 1, 2>(fin, nullptr, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y, 0, solid,
+                                               err, nullptr, nullptr, sm, &io);
 }
 
 // Batched step: CTAs walk the work list; each item is one tile of one instance.
@@ -631,8 +588,7 @@ static cudaError_t dispatch(int lat, int prec, const void* fin, void* fout, cons
         if (prec == PREC_FP64) return launch_tile<D2Q9, double, MODE>(fin, fout, p, rho, u, s);
         return launch_tile<D2Q9, float, MODE>(fin, fout, p, rho, u, s);
     }
-    if (prec == PREC_FP64) return launch_tile<D3Q19, double, MODE>(fin, fout, p, rho, u, s);
-    return launch_tile<D3Q19, float, MODE>(fin, fout, p, rho, u, s);
+    return launch_step3d(prec, MODE, fin, fout, geo_of(p), p, rho, u, s);
 }
 
 cudaError_t launch_step(int lat, int prec, const void* fin, void* fout, const DevParams& p, cudaStream_t s) {
@@ -659,8 +615,31 @@ cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& 
         if (prec == PREC_FP64) return batched_l<D2Q9, double>(parity, p, insts, items, n_items, ctas, s);
         return batched_l<D2Q9, float>(parity, p, insts, items, n_items, ctas, s);
     }
-    if (prec == PREC_FP64) return batched_l<D3Q19, double>(parity, p, insts, items, n_items, ctas, s);
-    return batched_l<D3Q19, float>(parity, p, insts, items, n_items, ctas, s);
+    return cudaErrorInvalidValue;   // batches are D2Q9
+}
+
+template <class S>
+static cudaError_t adj_local_t(const void* fstar, const DevParams& p, const AdjointFields& w, cudaStream_t s) {
+    using TS = TileShape<D2Q9, S>;
+    AdjIO<S> io;
+    io.mu = static_cast<const S*>(w.mu);
+    io.lam = static_cast<S*>(w.lam);
+    io.fmb_x = static_cast<S*>(w.fmb_x);
+    io.fmb_y = static_cast<S*>(w.fmb_y);
+    io.psib = static_cast<S*>(w.psib);
+    io.psi = static_cast<S*>(w.psi);
+    io.dpsi = static_cast<S*>(w.dpsi);
+    io.drw_k = static_cast<S*>(w.drw_k);
+    io.drw_a = static_cast<S*>(w.drw_a);
+    dim3 grid((p.nx + TS::X - 1) / TS::X, (p.ny + TS::Y - 1) / TS::Y, 1);
+    adjoint_local_tile<S><<<grid, dim3(TS::X, TS::Y, 1), 0, s>>>(static_cast<const S*>(fstar), geo_of(p),
+                                                                  make_phys<S>(p), p.err, io);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_local(int prec, const void* fstar, const DevParams& p, const AdjointFields& w,
+                                 cudaStream_t s) {
+    return prec == PREC_FP64 ? adj_local_t<double>(fstar, p, w, s) : adj_local_t<float>(fstar, p, w, s);
 }
 
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz) {
@@ -668,8 +647,7 @@ void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz) {
         if (prec == PREC_FP64) { *tx = TileShape<D2Q9, double>::X; *ty = TileShape<D2Q9, double>::Y; *tz = 1; }
         else { *tx = TileShape<D2Q9, float>::X; *ty = TileShape<D2Q9, float>::Y; *tz = 1; }
     } else {
-        if (prec == PREC_FP64) { *tx = TileShape<D3Q19, double>::X; *ty = TileShape<D3Q19, double>::Y; *tz = TileShape<D3Q19, double>::Z; }
-        else { *tx = TileShape<D3Q19, float>::X; *ty = TileShape<D3Q19, float>::Y; *tz = TileShape<D3Q19, float>::Z; }
+        zmarch_tile_shape(prec, tx, ty, tz);
     }
 }
 
@@ -684,8 +662,8 @@ static int occ() {
 }
 
 int batched_ctas_per_sm(int lat, int prec) {
-    if (lat == LAT_D2Q9) return prec == PREC_FP64 ? occ<D2Q9, double>() : occ<D2Q9, float>();
-    return prec == PREC_FP64 ? occ<D3Q19, double>() : occ<D3Q19, float>();
+    (void)lat;
+    return prec == PREC_FP64 ? occ<D2Q9, double>() : occ<D2Q9, float>();
 }
 
 static unsigned grid_for(long long n) {

@@ -1,0 +1,135 @@
+// Device helpers shared by the step kernels: physics constants in compute precision, grid
+// geometry, the equation of state and pseudopotential (Eq. 6 with Eq. 18 or Carnahan-Starling),
+// periodic wrapping and the enumeration of halo shells.
+#pragma once
+
+#include "kernels.h"
+#include "lattice.cuh"
+
+namespace lbmwet {
+
+// physics constants in compute precision
+template <class C>
+struct Phys {
+    int eos_kind, wall_kind;
+    C RT, a, b, b4, aphi, two_over_G, G;
+    C rho_l, rho_g, rho_ref, fx, fy, fz, rho_w_const;
+    Rates<C> r;
+};
+
+template <class C>
+Phys<C> make_phys(const DevParams& p) {
+    Phys<C> h;
+    h.eos_kind = p.eos_kind;
+    h.wall_kind = p.wall_kind;
+    h.RT = C(p.RT);
+    h.a = C(p.a);
+    h.b = C(p.b);
+    h.b4 = C(0.25 * p.b);
+    h.aphi = C(p.aphi);
+    h.two_over_G = C(p.two_over_G);
+    h.G = C(p.G);
+    h.rho_l = C(p.rho_l);
+    h.rho_g = C(p.rho_g);
+    h.rho_ref = C(p.rho_ref);
+    h.fx = C(p.fx);
+    h.fy = C(p.fy);
+    h.fz = C(p.fz);
+    h.rho_w_const = C(p.rho_w_const);
+    h.r.s_e = C(p.s_e);
+    h.r.s_eps = C(p.s_eps);
+    h.r.s_q = C(p.s_q);
+    h.r.s_nu = C(p.s_nu);
+    h.r.s_pi = C(p.s_pi);
+    h.r.s_m = C(p.s_m);
+    h.r.c_e = C(p.c_e);
+    h.r.c_eps = C(p.c_eps);
+    return h;
+}
+
+// geometry of one grid
+struct Geo {
+    int nx, ny, nz, N;
+    const uint8_t* type;
+    const uint8_t* tile_solid;   // per tile (single-grid kernel) or null
+    const int* wall_id;
+    const double* kappa_w;   // per wall node or null
+    double kappa;
+};
+
+// Division in compute precision: FP64 keeps IEEE division (parity with the FP64 oracle); the FP32
+// path uses the fast hardware approximation (relative error of a few ulp, below the rounding of the
+// FP32 state).
+__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+
+template <class C>
+__device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
+    C p;
+    if (e.eos_kind == 1) {  // Carnahan-Starling
+        const C eta = e.b4 * rho;
+        const C om = C(1) - eta;
+        p = cdiv(rho * e.RT * (C(1) + eta + eta * eta - eta * eta * eta), om * om * om) - e.a * rho * rho;
+    } else {                // Peng-Robinson, Eq. 18
+        p = cdiv(rho * e.RT, C(1) - e.b * rho) - cdiv(e.aphi * rho * rho, C(1) + C(2) * e.b * rho - e.b * e.b * rho * rho);
+    }
+    return e.two_over_G * (p - rho * C(1.0 / 3.0));   // Eq. 6 argument: 2 (p - rho c_s^2) / (G c^2)
+}
+
+template <class C>
+__device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err) {
+    const C arg = psi_arg(rho, e);
+    if (!(arg > C(0))) {
+        atomicOr(err, ERR_PSI);
+        return C(0);
+    }
+    return sqrt(arg);
+}
+
+// The k-th cell of the one-cell-thick shell of an AX x AY (x AZ) box, enumerated so that
+// consecutive k are neighbouring cells (warps stay coherent).
+template <int AX, int AY, int AZ, int D>
+struct Shell {
+    static constexpr int COUNT = D == 2 ? 2 * AX + 2 * (AY - 2) : 2 * AX * AY + (AZ - 2) * (2 * AX + 2 * (AY - 2));
+    __device__ static __forceinline__ void cell(int k, int& x, int& y, int& z) {
+        if (D == 2) {
+            z = 0;
+            if (k < 2 * AX) {
+                y = k < AX ? 0 : AY - 1;
+                x = k < AX ? k : k - AX;
+            } else {
+                const int j = k - 2 * AX;
+                y = 1 + (j >> 1);
+                x = (j & 1) ? AX - 1 : 0;
+            }
+        } else {
+            constexpr int plane = AX * AY, per = 2 * AX + 2 * (AY - 2);
+            if (k < 2 * plane) {
+                z = k < plane ? 0 : AZ - 1;
+                const int r = k < plane ? k : k - plane;
+                x = r % AX;
+                y = r / AX;
+            } else {
+                const int j = k - 2 * plane;
+                z = 1 + j / per;
+                const int r = j % per;
+                if (r < 2 * AX) {
+                    y = r < AX ? 0 : AY - 1;
+                    x = r < AX ? r : r - AX;
+                } else {
+                    const int t = r - 2 * AX;
+                    y = 1 + (t >> 1);
+                    x = (t & 1) ? AX - 1 : 0;
+                }
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ int wrap_full(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+}  // namespace lbmwet
