@@ -286,6 +286,47 @@ def adjoint_ratio(L, torch, stream, steps=2000, ckpt=100):
                     "the checkpointed forward pass", "grad_norm": float(np.linalg.norm(g))}
 
 
+def device_rate(L, torch, stream, name, steps, flush):
+    """Device-timed MLUPS and HBM-roofline fraction of another workload (same protocol as the
+    headline: L2 flushed before each timed step, CUDA events around each step)."""
+    wls, precision, label = workload(name)
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    e.T = wls[0].t_over_tc * L.lbm_critical_temperature(e)
+    rho_g, rho_l = L.lbm_coexistence(e)
+    if name == "c4":
+        for wl in wls:
+            if wl.kappa < 0:
+                wl.kappa *= (rho_l - rho_g)
+    cfgs = [make_cfg(L, wl, precision, rho_g, rho_l) for wl in wls]
+    run = Runner(L, cfgs, [wl.mask() for wl in wls], [wl.rho0(rho_l, rho_g) for wl in wls], stream)
+    nodes = sum(wl.nodes for wl in wls)
+    with torch.cuda.stream(stream):
+        run.enqueue(3)
+    run.step(0)
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(2e6 + 4e5 * steps))
+        for k in range(steps):
+            flush.zero_()
+            st[k].record(stream)
+            run.enqueue(1)
+            en[k].record(stream)
+    torch.cuda.synchronize()
+    run.step(0)
+    run.close()
+    ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / steps
+    peak = 6800.0
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        with open(pk_path) as fh:
+            peak = json.load(fh).get("hbm_gbs", peak)
+    gbs = bytes_per_lu(wls[0].lattice, precision) * nodes / (ms * 1e-3) / 1e9
+    return {"workload": label, "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 5),
+            "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT, "achieved_gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 4)}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -412,6 +453,9 @@ def run_ours(args):
     adjoint = None
     if not args.no_extras and args.workload in ("c2", "c5"):
         adjoint = adjoint_ratio(L, torch, stream, steps=args.adjoint_steps)
+    others = None
+    if not args.no_extras and args.workload == "c2":
+        others = {w: device_rate(L, torch, stream, w, steps, flush) for w, steps in (("c3", 10), ("c4", 20))}
 
     # end to end through the public API with host buffers: init from host arrays, K calls of the
     # stepping entry point with one step each (each reads back the 4-byte device status), then the
@@ -453,6 +497,8 @@ def run_ours(args):
         line["batched_vs_separate"] = batched_vs_separate
     if adjoint:
         line["adjoint_vs_forward"] = adjoint
+    if others:
+        line["other_workloads"] = others
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args.workload)

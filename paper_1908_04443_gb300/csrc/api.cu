@@ -917,7 +917,21 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             for (int y = 0; y < d.ny; y += ty)
                 for (int x = 0; x < d.nx; x += tx) {
                     const size_t t = ((size_t)(z / tz) * h->tiles[1] + y / ty) * h->tiles[0] + x / tx;
-                    items.push_back(BatchItem{i, x, y, z, int(h->tile_solid[t])});
+                    BatchItem it{};
+                    it.nx = d.nx;
+                    it.ny = d.ny;
+                    it.N = d.N;
+                    it.x0 = x;
+                    it.y0 = y;
+                    it.solid = int(h->tile_solid[t]);
+                    it.inst = i;
+                    it.f[0] = h->f[0];
+                    it.f[1] = h->f[1];
+                    it.type = h->d_type;
+                    it.wall_id = h->d_wall_id;
+                    it.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
+                    it.kappa = h->dp.kappa;
+                    items.push_back(it);
                 }
     }
     b->n_items = int(items.size());

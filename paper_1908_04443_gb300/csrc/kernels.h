@@ -37,11 +37,18 @@ struct BatchInstance {
     const double* kappa_w;     // per wall node or null (scalar kappa)
     double kappa;
 };
-// One work item of the batched step: a tile of an instance.
+// One work item of the batched step: a tile of an instance, with everything the tile needs
+// (one contiguous record, so that a CTA fetches the next item with one load per lane).
 struct BatchItem {
-    int inst, x0, y0, z0;
-    int solid;   // a solid node lies within the tile + 3-node halo
+    int nx, ny, N, x0, y0, solid;   // solid: a solid node lies within the tile's box + 3-node halo
+    int inst, pad;
+    const void* f[2];
+    const uint8_t* type;
+    const int* wall_id;
+    const double* kappa_w;
+    double kappa;
 };
+static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem is copied as 32-bit words");
 
 enum Lat { LAT_D2Q9 = 0, LAT_D3Q19 = 1 };
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1 };

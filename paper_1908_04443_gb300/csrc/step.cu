@@ -75,13 +75,16 @@ __device__ __forceinline__ C psi_slope(C rho, C psi, const Phys<C>& e) {
 
 // One tile: x0, y0, z0 is its first node.  All threads of the CTA call this together.
 // MODE 0: time step (writes f*); 1: fields (writes rho, u); 2: adjoint local part (writes AdjIO).
-template <class L, class S, class C, int TX, int TY, int TZ, int MODE>
+// SOLID = false compiles the body of a tile with no solid node within its box (every cell a bulk
+// fluid node: no node-type staging, no bounce-back, no wall nodes).
+template <class L, class S, class C, int TX, int TY, int TZ, int MODE, bool SOLID = true>
 __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
-                                          const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid,
+                                          const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid_arg,
                                           unsigned* err, double* __restrict__ rho_out, double* __restrict__ u_out,
                                           TileSmem<L, C, TX, TY, TZ, MODE == 2>& sm, const AdjIO<C>* adj = nullptr) {
     using T = TileSmem<L, C, TX, TY, TZ, MODE == 2>;
     constexpr int D = L::D, Q = L::Q;
+    const bool tile_solid = SOLID && tile_solid_arg;
     constexpr int NT = TX * TY * TZ;
     constexpr int RX = T::RX, RY = T::RY, RZ = T::RZ, PX = T::PX, PY = T::PY, PZ = T::PZ;
     constexpr int YX = T::YX, YY = T::YY, YZ = T::YZ, HZ = T::HZ, PZH = T::PZH, YZH = T::YZH;
@@ -99,18 +102,24 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     // 0. node types of the tile + 3-node halo (skipped when no solid node lies within it: then
     //    every cell is a bulk fluid node); does the 1-node halo region hold a wall node?
     if (tid == 0) sm.nwall = 0;
-    int wall_seen = 0;
-    for (int i = tid; tile_solid && i < YX * YY * YZ; i += NT) {
-        const int lx = i % YX, t = i / YX, ly = t % YY, lz = t / YY;
-        const int gx = wx(x0 + lx - 3), gy = wy(y0 + ly - 3), gz = wz(z0 + lz - YZH);
-        const uint8_t ty = g.type[(gz * ny + gy) * nx + gx];
-        sm.type[i] = ty;
-        const bool in_p = lx >= 2 && lx < TX + 4 && ly >= 2 && ly < TY + 4 &&
-                          (D == 2 || (lz >= YZH - PZH && lz < TZ + YZH + PZH));
-        if (in_p && (ty & T_WALL)) wall_seen = 1;
+    bool tile_has_wall = false;
+    if constexpr (SOLID) {
+        int wall_seen = 0;
+        for (int i = tid; tile_solid && i < YX * YY * YZ; i += NT) {
+            const int lx = i % YX, t = i / YX, ly = t % YY, lz = t / YY;
+            const int gx = wx(x0 + lx - 3), gy = wy(y0 + ly - 3), gz = wz(z0 + lz - YZH);
+            const uint8_t ty = g.type[(gz * ny + gy) * nx + gx];
+            sm.type[i] = ty;
+            const bool in_p = lx >= 2 && lx < TX + 4 && ly >= 2 && ly < TY + 4 &&
+                              (D == 2 || (lz >= YZH - PZH && lz < TZ + YZH + PZH));
+            if (in_p && (ty & T_WALL)) wall_seen = 1;
+        }
+        tile_has_wall = __syncthreads_or(wall_seen);
     }
-    const bool tile_has_wall = __syncthreads_or(wall_seen);
-    auto type_at = [&](int ti) -> uint8_t { return tile_solid ? sm.type[ti] : uint8_t(T_BULK); };
+    auto type_at = [&](int ti) -> uint8_t {
+        if constexpr (!SOLID) return uint8_t(T_BULK);
+        return tile_solid ? sm.type[ti] : uint8_t(T_BULK);
+    };
 
     // pull of one node at global (gx, gy, gz) whose type-tile cell is ti
     auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int ti, uint8_t self) {
@@ -128,7 +137,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
             pz[0] = pz[1] = pz[2] = 0;
         }
         const int gi = pz[1] + ry[1] + cx[1];
-        if (self & T_BULK) {
+        if (!SOLID || (self & T_BULK)) {
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
@@ -196,7 +205,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         sm.psi[i] = psi;
     }
     // 1c. the 2-node halo ring, only where Eq. 17 will need it
-    if (tile_has_wall) {
+    if (SOLID && tile_has_wall) {
         using ShellR = Shell<RX, RY, RZ, D>;
         for (int k = tid; k < ShellR::COUNT; k += NT) {
             int rx, ry, rz;
@@ -219,8 +228,8 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     __syncthreads();
 
     // 2. wall nodes of the tile + 1-node halo: virtual density and its psi
-    const int nwall = sm.nwall;
-    if (nwall > 0) {
+    const int nwall = SOLID ? sm.nwall : 0;
+    if (SOLID && nwall > 0) {
         for (int k = tid; k < nwall; k += NT) {
             const int i = sm.wall[k];
             const int px = i % PX, t = i / PX, py = t % PY, pz = t / PY;
@@ -380,8 +389,12 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
     __shared__ TileSmem<L, C, TS::X, TS::Y, TS::Z> sm;
     const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
-    tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
-                                                  blockIdx.z * TS::Z, solid, err, rho_out, u_out, sm);
+    if (solid)
+        tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE, true>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                            blockIdx.z * TS::Z, true, err, rho_out, u_out, sm);
+    else
+        tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE, false>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                             blockIdx.z * TS::Z, false, err, rho_out, u_out, sm);
 }
 
 // Adjoint local part (D2Q9): the forward tile machinery recomputes rho, psi and rho_w of the state
@@ -397,31 +410,50 @@ __global__ void __launch_bounds__(TileShape<D2Q9, S>::X* TileShape<D2Q9, S>::Y, 
                                                err, nullptr, nullptr, sm, &io);
 }
 
-// Batched step: CTAs walk the work list; each item is one tile of one instance.
+// Batched step: CTAs walk the work list; each item is one tile of one instance.  The next item's
+// record is fetched into registers by the first lanes while the current tile runs and handed over
+// through shared memory at the end of the iteration.
 template <class L, class S, class C>
 __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileShape<L, S>::Z, TileShape<L, S>::MINB)
     fused_step_batched(int parity, const BatchInstance* __restrict__ insts, const BatchItem* __restrict__ items,
                        int n_items, Phys<C> ph, unsigned* err) {
+    (void)insts;
     using TS = TileShape<L, S>;
+    constexpr int WORDS = int(sizeof(BatchItem) / 4);
     __shared__ TileSmem<L, C, TS::X, TS::Y, TS::Z> sm;
+    __shared__ BatchItem s_item[2];
+    const int tid = threadIdx.x + TS::X * (threadIdx.y + TS::Y * threadIdx.z);
+    if (tid < WORDS && blockIdx.x < n_items)
+        reinterpret_cast<uint32_t*>(&s_item[0])[tid] = reinterpret_cast<const uint32_t*>(&items[blockIdx.x])[tid];
+    __syncthreads();
+    int slot = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const BatchItem item = items[it];
-        const BatchInstance& in = insts[item.inst];
+        const BatchItem& item = s_item[slot];
+        const int next = it + gridDim.x;
+        uint32_t w = 0;
+        const bool fetch = tid < WORDS && next < n_items;
+        if (fetch) w = reinterpret_cast<const uint32_t*>(&items[next])[tid];
         Geo g;
-        g.nx = in.nx;
-        g.ny = in.ny;
-        g.nz = in.nz;
-        g.N = in.N;
-        g.type = in.type;
+        g.nx = item.nx;
+        g.ny = item.ny;
+        g.nz = 1;
+        g.N = item.N;
+        g.type = item.type;
         g.tile_solid = nullptr;
-        g.wall_id = in.wall_id;
-        g.kappa_w = in.kappa_w;
-        g.kappa = in.kappa;
-        const S* fin = static_cast<const S*>(in.f[parity]);
-        S* fout = static_cast<S*>(in.f[parity ^ 1]);
-        __syncthreads();   // the previous item's threads are done with shared memory
-        tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0>(fin, fout, g, ph, item.x0, item.y0, item.z0, item.solid != 0, err,
-                                                   nullptr, nullptr, sm);
+        g.wall_id = item.wall_id;
+        g.kappa_w = item.kappa_w;
+        g.kappa = item.kappa;
+        const S* fin = static_cast<const S*>(item.f[parity]);
+        S* fout = static_cast<S*>(const_cast<void*>(item.f[parity ^ 1]));
+        if (item.solid)
+            tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0, true>(fin, fout, g, ph, item.x0, item.y0, 0, true, err,
+                                                             nullptr, nullptr, sm);
+        else
+            tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0, false>(fin, fout, g, ph, item.x0, item.y0, 0, false, err,
+                                                              nullptr, nullptr, sm);
+        if (fetch) reinterpret_cast<uint32_t*>(&s_item[slot ^ 1])[tid] = w;
+        __syncthreads();   // the next record is visible, and this tile's threads are done with shared memory
+        slot ^= 1;
     }
 }
 
