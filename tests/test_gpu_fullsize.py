@@ -1,0 +1,126 @@
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py times.
+
+* The 600 x 400 cylinder workload over its 24-point wall-parameter sweep, stepped as one batch (FP32
+  deviation storage): one batched step from an evolved state, compared with one FP64 oracle step on
+  every node of three instances.
+* The 96-instance batch of 128^2..512^2 grids: the same on four instances.
+* The 256^3 sphere workload (D3Q19 z-march, FP32): one step compared at sampled nodes.  The oracle
+  steps a 15^3 window around each sampled node taken from the GPU state: one step's output at a node
+  depends on the state within 3 nodes (pull, psi of neighbours, virtual densities of neighbouring
+  wall nodes), so the window's centre is exact although its edges wrap.
+* The 600 x 400 workload run for its configured 20000 steps in FP32 deviation storage and in FP64:
+  the contact angle within 0.5 degrees and the density within 1e-4 of the liquid density.
+
+FP32 single-step tolerances: the stored deviations carry float rounding (relative 6e-8 of the
+distributions) through one collision; 2e-6 of the largest distribution bounds it with margin.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import eos as E, lbm
+
+pytestmark = pytest.mark.gpu
+
+
+def _eos(t_over_tc):
+    e = E.cs_config().at_reduced_temperature(t_over_tc)
+    g, l = E.maxwell(e)
+    return e, g, l
+
+
+def _cfg(L, wl, precision, g, l):
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
+    return L.make_config(wl.lattice, precision, wl.shape, e, sigma=0.12, rho_l=l, rho_g=g, kappa=wl.kappa,
+                         rho_ref=g, body=("ball", wl.body_center, wl.body_radius), drop_hint=wl.drop_center)
+
+
+def _oracle_params(wl, eos, g, l):
+    return lbm.Params(wl.lattice, eos, sigma=0.12, rho_l=l, rho_g=g, kappa=wl.kappa)
+
+
+def _batch_one_step(wls, check_idx, t_over_tc, warm=40):
+    from paper_1908_04443_gb300 import lbmwet as L
+    eos, g, l = _eos(t_over_tc)
+    cfgs = [_cfg(L, wl, "fp32", g, l) for wl in wls]
+    b = L.lbm_batch_init(cfgs, [wl.mask() for wl in wls], [wl.rho0(l, g) for wl in wls])
+    try:
+        L.lbm_batch_step(b, warm)
+        before = {i: L.lbm_get_state(L.lbm_batch_handle(b, i), 9, wls[i].nodes) for i in check_idx}
+        L.lbm_batch_step(b, 1)
+        for i in check_idx:
+            wl = wls[i]
+            after = L.lbm_get_state(L.lbm_batch_handle(b, i), 9, wl.nodes).reshape((9,) + wl.shape)
+            geo = lbm.Geometry(wl.mask(), "D2Q9")
+            ref = lbm.step(before[i].reshape((9,) + wl.shape), geo, _oracle_params(wl, eos, g, l))
+            scale = np.max(np.abs(ref))
+            assert np.max(np.abs(after - ref)) <= 2e-6 * scale, f"instance {i}"
+    finally:
+        L.lbm_batch_destroy(b)
+
+
+def test_c2_sweep_batch_one_step_full_size():
+    _, g, l = _eos(0.6)
+    wls = [W.c2_cylinder_600x400(kappa=k) for k in W.c2_cylinder_sweep_kappas(l, g)]
+    _batch_one_step(wls, [0, 11, 23], 0.6)
+
+
+def test_c4_batch_one_step_full_size():
+    _, g, l = _eos(0.7)
+    wls = W.c4_batch(96)
+    for wl in wls:
+        if wl.kappa < 0:
+            wl.kappa *= (l - g)
+    _batch_one_step(wls, [0, 17, 58, 95], 0.7, warm=20)
+
+
+def test_c3_sphere_one_step_sampled():
+    from paper_1908_04443_gb300 import lbmwet as L
+    wl = W.c3_sphere_256()
+    eos, g, l = _eos(wl.t_over_tc)
+    mask = wl.mask()
+    with L.Simulation(_cfg(L, wl, "fp32", g, l), mask, wl.rho0(l, g)) as sim:
+        sim.step(3)
+        before = sim.get_state()
+        sim.step(1)
+        after = sim.get_state()
+    geo_full = lbm.Geometry(mask, "D3Q19")
+    rng = np.random.default_rng(3)
+    fluid = np.argwhere(mask == 0)
+    # sampled nodes: random fluid nodes, plus fluid nodes next to the sphere and at grid edges
+    near = np.argwhere((mask == 0) & np.roll(geo_full.wall, 1, axis=0))
+    picks = list(fluid[rng.choice(len(fluid), 40, replace=False)]) + list(near[rng.choice(len(near), 20, replace=False)])
+    picks += [np.array([0, 0, 0]), np.array([255, 255, 255]), np.array([0, 128, 255])]
+    p = _oracle_params(wl, eos, g, l)
+    r = 7
+    for z, y, x in picks:
+        zs = np.arange(z - r, z + r + 1) % 256
+        ys = np.arange(y - r, y + r + 1) % 256
+        xs = np.arange(x - r, x + r + 1) % 256
+        win = np.ix_(zs, ys, xs)
+        m = mask[win]
+        if m[r, r, r]:
+            continue
+        geo = lbm.Geometry(m, "D3Q19")
+        f0 = before[(slice(None),) + win]
+        ref = lbm.step(f0, geo, p)[:, r, r, r]
+        got = after[:, z, y, x]
+        assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref)), (z, y, x)
+
+
+def test_c2_20000_steps_fp32_against_fp64():
+    from paper_1908_04443_gb300 import lbmwet as L
+    eos, g, l = _eos(0.6)
+    wl = W.c2_cylinder_600x400(kappa=0.15)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        with L.Simulation(_cfg(L, wl, prec, g, l), wl.mask(), wl.rho0(l, g)) as sim:
+            sim.step(wl.steps)
+            out[prec] = sim.observables(fields=True)
+    o64, r64, _ = out["fp64"]
+    o32, r32, _ = out["fp32"]
+    fl = wl.mask() == 0
+    assert np.max(np.abs(r32[fl] - r64[fl])) <= 1e-4 * l
+    assert abs(o32.theta_deg - o64.theta_deg) <= 0.5
+    assert abs(o32.mass / o64.mass - 1) <= 1e-4

@@ -139,11 +139,16 @@ def c1_parity_cylinder() -> Workload:
                     (50.0, 95.0), 25.0, "CS", 0.7, 0.2, 1000)
 
 
-def c2_cylinder_sweep_kappas(rho_l: float, rho_g: float) -> list:
-    """Wall-parameter sweep of the 600x400 cylinder workload: phi in {1.5,1.3,1.15,1.0} (hydrophilic)
-    and drho in {0.05,0.1,0.2}*(rho_l-rho_g) (hydrophobic), in the unified kappa form."""
+def c2_cylinder_sweep_kappas(rho_l: float, rho_g: float, points: int = 24) -> list:
+    """Wall-parameter sweep of the 600x400 cylinder workload from hydrophilic to hydrophobic, in the
+    unified kappa form: half of the points have phi evenly spaced from 1.5 down to 1.0 (kappa =
+    phi - 1, Eq. 16's first branch, theta below about 90 degrees), the other half drho evenly
+    spaced up to 0.25 (rho_l - rho_g) (kappa = -drho, the second branch, theta above it)."""
     d = rho_l - rho_g
-    return [0.5, 0.3, 0.15, 0.0, -0.05 * d, -0.1 * d, -0.2 * d]
+    h = points // 2
+    phi = [0.5 - 0.5 * i / (h - 1) for i in range(h)]                       # kappa = phi - 1
+    drho = [0.25 * d * (i + 1) / (points - h) for i in range(points - h)]   # kappa = -drho
+    return phi + [-x for x in drho]
 
 
 def c2_cylinder_600x400(kappa: float = 0.15) -> Workload:
