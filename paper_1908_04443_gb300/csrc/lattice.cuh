@@ -101,8 +101,6 @@ __host__ __device__ __forceinline__ void collide_d2q9(C (&f)[9], C drho, C rho, 
                                              const Rates<C>& r) {
     const C s14 = f[1] + f[2] + f[3] + f[4];
     const C s58 = f[5] + f[6] + f[7] + f[8];
-    const C jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    const C jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     const C m1 = -C(4) * f[0] - s14 + C(2) * s58;
     const C m2 = C(4) * f[0] - C(2) * s14 + s58;
     const C m4 = -C(2) * f[1] + C(2) * f[3] + f[5] - f[6] - f[7] + f[8];
@@ -111,37 +109,38 @@ __host__ __device__ __forceinline__ void collide_d2q9(C (&f)[9], C drho, C rho, 
     const C m8 = f[5] - f[6] + f[7] - f[8];
     const C u2 = ux * ux + uy * uy;
     const C uF = ux * Fx + uy * Fy;
-    // equilibria in deviation form: e^eq = -2 rho + 3 rho u^2, eps^eq = rho - 3 rho u^2
+    // increments m* - m; equilibria in deviation form: e^eq = -2 rho + 3 rho u^2, eps^eq = rho - 3 rho u^2
     const C e_eq = -C(2) * drho + C(3) * rho * u2;
     const C eps_eq = drho - C(3) * rho * u2;
-    const C m1s = m1 - r.s_e * (m1 - e_eq) + (C(1) - C(0.5) * r.s_e) * (C(6) * uF + r.c_e * X);
-    const C m2s = m2 - r.s_eps * (m2 - eps_eq) + (C(1) - C(0.5) * r.s_eps) * (-C(6) * uF - r.c_eps * X);
-    const C m4s = m4 - r.s_q * (m4 + rho * ux) - (C(1) - C(0.5) * r.s_q) * Fx;
-    const C m6s = m6 - r.s_q * (m6 + rho * uy) - (C(1) - C(0.5) * r.s_q) * Fy;
-    const C m7s = m7 - r.s_nu * (m7 - rho * (ux * ux - uy * uy)) + (C(1) - C(0.5) * r.s_nu) * C(2) * (ux * Fx - uy * Fy);
-    const C m8s = m8 - r.s_nu * (m8 - rho * ux * uy) + (C(1) - C(0.5) * r.s_nu) * (ux * Fy + uy * Fx);
-    // conserved: rho unchanged, j* = j + F (independent of s_rho and s_j)
-    const C a0 = drho * C(1.0 / 9);
-    const C a1 = m1s * C(1.0 / 36);
-    const C a2 = m2s * C(1.0 / 36);
-    const C a3 = (jx + Fx) * C(1.0 / 6);
-    const C a4 = m4s * C(1.0 / 12);
-    const C a5 = (jy + Fy) * C(1.0 / 6);
-    const C a6 = m6s * C(1.0 / 12);
-    const C a7 = m7s * C(0.25);
-    const C a8 = m8s * C(0.25);
-    // f = M^T diag(1/|row|^2) m*
-    const C b = a0 - a1 - C(2) * a2;
-    const C c = a0 + C(2) * a1 + a2;
-    f[0] = a0 - C(4) * a1 + C(4) * a2;
-    f[1] = b + a3 - C(2) * a4 + a7;
-    f[2] = b + a5 - C(2) * a6 - a7;
-    f[3] = b - a3 + C(2) * a4 + a7;
-    f[4] = b - a5 + C(2) * a6 - a7;
-    f[5] = c + a3 + a4 + a5 + a6 + a8;
-    f[6] = c - a3 - a4 + a5 + a6 - a8;
-    f[7] = c - a3 - a4 - a5 - a6 + a8;
-    f[8] = c + a3 + a4 - a5 - a6 - a8;
+    const C d1 = -r.s_e * (m1 - e_eq) + (C(1) - C(0.5) * r.s_e) * (C(6) * uF + r.c_e * X);
+    const C d2 = -r.s_eps * (m2 - eps_eq) + (C(1) - C(0.5) * r.s_eps) * (-C(6) * uF - r.c_eps * X);
+    const C d4 = -r.s_q * (m4 + rho * ux) - (C(1) - C(0.5) * r.s_q) * Fx;
+    const C d6 = -r.s_q * (m6 + rho * uy) - (C(1) - C(0.5) * r.s_q) * Fy;
+    const C d7 = -r.s_nu * (m7 - rho * (ux * ux - uy * uy)) + (C(1) - C(0.5) * r.s_nu) * C(2) * (ux * Fx - uy * Fy);
+    const C d8 = -r.s_nu * (m8 - rho * ux * uy) + (C(1) - C(0.5) * r.s_nu) * (ux * Fy + uy * Fx);
+    // conserved: the density increment is zero, j* - j = F (independent of s_rho and s_j).  Adding
+    // M^-1 (m* - m) to f, rather than rebuilding f from m*, keeps the mass of the stored deviations
+    // exact up to unbiased rounding: rebuilding scales drho by 9 * round(1/9) every step.
+    const C a1 = d1 * C(1.0 / 36);
+    const C a2 = d2 * C(1.0 / 36);
+    const C a3 = Fx * C(1.0 / 6);
+    const C a4 = d4 * C(1.0 / 12);
+    const C a5 = Fy * C(1.0 / 6);
+    const C a6 = d6 * C(1.0 / 12);
+    const C a7 = d7 * C(0.25);
+    const C a8 = d8 * C(0.25);
+    // f += M^T diag(1/|row|^2) (m* - m)
+    const C b = -a1 - C(2) * a2;
+    const C c = C(2) * a1 + a2;
+    f[0] += C(4) * (a2 - a1);
+    f[1] += b + a3 - C(2) * a4 + a7;
+    f[2] += b + a5 - C(2) * a6 - a7;
+    f[3] += b - a3 + C(2) * a4 + a7;
+    f[4] += b - a5 + C(2) * a6 - a7;
+    f[5] += c + a3 + a4 + a5 + a6 + a8;
+    f[6] += c - a3 - a4 + a5 + a6 - a8;
+    f[7] += c - a3 - a4 - a5 - a6 + a8;
+    f[8] += c + a3 + a4 - a5 - a6 - a8;
 }
 
 // MRT collision of one D3Q19 node (d'Humieres basis) in deviation variables.
@@ -157,10 +156,6 @@ __host__ __device__ __forceinline__ void collide_d3q19(C (&f)[19], C drho, C rho
     // sums over the velocity groups
     const C s16 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6];
     const C s718 = f[7] + f[8] + f[9] + f[10] + f[11] + f[12] + f[13] + f[14] + f[15] + f[16] + f[17] + f[18];
-    // momentum
-    const C jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-    const C jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
-    const C jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
     // e = 19|e|^2 - 30:  -30 f0 - 11 (axis) + 8 (edges)
     const C m1 = -C(30) * f[0] - C(11) * s16 + C(8) * s718;
     // eps = (21|e|^4 - 53|e|^2 + 24)/2:  12 f0 - 4 (axis) + 1 (edges)
@@ -192,82 +187,84 @@ __host__ __device__ __forceinline__ void collide_d3q19(C (&f)[19], C drho, C rho
     const C uF = ux * Fx + uy * Fy + uz * Fz;
     const C h_e = C(1) - C(0.5) * r.s_e, h_eps = C(1) - C(0.5) * r.s_eps, h_q = C(1) - C(0.5) * r.s_q;
     const C h_nu = C(1) - C(0.5) * r.s_nu, h_pi = C(1) - C(0.5) * r.s_pi;
-    const C m1s = m1 - r.s_e * (m1 - (-C(11) * drho + C(19) * rho * u2)) + h_e * (C(38) * uF + r.c_e * X);
-    const C m2s = m2 - r.s_eps * (m2 - (C(3) * drho - C(5.5) * rho * u2)) + h_eps * (-C(11) * uF - r.c_eps * X);
+    // increments m* - m of the non-conserved moments
+    const C d1 = -r.s_e * (m1 - (-C(11) * drho + C(19) * rho * u2)) + h_e * (C(38) * uF + r.c_e * X);
+    const C d2 = -r.s_eps * (m2 - (C(3) * drho - C(5.5) * rho * u2)) + h_eps * (-C(11) * uF - r.c_eps * X);
     const C c23 = C(2.0 / 3.0);
-    const C m4s = m4 - r.s_q * (m4 + c23 * rho * ux) - h_q * c23 * Fx;
-    const C m6s = m6 - r.s_q * (m6 + c23 * rho * uy) - h_q * c23 * Fy;
-    const C m8s = m8 - r.s_q * (m8 + c23 * rho * uz) - h_q * c23 * Fz;
+    const C d4 = -r.s_q * (m4 + c23 * rho * ux) - h_q * c23 * Fx;
+    const C d6 = -r.s_q * (m6 + c23 * rho * uy) - h_q * c23 * Fy;
+    const C d8 = -r.s_q * (m8 + c23 * rho * uz) - h_q * c23 * Fz;
     const C p3xx_eq = rho * (C(3) * ux * ux - u2);
     const C S3xx = C(2) * (C(2) * ux * Fx - uy * Fy - uz * Fz);
-    const C m9s = m9 - r.s_nu * (m9 - p3xx_eq) + h_nu * S3xx;
-    const C m10s = m10 - r.s_pi * (m10 + C(0.5) * p3xx_eq) - h_pi * C(0.5) * S3xx;
+    const C d9 = -r.s_nu * (m9 - p3xx_eq) + h_nu * S3xx;
+    const C d10 = -r.s_pi * (m10 + C(0.5) * p3xx_eq) - h_pi * C(0.5) * S3xx;
     const C pww_eq = rho * (uy * uy - uz * uz);
     const C Sww = C(2) * (uy * Fy - uz * Fz);
-    const C m11s = m11 - r.s_nu * (m11 - pww_eq) + h_nu * Sww;
-    const C m12s = m12 - r.s_pi * (m12 + C(0.5) * pww_eq) - h_pi * C(0.5) * Sww;
-    const C m13s = m13 - r.s_nu * (m13 - rho * ux * uy) + h_nu * (ux * Fy + uy * Fx);
-    const C m14s = m14 - r.s_nu * (m14 - rho * uy * uz) + h_nu * (uy * Fz + uz * Fy);
-    const C m15s = m15 - r.s_nu * (m15 - rho * ux * uz) + h_nu * (ux * Fz + uz * Fx);
-    const C m16s = m16 - r.s_m * m16;
-    const C m17s = m17 - r.s_m * m17;
-    const C m18s = m18 - r.s_m * m18;
+    const C d11 = -r.s_nu * (m11 - pww_eq) + h_nu * Sww;
+    const C d12 = -r.s_pi * (m12 + C(0.5) * pww_eq) - h_pi * C(0.5) * Sww;
+    const C d13 = -r.s_nu * (m13 - rho * ux * uy) + h_nu * (ux * Fy + uy * Fx);
+    const C d14 = -r.s_nu * (m14 - rho * uy * uz) + h_nu * (uy * Fz + uz * Fy);
+    const C d15 = -r.s_nu * (m15 - rho * ux * uz) + h_nu * (ux * Fz + uz * Fx);
+    const C d16 = -r.s_m * m16;
+    const C d17 = -r.s_m * m17;
+    const C d18 = -r.s_m * m18;
 
-    // scale by 1/|row|^2: (19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8)
-    const C a0 = drho * C(1.0 / 19);
-    const C a1 = m1s * C(1.0 / 2394);
-    const C a2 = m2s * C(1.0 / 252);
-    const C a3 = (jx + Fx) * C(0.1);
-    const C a4 = m4s * C(1.0 / 40);
-    const C a5 = (jy + Fy) * C(0.1);
-    const C a6 = m6s * C(1.0 / 40);
-    const C a7 = (jz + Fz) * C(0.1);
-    const C a8 = m8s * C(1.0 / 40);
-    const C a9 = m9s * C(1.0 / 36);
-    const C a10 = m10s * C(1.0 / 72);
-    const C a11 = m11s * C(1.0 / 12);
-    const C a12 = m12s * C(1.0 / 24);
-    const C a13 = m13s * C(0.25);
-    const C a14 = m14s * C(0.25);
-    const C a15 = m15s * C(0.25);
-    const C a16 = m16s * C(0.125);
-    const C a17 = m17s * C(0.125);
-    const C a18 = m18s * C(0.125);
+    // scale by 1/|row|^2: (19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8).
+    // The density increment is zero and j* - j = F; adding M^-1 (m* - m) to f keeps the stored
+    // deviations' mass exact up to unbiased rounding.
+    const C a1 = d1 * C(1.0 / 2394);
+    const C a2 = d2 * C(1.0 / 252);
+    const C a3 = Fx * C(0.1);
+    const C a4 = d4 * C(1.0 / 40);
+    const C a5 = Fy * C(0.1);
+    const C a6 = d6 * C(1.0 / 40);
+    const C a7 = Fz * C(0.1);
+    const C a8 = d8 * C(1.0 / 40);
+    const C a9 = d9 * C(1.0 / 36);
+    const C a10 = d10 * C(1.0 / 72);
+    const C a11 = d11 * C(1.0 / 12);
+    const C a12 = d12 * C(1.0 / 24);
+    const C a13 = d13 * C(0.25);
+    const C a14 = d14 * C(0.25);
+    const C a15 = d15 * C(0.25);
+    const C a16 = d16 * C(0.125);
+    const C a17 = d17 * C(0.125);
+    const C a18 = d18 * C(0.125);
 
-    // f_a = sum_k M[k][a] a_k; columns of M written per velocity
-    f[0] = a0 - C(30) * a1 + C(12) * a2;
-    const C axis = a0 - C(11) * a1 - C(4) * a2;
+    // f_a += sum_k M[k][a] a_k; columns of M written per velocity
+    f[0] += -C(30) * a1 + C(12) * a2;
+    const C axis = -C(11) * a1 - C(4) * a2;
     // x axis: 3pxx = 2, 3pixx = -4, pww = piww = 0
     const C axx = axis + C(2) * a9 - C(4) * a10;
-    f[1] = axx + a3 - C(4) * a4;
-    f[2] = axx - a3 + C(4) * a4;
+    f[1] += axx + a3 - C(4) * a4;
+    f[2] += axx - a3 + C(4) * a4;
     // y axis: 3pxx = -1, 3pixx = 2, pww = 1, piww = -2
     const C ayy = axis - a9 + C(2) * a10 + a11 - C(2) * a12;
-    f[3] = ayy + a5 - C(4) * a6;
-    f[4] = ayy - a5 + C(4) * a6;
+    f[3] += ayy + a5 - C(4) * a6;
+    f[4] += ayy - a5 + C(4) * a6;
     // z axis: 3pxx = -1, 3pixx = 2, pww = -1, piww = 2
     const C azz = axis - a9 + C(2) * a10 - a11 + C(2) * a12;
-    f[5] = azz + a7 - C(4) * a8;
-    f[6] = azz - a7 + C(4) * a8;
-    const C edge = a0 + C(8) * a1 + a2;
+    f[5] += azz + a7 - C(4) * a8;
+    f[6] += azz - a7 + C(4) * a8;
+    const C edge = C(8) * a1 + a2;
     // xy edges: 3pxx = 1, 3pixx = 1, pww = 1, piww = 1
     const C exy0 = edge + a9 + a10 + a11 + a12;
-    f[7] = exy0 + (a3 + a4) + (a5 + a6) + a13 + (a16 - a17);
-    f[8] = exy0 - (a3 + a4) - (a5 + a6) + a13 - (a16 - a17);
-    f[9] = exy0 + (a3 + a4) - (a5 + a6) - a13 + (a16 + a17);
-    f[10] = exy0 - (a3 + a4) + (a5 + a6) - a13 - (a16 + a17);
+    f[7] += exy0 + (a3 + a4) + (a5 + a6) + a13 + (a16 - a17);
+    f[8] += exy0 - (a3 + a4) - (a5 + a6) + a13 - (a16 - a17);
+    f[9] += exy0 + (a3 + a4) - (a5 + a6) - a13 + (a16 + a17);
+    f[10] += exy0 - (a3 + a4) + (a5 + a6) - a13 - (a16 + a17);
     // xz edges: 3pxx = 1, 3pixx = 1, pww = -1, piww = -1
     const C exz0 = edge + a9 + a10 - a11 - a12;
-    f[11] = exz0 + (a3 + a4) + (a7 + a8) + a15 + (-a16 + a18);
-    f[12] = exz0 - (a3 + a4) - (a7 + a8) + a15 - (-a16 + a18);
-    f[13] = exz0 + (a3 + a4) - (a7 + a8) - a15 + (-a16 - a18);
-    f[14] = exz0 - (a3 + a4) + (a7 + a8) - a15 - (-a16 - a18);
+    f[11] += exz0 + (a3 + a4) + (a7 + a8) + a15 + (-a16 + a18);
+    f[12] += exz0 - (a3 + a4) - (a7 + a8) + a15 - (-a16 + a18);
+    f[13] += exz0 + (a3 + a4) - (a7 + a8) - a15 + (-a16 - a18);
+    f[14] += exz0 - (a3 + a4) + (a7 + a8) - a15 - (-a16 - a18);
     // yz edges: 3pxx = -2, 3pixx = -2, pww = 0, piww = 0
     const C eyz0 = edge - C(2) * a9 - C(2) * a10;
-    f[15] = eyz0 + (a5 + a6) + (a7 + a8) + a14 + (a17 - a18);
-    f[16] = eyz0 - (a5 + a6) - (a7 + a8) + a14 - (a17 - a18);
-    f[17] = eyz0 + (a5 + a6) - (a7 + a8) - a14 + (a17 + a18);
-    f[18] = eyz0 - (a5 + a6) + (a7 + a8) - a14 - (a17 + a18);
+    f[15] += eyz0 + (a5 + a6) + (a7 + a8) + a14 + (a17 - a18);
+    f[16] += eyz0 - (a5 + a6) - (a7 + a8) + a14 - (a17 - a18);
+    f[17] += eyz0 + (a5 + a6) - (a7 + a8) - a14 + (a17 + a18);
+    f[18] += eyz0 - (a5 + a6) + (a7 + a8) - a14 - (a17 + a18);
 }
 
 // Reverse of collide_d2q9: given mu = dL/df* at one node, the adjoints of its inputs.  f holds the

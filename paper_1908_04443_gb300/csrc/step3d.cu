@@ -43,7 +43,15 @@ __device__ __forceinline__ int ring(int z, int r) {
 
 template <class S>
 struct ZShape;
-template <> struct ZShape<float> { static constexpr int X = 32, Y = 8, Z = 32, MINB = 2; };
+#ifndef LBMWET_Z3F_X   // column and chunk of the FP32 z-march (compile-time; chosen by measurement)
+#define LBMWET_Z3F_X 32
+#define LBMWET_Z3F_Y 4
+#define LBMWET_Z3F_Z 32
+#define LBMWET_Z3F_MINB 3
+#endif
+template <> struct ZShape<float> {
+    static constexpr int X = LBMWET_Z3F_X, Y = LBMWET_Z3F_Y, Z = LBMWET_Z3F_Z, MINB = LBMWET_Z3F_MINB;
+};
 template <> struct ZShape<double> { static constexpr int X = 32, Y = 4, Z = 32, MINB = 1; };
 
 template <class S, class C, int MODE>
