@@ -46,7 +46,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "kernels.h"):
+    for f in ("step.cu", "step2d.cu", "step3d.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):
         with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -201,12 +201,15 @@ def dist_setup():
     return world, rank, local
 
 
+STEP_KERNEL = "auto"   # --step-kernel
+
+
 def make_cfg(L, wl, precision, rho_g, rho_l):
     e = L.make_eos(wl.eos, 0.25, 4.0, 1.0, 0.0)
     e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
     return L.make_config(wl.lattice, precision, wl.shape, e, sigma=sigma_for(wl), rho_l=rho_l, rho_g=rho_g,
                          kappa=wl.kappa, rho_ref=rho_g, body=("ball", wl.body_center, wl.body_radius),
-                         drop_hint=wl.drop_center)
+                         drop_hint=wl.drop_center, step_kernel=STEP_KERNEL)
 
 
 class Runner:
@@ -237,6 +240,15 @@ class Runner:
 
     def launches(self):
         return self.L.lbm_batch_kernel_launches(self.b) if self.batch else self.L.lbm_kernel_launches(self.h)
+
+    def kernel_name(self):
+        """Name of the step kernel this run launches."""
+        k = self.L.lbm_batch_step_kernel_used(self.b) if self.batch else self.L.lbm_step_kernel_used(self.h)
+        if k == "ymarch":
+            return "ymarch_step"
+        if k == "tile":
+            return "fused_step_batched" if self.batch else "fused_step"
+        return "zmarch_step"
 
     def close(self):
         if self.batch:
@@ -427,7 +439,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes, "kernel": "fused_step" + ("_batched" if run.batch else "")}
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel": run.kernel_name()}
 
     # batched launch vs one launch per instance (no L2 flush: back-to-back steps)
     batched_vs_separate = None
@@ -542,6 +554,7 @@ def run_reference(args):
 
 
 def main():
+    global STEP_KERNEL
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -552,7 +565,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint side measurements")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "tile", "ymarch"],
+                    help="D2Q9 step kernel (batches: ymarch unless tile)")
     args = ap.parse_args()
+    STEP_KERNEL = args.step_kernel
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -11,6 +11,7 @@
 #include "eos_host.h"
 #include "kernels.h"
 #include "lattice.cuh"
+#include "plan.h"
 
 using namespace lbmwet;
 
@@ -37,6 +38,11 @@ struct lbm_handle {
     int int_tile[3] = {1, 1, 1};
     int* d_wall_id = nullptr;
     double* d_kappa = nullptr;
+    std::vector<uint8_t> mask;         // host solid mask (D2Q9: planning of y-march runs)
+    bool ymarch = false;               // single-grid steps by the y-march kernel
+    BatchItem* d_yitems = nullptr;     // its runs and per-CTA ranges
+    int* d_ybegin = nullptr;
+    int yctas = 0;
     unsigned* d_err = nullptr;
     double* d_rho = nullptr;
     double* d_u = nullptr;
@@ -88,6 +94,8 @@ void free_all(lbm_handle* h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_type);
     cudaFree(h->d_tile_solid);
+    cudaFree(h->d_yitems);
+    cudaFree(h->d_ybegin);
     cudaFree(h->d_wall_id);
     cudaFree(h->d_kappa);
     cudaFree(h->d_err);
@@ -120,8 +128,13 @@ lbm_status ensure_obs_buffers(lbm_handle* h) {
     return LBM_OK;
 }
 
+cudaError_t launch_handle_step(lbm_handle* h, cudaStream_t s, int from) {
+    if (h->ymarch) return launch_ymarch(h->prec, from, h->dp, h->d_yitems, h->d_ybegin, h->yctas, s);
+    return launch_step(h->lat, h->prec, h->f[from], h->f[from ^ 1], h->dp, s);
+}
+
 lbm_status launch_one_step(lbm_handle* h, cudaStream_t s, int from) {
-    cudaError_t e = launch_step(h->lat, h->prec, h->f[from], h->f[from ^ 1], h->dp, s);
+    cudaError_t e = launch_handle_step(h, s, from);
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
     return LBM_OK;
 }
@@ -132,7 +145,7 @@ lbm_status build_graph(lbm_handle* h, int parity) {
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int b = parity;
     for (int i = 0; i < GRAPH_STEPS; ++i) {
-        cudaError_t e = launch_step(h->lat, h->prec, h->f[b], h->f[b ^ 1], h->dp, h->cap_stream);
+        cudaError_t e = launch_handle_step(h, h->cap_stream, b);
         if (e != cudaSuccess) {
             cudaStreamEndCapture(h->cap_stream, &g);
             if (g) cudaGraphDestroy(g);
@@ -223,6 +236,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
     if (!(c.G != 0.0) || !std::isfinite(c.G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
     if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD) return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
+    if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH)
+        return fail(nullptr, LBM_ERR_ARG, "unknown step kernel");
     double tc;
     lbm_status st = lbm_critical_temperature(&c.eos, &tc);
     if (st != LBM_OK) return st;
@@ -421,6 +436,32 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         cudaFree(d_u0);
         if (e != cudaSuccess) return oom(e, "initial state");
         h->launches += 1;
+    }
+    // D2Q9: keep the mask (batches plan their runs from it); plan this grid's y-march runs if asked
+    if (h->D == 2) {
+        h->mask.assign(solid_mask, solid_mask + N);
+        if (c.step_kernel == LBM_KERNEL_YMARCH) {
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            YGrid grid{nx, ny, h->mask.data(), BatchItem{}};
+            grid.proto.f[0] = h->f[0];
+            grid.proto.f[1] = h->f[1];
+            grid.proto.type = h->d_type;
+            grid.proto.wall_id = h->d_wall_id;
+            grid.proto.kappa_w = h->d_kappa;   // holds the scalar kappa at every wall node unless set per node
+            grid.proto.kappa = c.kappa;
+            const YPlan plan = plan_ymarch({grid}, ymarch_threads(h->prec), sms * ymarch_ctas_per_sm(h->prec));
+            CKI(cudaMalloc(&h->d_yitems, sizeof(BatchItem) * plan.items.size()), "cudaMalloc runs");
+            CKI(cudaMalloc(&h->d_ybegin, sizeof(int) * plan.begin.size()), "cudaMalloc runs");
+            CKI(cudaMemcpyAsync(h->d_yitems, plan.items.data(), sizeof(BatchItem) * plan.items.size(),
+                                cudaMemcpyHostToDevice, h->stream), "copy runs");
+            CKI(cudaMemcpyAsync(h->d_ybegin, plan.begin.data(), sizeof(int) * plan.begin.size(),
+                                cudaMemcpyHostToDevice, h->stream), "copy runs");
+            CKI(cudaStreamSynchronize(h->stream), "sync");
+            h->yctas = plan.ctas;
+            h->ymarch = true;
+        }
     }
 #undef CKI
     h->cur = 0;
@@ -642,6 +683,11 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
 
+int32_t lbm_step_kernel_used(const lbm_handle* h) {
+    if (!h || h->D != 2) return LBM_KERNEL_AUTO;
+    return h->ymarch ? LBM_KERNEL_YMARCH : LBM_KERNEL_TILE;
+}
+
 void lbm_destroy(lbm_handle* h) {
     if (!h || h->batch_member) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -763,6 +809,8 @@ struct lbm_batch {
     unsigned* d_err = nullptr;
     BatchInstance* d_insts = nullptr;
     BatchItem* d_items = nullptr;
+    int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
+    bool ymarch = false;
     int n_items = 0, ctas = 1, cur = 0;
     int64_t step = 0, launches = 0, nodes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -802,6 +850,7 @@ void batch_free(lbm_batch* b) {
     cudaFree(b->d_err);
     cudaFree(b->d_insts);
     cudaFree(b->d_items);
+    cudaFree(b->d_begin);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -809,8 +858,13 @@ void batch_free(lbm_batch* b) {
     b->inst.clear();
 }
 
+cudaError_t batch_step_kernel(lbm_batch* b, cudaStream_t s, int parity) {
+    if (b->ymarch) return launch_ymarch(b->prec, parity, b->phys, b->d_items, b->d_begin, b->ctas, s);
+    return launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
+}
+
 lbm_status batch_launch(lbm_batch* b, cudaStream_t s, int parity) {
-    cudaError_t e = launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
+    cudaError_t e = batch_step_kernel(b, s, parity);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -821,8 +875,7 @@ lbm_status batch_graph(lbm_batch* b, int parity) {
     CKB(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     int par = parity;
     for (int i = 0; i < GRAPH_STEPS; ++i) {
-        cudaError_t e = launch_step_batched(b->lat, b->prec, par, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas,
-                                            b->cap_stream);
+        cudaError_t e = batch_step_kernel(b, b->cap_stream, par);
         if (e != cudaSuccess) {
             cudaStreamEndCapture(b->cap_stream, &g);
             if (g) cudaGraphDestroy(g);
@@ -884,7 +937,9 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     b->prec = cfgs[0].precision;
     for (int i = 0; i < n; ++i) {
         lbm_handle* h = nullptr;
-        lbm_status st = lbm_init(&cfgs[i], masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
+        lbm_config ci = cfgs[i];
+        ci.step_kernel = LBM_KERNEL_TILE;   // the batch plans its own runs; members are not stepped alone
+        lbm_status st = lbm_init(&ci, masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
                                  kappas_per_wall ? kappas_per_wall[i] : nullptr, stream, &h);
         if (st != LBM_OK) {
             const std::string m = "instance " + std::to_string(i) + ": " + g_init_error;
@@ -896,33 +951,58 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         b->inst.push_back(h);
         b->nodes += h->N;
     }
-    int tx, ty, tz;
-    step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     std::vector<BatchInstance> insts(n);
     std::vector<BatchItem> items;
-    for (int i = 0; i < n; ++i) {
-        lbm_handle* h = b->inst[i];
-        BatchInstance& d = insts[i];
-        d.nx = h->cfg.nx;
-        d.ny = h->cfg.ny;
-        d.nz = h->cfg.nz;
-        d.N = int(h->N);
-        d.f[0] = h->f[0];
-        d.f[1] = h->f[1];
-        d.type = h->d_type;
-        d.wall_id = h->d_wall_id;
-        d.kappa_w = h->dp.kappa_w;
-        d.kappa = h->dp.kappa;
-        for (int z = 0; z < d.nz; z += tz)
+    std::vector<int> begin;
+    b->ymarch = cfgs[0].step_kernel == LBM_KERNEL_YMARCH;
+    if (b->ymarch) {
+        // y-march runs of every instance, balanced over the resident CTAs
+        std::vector<YGrid> grids;
+        for (int i = 0; i < n; ++i) {
+            lbm_handle* h = b->inst[i];
+            YGrid g{h->cfg.nx, h->cfg.ny, h->mask.data(), BatchItem{}};
+            g.proto.inst = i;
+            g.proto.f[0] = h->f[0];
+            g.proto.f[1] = h->f[1];
+            g.proto.type = h->d_type;
+            g.proto.wall_id = h->d_wall_id;
+            g.proto.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
+            g.proto.kappa = h->dp.kappa;
+            grids.push_back(g);
+        }
+        YPlan plan = plan_ymarch(grids, ymarch_threads(b->prec), sms * ymarch_ctas_per_sm(b->prec));
+        items = std::move(plan.items);
+        begin = std::move(plan.begin);
+        b->ctas = plan.ctas;
+    } else {
+        int tx, ty, tz;
+        step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
+        for (int i = 0; i < n; ++i) {
+            lbm_handle* h = b->inst[i];
+            BatchInstance& d = insts[i];
+            d.nx = h->cfg.nx;
+            d.ny = h->cfg.ny;
+            d.nz = h->cfg.nz;
+            d.N = int(h->N);
+            d.f[0] = h->f[0];
+            d.f[1] = h->f[1];
+            d.type = h->d_type;
+            d.wall_id = h->d_wall_id;
+            d.kappa_w = h->dp.kappa_w;
+            d.kappa = h->dp.kappa;
             for (int y = 0; y < d.ny; y += ty)
                 for (int x = 0; x < d.nx; x += tx) {
-                    const size_t t = ((size_t)(z / tz) * h->tiles[1] + y / ty) * h->tiles[0] + x / tx;
+                    const size_t t = (size_t)(y / ty) * h->tiles[0] + x / tx;
                     BatchItem it{};
                     it.nx = d.nx;
                     it.ny = d.ny;
                     it.N = d.N;
                     it.x0 = x;
                     it.y0 = y;
+                    it.y1 = std::min(y + ty, d.ny);
                     it.solid = int(h->tile_solid[t]);
                     it.inst = i;
                     it.f[0] = h->f[0];
@@ -933,17 +1013,18 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
                     it.kappa = h->dp.kappa;
                     items.push_back(it);
                 }
+        }
+        const long long cap = (long long)sms * batched_ctas_per_sm(b->lat, b->prec);
+        b->ctas = int((long long)items.size() < cap ? (long long)items.size() : cap);
     }
     b->n_items = int(items.size());
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long cap = (long long)sms * batched_ctas_per_sm(b->lat, b->prec);
-    b->ctas = int(b->n_items < cap ? b->n_items : cap);
     b->phys = b->inst[0]->dp;
     cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
+    if (e == cudaSuccess && b->ymarch) e = cudaMalloc(&b->d_begin, sizeof(int) * begin.size());
+    if (e == cudaSuccess && b->ymarch)
+        e = cudaMemcpyAsync(b->d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
@@ -995,6 +1076,11 @@ int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->inst.size() 
 
 int64_t lbm_batch_kernel_launches(const lbm_batch* b) { return b ? b->launches : 0; }
 
+int32_t lbm_batch_step_kernel_used(const lbm_batch* b) {
+    if (!b) return LBM_KERNEL_AUTO;
+    return b->ymarch ? LBM_KERNEL_YMARCH : LBM_KERNEL_TILE;
+}
+
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
 
 void lbm_batch_destroy(lbm_batch* b) {
@@ -1017,9 +1103,11 @@ extern "C" lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_ev
     if (h->D != 2) return fail(h, LBM_ERR_ARG, "the adjoint is implemented for D2Q9");
     if (n_steps < 1 || ckpt_every < 1) return fail(h, LBM_ERR_ARG, "n_steps and ckpt_every must be >= 1");
     if (h->cfg.wall_kind != LBM_WALL_IVD) return fail(h, LBM_ERR_ARG, "the adjoint differentiates the IVD scheme");
-    if (!h->dp.kappa_w) {
+    if (!h->dp.kappa_w || h->ymarch) {
         // switch to per-wall-node kappa (d_kappa already holds the scalar value at every wall node)
+        // and to the tile kernel, which the adjoint's replay of the recorded segments uses too
         h->dp.kappa_w = h->d_kappa;
+        h->ymarch = false;
         for (int i = 0; i < 2; ++i)
             if (h->graph[i]) {
                 cudaGraphExecDestroy(h->graph[i]);

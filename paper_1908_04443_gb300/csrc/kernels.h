@@ -37,11 +37,12 @@ struct BatchInstance {
     const double* kappa_w;     // per wall node or null (scalar kappa)
     double kappa;
 };
-// One work item of the batched step: a tile of an instance, with everything the tile needs
-// (one contiguous record, so that a CTA fetches the next item with one load per lane).
+// One work item of the batched tile kernel (a tile of an instance) or of the y-march (a run of rows
+// y0 .. y1 - 1 of a column block), with everything it needs (one contiguous record, so that a CTA
+// fetches the next item with one load per lane).
 struct BatchItem {
-    int nx, ny, N, x0, y0, solid;   // solid: a solid node lies within the tile's box + 3-node halo
-    int inst, pad;
+    int nx, ny, N, x0, y0, solid;   // solid: a solid node lies within the item's box + 3-node halo
+    int inst, y1;
     const void* f[2];
     const uint8_t* type;
     const int* wall_id;
@@ -70,6 +71,12 @@ cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, 
 // instance of the batch; each instance reads f[parity] and writes f[parity ^ 1].
 cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& phys, const BatchInstance* insts,
                                 const BatchItem* items, int n_items, int ctas, cudaStream_t s);
+// D2Q9 y-march step: `ctas` persistent CTAs of ymarch_threads(prec) threads; CTA c walks the runs
+// items[begin[c] .. begin[c + 1]), each reading f[parity] of its grid and writing f[parity ^ 1].
+cudaError_t launch_ymarch(int prec, int parity, const DevParams& phys, const BatchItem* items, const int* begin,
+                          int ctas, cudaStream_t s);
+int ymarch_threads(int prec);
+int ymarch_ctas_per_sm(int prec);
 // D3Q19 z-march step (mode 0: time step, 1: fields) and its tile (x, y, z-chunk).
 struct Geo;
 cudaError_t launch_step3d(int prec, int mode, const void* fin, void* fout, const Geo& g, const DevParams& p,

@@ -38,7 +38,8 @@ class lbm_config(C.Structure):
                 ("rho_l", C.c_double), ("rho_g", C.c_double), ("rho_ref", C.c_double),
                 ("body_force", C.c_double * 3), ("wall_kind", C.c_int32), ("kappa", C.c_double),
                 ("rho_w_const", C.c_double), ("body_kind", C.c_int32), ("body_center", C.c_double * 3),
-                ("body_radius", C.c_double), ("drop_hint", C.c_double * 3)]
+                ("body_radius", C.c_double), ("drop_hint", C.c_double * 3),
+                ("step_kernel", C.c_int32)]
 
 
 class lbm_obs(C.Structure):
@@ -79,6 +80,7 @@ def _load():
         "lbm_set_kappa": (C.c_int, [H, C.c_void_p]),
         "lbm_limiter_bounds": (C.c_int, [H, dp, dp]),
         "lbm_kernel_launches": (C.c_int64, [H]),
+        "lbm_step_kernel_used": (C.c_int32, [H]),
         "lbm_destroy": (None, [H]),
         "lbm_last_error": (C.c_char_p, [H]),
         "lbm_status_string": (C.c_char_p, [C.c_int]),
@@ -92,6 +94,7 @@ def _load():
         "lbm_batch_handle": (C.c_void_p, [C.c_void_p, C.c_int32]),
         "lbm_batch_size": (C.c_int32, [C.c_void_p]),
         "lbm_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
+        "lbm_batch_step_kernel_used": (C.c_int32, [C.c_void_p]),
         "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
         "lbm_batch_destroy": (None, [C.c_void_p]),
     }
@@ -106,6 +109,7 @@ _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
+            "lbm_step_kernel_used", "lbm_batch_step_kernel_used",
             "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_record", "lbm_adjoint", "lbm_batch_init", "lbm_batch_step",
             "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_handle", "lbm_batch_size",
             "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
@@ -247,6 +251,14 @@ def lbm_kernel_launches(h) -> int:
     return int(_lib.lbm_kernel_launches(h))
 
 
+KERNEL_NAMES = {0: "auto", 1: "tile", 2: "ymarch"}
+
+
+def lbm_step_kernel_used(h) -> str:
+    """"tile" or "ymarch" (D2Q9), "auto" for D3Q19 (its z-march)."""
+    return KERNEL_NAMES[int(_lib.lbm_step_kernel_used(h))]
+
+
 def lbm_destroy(h):
     _lib.lbm_destroy(h)
 
@@ -324,6 +336,10 @@ def lbm_batch_kernel_launches(b) -> int:
     return int(_lib.lbm_batch_kernel_launches(b))
 
 
+def lbm_batch_step_kernel_used(b) -> str:
+    return KERNEL_NAMES[int(_lib.lbm_batch_step_kernel_used(b))]
+
+
 def lbm_batch_destroy(b):
     _lib.lbm_batch_destroy(b)
 
@@ -337,9 +353,10 @@ def make_eos(kind: str, a: float, b: float, R: float = 1.0, T: float = 0.0, omeg
 def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos, *, G=-1.0, sigma=0.12,
                 s_rho=1.0, s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1, s_nu=1.0 / 0.95, s_pi=1.1, s_m=1.1,
                 rho_l=0.0, rho_g=0.0, rho_ref=0.0, body_force=(0.0, 0.0, 0.0), wall="IVD", kappa=0.0,
-                rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0)) -> lbm_config:
+                rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0), step_kernel="auto") -> lbm_config:
     """Build an lbm_config.  `shape` is the numpy shape (ny, nx) or (nz, ny, nx).  `body` is
-    ("ball", center, radius) or ("plane", wall_y) or None."""
+    ("ball", center, radius) or ("plane", wall_y) or None.  `step_kernel` is "auto", "tile" or
+    "ymarch" (D2Q9 work decomposition; results are the same)."""
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
     else:
@@ -358,6 +375,7 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
     cfg.wall_kind = {"IVD": LBM_WALL_IVD, "VD": LBM_WALL_VD}[wall]
     cfg.kappa = kappa
     cfg.rho_w_const = rho_w_const
+    cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2}[step_kernel]
     cfg.body_kind = LBM_BODY_NONE
     if body is not None:
         if body[0] == "ball":
@@ -413,6 +431,9 @@ class Simulation:
 
     def launches(self) -> int:
         return lbm_kernel_launches(self.h)
+
+    def step_kernel(self) -> str:
+        return lbm_step_kernel_used(self.h)
 
     def close(self):
         if self.h is not None:

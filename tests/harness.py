@@ -34,6 +34,7 @@ class Case:
     body: Optional[tuple] = None
     drop_hint: tuple = (0.0, 0.0, 0.0)
     rho_ref: float = 0.0
+    step_kernel: str = "auto"
 
     def oracle_eos(self):
         base = E.cs_config() if self.eos_kind == "CS" else E.pr_paper()
@@ -59,7 +60,7 @@ class Case:
         cfg = L.make_config(self.lattice, precision, self.shape, e, sigma=self.sigma, rho_l=l, rho_g=g,
                             kappa=kappa_scalar, wall=self.wall, rho_w_const=self.rho_w_const,
                             body_force=self.body_force, body=self.body, drop_hint=self.drop_hint,
-                            rho_ref=self.rho_ref, **self.rates)
+                            rho_ref=self.rho_ref, step_kernel=self.step_kernel, **self.rates)
         kpw = None if np.ndim(self.kappa) == 0 else np.asarray(self.kappa, dtype=np.float64)
         u0 = None if self.u0 is None else self.u0.reshape(-1)
         return L.Simulation(cfg, self.mask, self.rho0, u0, kpw, stream)

@@ -10,13 +10,18 @@ from tests.harness import drop_on_cylinder
 pytestmark = pytest.mark.gpu
 
 
-def _cases():
+def _cases(kernel="ymarch"):
     a = drop_on_cylinder((40, 48), (24.0, 14.0), 7.0, (24.0, 27.0), 8.0, kappa=0.2)
     b = drop_on_cylinder((37, 53), (20.3, 17.1), 9.5, (21.0, 30.0), 10.0, kappa=-0.02)
     c = drop_on_cylinder((64, 70), (35.0, 20.0), 10.0, (35.0, 38.0), 12.0, kappa=0.1)
+    # wider than one y-march column block (124 own columns): two blocks, the second ragged
+    d = drop_on_cylinder((50, 150), (70.0, 20.0), 9.0, (70.0, 38.0), 10.0, kappa=0.05)
     geo = lbm.Geometry(c.mask, "D2Q9")
     c.kappa = np.random.default_rng(4).uniform(-0.02, 0.3, len(geo.wall_flat))
-    return [a, b, c]
+    cases = [a, b, c, d]
+    for cs in cases:
+        cs.step_kernel = kernel   # the batch takes instance 0's choice; single runs use the same kernel
+    return cases
 
 
 def _batch(cases, precision):
@@ -31,12 +36,14 @@ def _batch(cases, precision):
     return L.lbm_batch_init(cfgs, masks, rho0s, kpw)
 
 
+@pytest.mark.parametrize("kernel", ["ymarch", "tile"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_equals_single_runs(precision):
+def test_batch_equals_single_runs(precision, kernel):
     from paper_1908_04443_gb300 import lbmwet as L
-    cases = _cases()
+    cases = _cases(kernel)
     b = _batch(cases, precision)
     try:
+        assert L.lbm_batch_step_kernel_used(b) == kernel
         L.lbm_batch_step(b, 37)          # 2 graph chunks of 16 + 5 single launches
         assert L.lbm_batch_kernel_launches(b) == 37
         for i, cs in enumerate(cases):
@@ -44,18 +51,20 @@ def test_batch_equals_single_runs(precision):
             q, n = 9, cs.mask.size
             fb = L.lbm_get_state(h, q, n)
             with cs.gpu(precision) as sim:
+                assert sim.step_kernel() == kernel
                 sim.step(37)
                 fs = sim.get_state().reshape(-1)
             assert np.max(np.abs(fb - fs)) == 0.0
         obs = L.lbm_batch_observables(b)
-        assert len(obs) == 3 and all(o.step == 37 for o in obs)
+        assert len(obs) == len(cases) and all(o.step == 37 for o in obs)
     finally:
         L.lbm_batch_destroy(b)
 
 
-def test_batched_step_matches_oracle():
+@pytest.mark.parametrize("kernel", ["ymarch", "tile"])
+def test_batched_step_matches_oracle(kernel):
     from paper_1908_04443_gb300 import lbmwet as L
-    cases = _cases()
+    cases = _cases(kernel)
     b = _batch(cases, "fp64")
     try:
         L.lbm_batch_step(b, 3)
@@ -83,6 +92,6 @@ def test_batch_member_rules():
         L.lbm_batch_step(b, 2)
         assert L.lbm_observables(h).step == 2
         with pytest.raises(IndexError):
-            L.lbm_batch_handle(b, 3)
+            L.lbm_batch_handle(b, 4)
     finally:
         L.lbm_batch_destroy(b)

@@ -34,8 +34,9 @@ def _one_step_case(case: Case, precision="fp64", steps_before=0):
     ((8, 8), (3.0, 4.0), 1.5, (5.0, 4.0), 2.5),                # grid smaller than one tile
     ((5, 70), (30.0, 2.0), 1.0, (40.0, 2.0), 3.0),             # thin strip
 ])
-def test_one_step_fp64(shape, center, R, dc, r):
-    case = drop_on_cylinder(shape, center, R, dc, r, kappa=0.15)
+@pytest.mark.parametrize("kernel", ["tile", "ymarch"])
+def test_one_step_fp64(shape, center, R, dc, r, kernel):
+    case = drop_on_cylinder(shape, center, R, dc, r, kappa=0.15, step_kernel=kernel)
     f0, f1, ref, geo = _one_step_case(case, steps_before=3)
     assert np.max(np.abs(f1 - ref)) < 1e-13
 
@@ -47,17 +48,19 @@ def test_one_step_fp64(shape, center, R, dc, r):
     dict(eos_kind="PR", t_over_tc=0.86, sigma=0.11),          # the paper's equation of state
     dict(rates=dict(s_e=0.6, s_eps=1.5, s_q=1.2, s_nu=1.7)),
 ])
-def test_one_step_variants(kw):
+@pytest.mark.parametrize("kernel", ["tile", "ymarch"])
+def test_one_step_variants(kw, kernel):
     shape = (48, 40)
-    case = drop_on_cylinder(shape, (20.0, 15.0), 7.0, (20.0, 28.0), 9.0, **kw)
+    case = drop_on_cylinder(shape, (20.0, 15.0), 7.0, (20.0, 28.0), 9.0, step_kernel=kernel, **kw)
     f0, f1, ref, geo = _one_step_case(case, steps_before=2)
     scale = max(1.0, np.abs(ref).max())
     assert np.max(np.abs(f1 - ref)) < 1e-13 * scale
 
 
-def test_per_wall_node_kappa():
+@pytest.mark.parametrize("kernel", ["tile", "ymarch"])
+def test_per_wall_node_kappa(kernel):
     shape = (40, 44)
-    base = drop_on_cylinder(shape, (22.0, 15.0), 8.0, (22.0, 28.0), 8.0)
+    base = drop_on_cylinder(shape, (22.0, 15.0), 8.0, (22.0, 28.0), 8.0, step_kernel=kernel)
     geo = lbm.Geometry(base.mask, "D2Q9")
     rng = np.random.default_rng(3)
     base.kappa = rng.uniform(-0.02, 0.4, len(geo.wall_flat))
@@ -67,11 +70,12 @@ def test_per_wall_node_kappa():
     assert np.max(np.abs(f1 - ref)) < 1e-13
 
 
-def test_all_fluid_and_flat_interface():
+@pytest.mark.parametrize("kernel", ["tile", "ymarch"])
+def test_all_fluid_and_flat_interface(kernel):
     shape = (64, 6)
     g_l = Case("D2Q9", shape, np.zeros(shape, np.uint8), np.zeros(shape)).bounds()
     rho = W.slab_density(shape, 16, 48, g_l[1], g_l[0])
-    case = Case("D2Q9", shape, np.zeros(shape, np.uint8), rho)
+    case = Case("D2Q9", shape, np.zeros(shape, np.uint8), rho, step_kernel=kernel)
     f0, f1, ref, _ = _one_step_case(case, steps_before=5)
     assert np.max(np.abs(f1 - ref)) < 1e-13
 
@@ -151,11 +155,12 @@ def test_state_round_trips():
         assert o.step == 7
 
 
-def test_unstable_state_is_reported():
+@pytest.mark.parametrize("kernel", ["tile", "ymarch"])
+def test_unstable_state_is_reported(kernel):
     """G > 0 makes the square-root argument of Eq. 6 negative: the device flags it, the call fails
     with LBM_ERR_UNSTABLE, and the context stays usable."""
     from paper_1908_04443_gb300 import lbmwet as L
-    case = drop_on_cylinder((16, 16), (8.0, 5.0), 2.0, (8.0, 10.0), 3.0)
+    case = drop_on_cylinder((16, 16), (8.0, 5.0), 2.0, (8.0, 10.0), 3.0, step_kernel=kernel)
     sim = case.gpu("fp64")
     sim.cfg.G = 1.0
     sim.close()
