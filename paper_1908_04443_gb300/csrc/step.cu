@@ -76,8 +76,10 @@ __device__ __forceinline__ C psi_slope(C rho, C psi, const Phys<C>& e) {
 // One tile: x0, y0, z0 is its first node.  All threads of the CTA call this together.
 // MODE 0: time step (writes f*); 1: fields (writes rho, u); 2: adjoint local part (writes AdjIO).
 // SOLID = false compiles the body of a tile with no solid node within its box (every cell a bulk
-// fluid node: no node-type staging, no bounce-back, no wall nodes).
-template <class L, class S, class C, int TX, int TY, int TZ, int MODE, bool SOLID = true>
+// fluid node: no node-type staging, no bounce-back, no wall nodes).  WRAP 0 compiles a tile whose
+// pulls touch no cell beyond the grid (no periodic wrapping: neighbours at constant offsets),
+// 1 a tile that wraps once, 2 a grid narrower than a tile plus its halo (full modulo).
+template <class L, class S, class C, int TX, int TY, int TZ, int MODE, bool SOLID = true, int WRAP = 2>
 __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
                                           const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid_arg,
                                           unsigned* err, double* __restrict__ rho_out, double* __restrict__ u_out,
@@ -90,11 +92,10 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     constexpr int YX = T::YX, YY = T::YY, YZ = T::YZ, HZ = T::HZ, PZH = T::PZH, YZH = T::YZH;
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
-    // grids narrower than a tile plus its halo wrap more than once: use the full modulo there
-    const bool small = nx < TX + 8 || ny < TY + 8 || (D == 3 && nz < TZ + 8);
-    auto wx = [&](int v) { return small ? wrap_full(v, nx) : wrap1(v, nx); };
-    auto wy = [&](int v) { return small ? wrap_full(v, ny) : wrap1(v, ny); };
-    auto wz = [&](int v) { return (D == 3) ? (small ? wrap_full(v, nz) : wrap1(v, nz)) : 0; };
+    auto wrapc = [](int v, int n) { return WRAP == 0 ? v : (WRAP == 1 ? wrap1(v, n) : wrap_full(v, n)); };
+    auto wx = [&](int v) { return wrapc(v, nx); };
+    auto wy = [&](int v) { return wrapc(v, ny); };
+    auto wz = [&](int v) { return (D == 3) ? wrapc(v, nz) : 0; };
     auto tix = [](int lx, int ly, int lz) { return (lz * YY + ly) * YX + lx; };
     auto rix = [](int lx, int ly, int lz) { return (lz * RY + ly) * RX + lx; };
     auto pix = [](int lx, int ly, int lz) { return (lz * PY + ly) * PX + lx; };
@@ -123,6 +124,26 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
 
     // pull of one node at global (gx, gy, gz) whose type-tile cell is ti
     auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int ti, uint8_t self) {
+        if constexpr (WRAP == 0) {
+            // every upstream node at a constant offset from the node itself
+            const int nxy = nx * ny;
+            const S* p = fin + ((gz * ny + gy) * nx + gx);
+            if (!SOLID || (self & T_BULK)) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                    f[a] = C(p[a * N - ex - ey * nx - ez * nxy]);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                    const bool bb = (sm.type[ti - ex - ey * YX - ez * YX * YY] & T_SOLID) != 0;
+                    f[a] = C(p[bb ? L::opp(a) * N : a * N - ex - ey * nx - ez * nxy]);
+                }
+            }
+            return;
+        }
         const int xm = wrap1(gx - 1, nx), xp = wrap1(gx + 1, nx);
         const int ym = wrap1(gy - 1, ny), yp = wrap1(gy + 1, ny);
         const int cx[3] = {xm, gx, xp};
@@ -162,6 +183,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     const uint8_t my_type = type_at(my_ti);
     const bool my_fluid = !(my_type & T_SOLID);
     C f[Q];
+    C my_drho = C(0);
     {
         C rho = C(0);
         if (my_fluid) {
@@ -169,6 +191,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
             C drho = C(0);
 #pragma unroll
             for (int a = 0; a < Q; ++a) drho += f[a];
+            my_drho = drho;
             rho = ph.rho_ref + drho;
             sm.psi[pix(lx + 1, ly + 1, lz + PZH)] = psi_checked(rho, ph, err);
         } else {
@@ -315,10 +338,10 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     // Eq. 5
     const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy, Fmz = -ph.G * psi_c * sz;
     const C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
-    C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    const C drho = my_drho;   // sum of f in the order of the pull's density
+    C jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        drho += f[a];
         if (L::ex(a)) jx += C(L::ex(a)) * f[a];
         if (L::ey(a)) jy += C(L::ey(a)) * f[a];
         if (D == 3 && L::ez(a)) jz += C(L::ez(a)) * f[a];
@@ -380,6 +403,35 @@ template <> struct TileShape<D2Q9, float> {
 };
 template <> struct TileShape<D2Q9, double> { static constexpr int X = 32, Y = 8, Z = 1, MINB = 2; };
 
+// Wrap mode of a tile (the WRAP parameter of tile_body): 0 when every cell its pulls touch (the
+// tile + 3 cells on each side) lies inside the grid, 2 for grids narrower than a tile plus its
+// halo, else 1.
+template <int D, int TX, int TY, int TZ>
+__device__ __forceinline__ int tile_wrap(int x0, int y0, int z0, int nx, int ny, int nz) {
+    if (nx < TX + 8 || ny < TY + 8 || (D == 3 && nz < TZ + 8)) return 2;
+    const bool inside = x0 >= 3 && x0 + TX + 2 < nx && y0 >= 3 && y0 + TY + 2 < ny &&
+                        (D == 2 || (z0 >= 3 && z0 + TZ + 2 < nz));
+    return inside ? 0 : 1;
+}
+
+// tile_body with the wrap mode chosen at run time (uniform per CTA)
+template <class L, class S, class C, int TX, int TY, int TZ, int MODE, bool SOLID>
+__device__ __forceinline__ void tile_body_w(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,
+                                            const Phys<C>& ph, int x0, int y0, int z0, bool tile_solid_arg,
+                                            unsigned* err, double* __restrict__ rho_out, double* __restrict__ u_out,
+                                            TileSmem<L, C, TX, TY, TZ, MODE == 2>& sm, const AdjIO<C>* adj = nullptr) {
+    const int w = tile_wrap<L::D, TX, TY, TZ>(x0, y0, z0, g.nx, g.ny, g.nz);
+    if (w == 0)
+        tile_body<L, S, C, TX, TY, TZ, MODE, SOLID, 0>(fin, fout, g, ph, x0, y0, z0, tile_solid_arg, err, rho_out,
+                                                       u_out, sm, adj);
+    else if (w == 1)
+        tile_body<L, S, C, TX, TY, TZ, MODE, SOLID, 1>(fin, fout, g, ph, x0, y0, z0, tile_solid_arg, err, rho_out,
+                                                       u_out, sm, adj);
+    else
+        tile_body<L, S, C, TX, TY, TZ, MODE, SOLID, 2>(fin, fout, g, ph, x0, y0, z0, tile_solid_arg, err, rho_out,
+                                                       u_out, sm, adj);
+}
+
 
 template <class L, class S, class C, int MODE>
 __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileShape<L, S>::Z, TileShape<L, S>::MINB)
@@ -390,11 +442,12 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
     const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
     if (solid)
-        tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE, true>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
-                                                            blockIdx.z * TS::Z, true, err, rho_out, u_out, sm);
+        tile_body_w<L, S, C, TS::X, TS::Y, TS::Z, MODE, true>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
+                                                              blockIdx.z * TS::Z, true, err, rho_out, u_out, sm);
     else
-        tile_body<L, S, C, TS::X, TS::Y, TS::Z, MODE, false>(fin, fout, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y,
-                                                             blockIdx.z * TS::Z, false, err, rho_out, u_out, sm);
+        tile_body_w<L, S, C, TS::X, TS::Y, TS::Z, MODE, false>(fin, fout, g, ph, blockIdx.x * TS::X,
+                                                               blockIdx.y * TS::Y, blockIdx.z * TS::Z, false, err,
+                                                               rho_out, u_out, sm);
 }
 
 // Adjoint local part (D2Q9): the forward tile machinery recomputes rho, psi and rho_w of the state
@@ -406,8 +459,8 @@ __global__ void __launch_bounds__(TileShape<D2Q9, S>::X* TileShape<D2Q9, S>::Y, 
     __shared__ TileSmem<D2Q9, S, TS::X, TS::Y, 1, true> sm;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
-    tile_body<D2Q9, S, S, TS::X, TS::Y, 1, 2>(fin, nullptr, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y, 0, solid,
-                                               err, nullptr, nullptr, sm, &io);
+    tile_body_w<D2Q9, S, S, TS::X, TS::Y, 1, 2, true>(fin, nullptr, g, ph, blockIdx.x * TS::X, blockIdx.y * TS::Y, 0,
+                                                       solid, err, nullptr, nullptr, sm, &io);
 }
 
 // Batched step: CTAs walk the work list; each item is one tile of one instance.  The next item's
@@ -446,11 +499,11 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
         const S* fin = static_cast<const S*>(item.f[parity]);
         S* fout = static_cast<S*>(const_cast<void*>(item.f[parity ^ 1]));
         if (item.solid)
-            tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0, true>(fin, fout, g, ph, item.x0, item.y0, 0, true, err,
-                                                             nullptr, nullptr, sm);
+            tile_body_w<L, S, C, TS::X, TS::Y, TS::Z, 0, true>(fin, fout, g, ph, item.x0, item.y0, 0, true, err,
+                                                               nullptr, nullptr, sm);
         else
-            tile_body<L, S, C, TS::X, TS::Y, TS::Z, 0, false>(fin, fout, g, ph, item.x0, item.y0, 0, false, err,
-                                                              nullptr, nullptr, sm);
+            tile_body_w<L, S, C, TS::X, TS::Y, TS::Z, 0, false>(fin, fout, g, ph, item.x0, item.y0, 0, false, err,
+                                                                nullptr, nullptr, sm);
         if (fetch) reinterpret_cast<uint32_t*>(&s_item[slot ^ 1])[tid] = w;
         __syncthreads();   // the next record is visible, and this tile's threads are done with shared memory
         slot ^= 1;

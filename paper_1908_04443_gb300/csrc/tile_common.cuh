@@ -76,6 +76,11 @@ __device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {
     return e.two_over_G * (p - rho * C(1.0 / 3.0));   // Eq. 6 argument: 2 (p - rho c_s^2) / (G c^2)
 }
 
+// Square root in compute precision: IEEE in FP64; in FP32 x * rsqrt(x) (a few ulp, below the
+// rounding of the FP32 state; x > 0 here).
+__device__ __forceinline__ float csqrt(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double csqrt(double x) { return sqrt(x); }
+
 template <class C>
 __device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err) {
     const C arg = psi_arg(rho, e);
@@ -83,7 +88,7 @@ __device__ __forceinline__ C psi_checked(C rho, const Phys<C>& e, unsigned* err)
         atomicOr(err, ERR_PSI);
         return C(0);
     }
-    return sqrt(arg);
+    return csqrt(arg);
 }
 
 // The k-th cell of the one-cell-thick shell of an AX x AY (x AZ) box, enumerated so that
