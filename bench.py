@@ -46,7 +46,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("step.cu", "step2d.cu", "step3d.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):
+    for f in ("step.cu", "step2p.cu", "step2d.cu", "step3d.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):
         with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -246,6 +246,8 @@ class Runner:
         k = self.L.lbm_batch_step_kernel_used(self.b) if self.batch else self.L.lbm_step_kernel_used(self.h)
         if k == "ymarch":
             return "ymarch_step"
+        if k == "pair":
+            return "pair_step_batched" if self.batch else "pair_step"
         if k == "tile":
             return "fused_step_batched" if self.batch else "fused_step"
         return "zmarch_step"
@@ -565,8 +567,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint side measurements")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "tile", "ymarch"],
-                    help="D2Q9 step kernel (batches: ymarch unless tile)")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "tile", "ymarch", "pair"],
+                    help="D2Q9 step kernel (auto: pair in FP32, tile in FP64)")
     args = ap.parse_args()
     STEP_KERNEL = args.step_kernel
     if args.impl == "reference":

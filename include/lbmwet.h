@@ -68,13 +68,15 @@ typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1 } lbm_wall_kind;
  * PLANE: a flat wall at y = body_center[1] (the halfway position), liquid at larger y. */
 typedef enum { LBM_BODY_NONE = 0, LBM_BODY_BALL = 1, LBM_BODY_PLANE = 2 } lbm_body_kind;
 
-/* Step kernel of a D2Q9 grid (no counterpart in the paper: a choice of work decomposition that
- * leaves every result unchanged, bit for bit).  TILE: one CTA per 32 x 8 tile with its halo ring.
- * YMARCH: persistent CTAs walking runs of rows of column blocks (124 own columns plus a 2-cell
- * halo on each side), planned on the host so that every CTA pulls about the same number of rows.
- * AUTO: TILE (the faster of the two on the measured workloads).  A batch uses instance 0's choice.
- * A handle that records a trajectory for the adjoint steps with TILE from lbm_record on. */
-typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_TILE = 1, LBM_KERNEL_YMARCH = 2 } lbm_step_kernel;
+/* Step kernel of a D2Q9 grid (no counterpart in the paper: a choice of work decomposition).
+ * TILE: one CTA per 32 x 8 tile with its halo ring, one node per thread.  YMARCH: persistent CTAs
+ * walking runs of rows of column blocks (124 own columns plus a 2-cell halo on each side),
+ * planned on the host so that every CTA pulls about the same number of rows; bit-identical to
+ * TILE.  PAIR (FP32 only): 32 x 16 tiles, two nodes per thread computed together with packed
+ * FP32x2 instructions; equal to TILE up to FP32 rounding (the operations are regrouped).  AUTO:
+ * PAIR in FP32, TILE in FP64.  A batch uses instance 0's choice.  A y-march handle that records a
+ * trajectory for the adjoint steps with TILE from lbm_record on. */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_TILE = 1, LBM_KERNEL_YMARCH = 2, LBM_KERNEL_PAIR = 3 } lbm_step_kernel;
 
 typedef struct {
     int32_t kind;      /* lbm_eos_kind                                       */
@@ -213,8 +215,8 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
-/* Step kernel the handle's lbm_step uses now: LBM_KERNEL_TILE or LBM_KERNEL_YMARCH (D2Q9, see
- * lbm_step_kernel), LBM_KERNEL_AUTO for D3Q19 (z-march) or a NULL handle. */
+/* Step kernel the handle's lbm_step uses now: LBM_KERNEL_TILE, LBM_KERNEL_YMARCH or
+ * LBM_KERNEL_PAIR (D2Q9, see lbm_step_kernel), LBM_KERNEL_AUTO for D3Q19 (z-march) or a NULL handle. */
 int32_t lbm_step_kernel_used(const lbm_handle* h);
 
 /* ---- Adjoint (D2Q9, IVD walls) -------------------------------------------------------------
@@ -265,7 +267,7 @@ lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n);
 lbm_handle* lbm_batch_handle(lbm_batch* b, int32_t i);
 int32_t lbm_batch_size(const lbm_batch* b);
 int64_t lbm_batch_kernel_launches(const lbm_batch* b);
-/* Step kernel of the batch: LBM_KERNEL_TILE or LBM_KERNEL_YMARCH (0 for NULL). */
+/* Step kernel of the batch: LBM_KERNEL_TILE, LBM_KERNEL_YMARCH or LBM_KERNEL_PAIR (0 for NULL). */
 int32_t lbm_batch_step_kernel_used(const lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);

@@ -34,6 +34,8 @@ struct lbm_handle {
     uint8_t* d_type = nullptr;
     uint8_t* d_tile_solid = nullptr;
     std::vector<uint8_t> tile_solid;   // per step-kernel tile: a solid node within the tile + 3-node halo
+    std::vector<uint8_t> pair_solid;   // the same per tile of the FP32 pair kernel (D2Q9)
+    uint8_t* d_pair_solid = nullptr;   // set when this handle steps with the pair kernel
     int tiles[3] = {1, 1, 1};
     int int_tile[3] = {1, 1, 1};
     int* d_wall_id = nullptr;
@@ -65,6 +67,35 @@ struct lbm_handle {
 
 namespace {
 
+// Per tile of a t[0] x t[1] x t[2] tiling: does a solid node lie within the box of cells the tile
+// touches (the full tile, including cells of a ragged tile that wrap past the grid edge, plus a
+// 3-node halo; no z halo in 2D)?  Tiles without one skip the node-type staging.
+std::vector<uint8_t> tile_solid_flags(const uint8_t* mask, int nx, int ny, int nz, const int t[3], int D) {
+    const int tiles[3] = {(nx + t[0] - 1) / t[0], (ny + t[1] - 1) / t[1], (nz + t[2] - 1) / t[2]};
+    const int hz = D == 3 ? 3 : 0;
+    std::vector<uint8_t> out((size_t)tiles[0] * tiles[1] * tiles[2], 0);
+    for (int tz = 0; tz < tiles[2]; ++tz)
+        for (int ty = 0; ty < tiles[1]; ++ty)
+            for (int tx = 0; tx < tiles[0]; ++tx) {
+                bool found = false;
+                for (int dz = -hz; dz < (D == 3 ? t[2] + hz : 1) && !found; ++dz) {
+                    const int z = ((tz * t[2] + dz) % nz + nz) % nz;
+                    for (int dy = -3; dy < t[1] + 3 && !found; ++dy) {
+                        const int y = ((ty * t[1] + dy) % ny + ny) % ny;
+                        const uint8_t* row = mask + ((long long)z * ny + y) * nx;
+                        for (int dx = -3; dx < t[0] + 3; ++dx) {
+                            if (row[((tx * t[0] + dx) % nx + nx) % nx]) {
+                                found = true;
+                                break;
+                            }
+                        }
+                    }
+                }
+                out[((size_t)tz * tiles[1] + ty) * tiles[0] + tx] = found ? 1 : 0;
+            }
+    return out;
+}
+
 lbm_status fail(lbm_handle* h, lbm_status s, const std::string& msg) {
     if (h) h->err = msg;
     else g_init_error = msg;
@@ -94,6 +125,7 @@ void free_all(lbm_handle* h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_type);
     cudaFree(h->d_tile_solid);
+    cudaFree(h->d_pair_solid);
     cudaFree(h->d_yitems);
     cudaFree(h->d_ybegin);
     cudaFree(h->d_wall_id);
@@ -236,8 +268,11 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
     if (!(c.G != 0.0) || !std::isfinite(c.G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
     if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD) return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
-    if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH)
+    if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH &&
+        c.step_kernel != LBM_KERNEL_PAIR)
         return fail(nullptr, LBM_ERR_ARG, "unknown step kernel");
+    if (c.step_kernel == LBM_KERNEL_PAIR && (c.lattice != LBM_D2Q9 || c.precision != LBM_FP32_DEV))
+        return fail(nullptr, LBM_ERR_ARG, "the pair kernel is for D2Q9 in FP32");
     double tc;
     lbm_status st = lbm_critical_temperature(&c.eos, &tc);
     if (st != LBM_OK) return st;
@@ -295,9 +330,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "the grid has no fluid node");
     }
-    // per tile of the step kernel: does a solid node lie within the box of cells the tile touches
-    // (the full tile, including cells of a ragged tile that wrap past the grid edge, plus a 3-node
-    // halo)?  Tiles without one skip the node-type staging.
+    // solid flags per tile of the step kernels (see tile_solid_flags)
     {
         int t[3];
         step_tile_shape(c.lattice, c.precision, &t[0], &t[1], &t[2]);
@@ -306,28 +339,11 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             h->int_tile[k] = t[k];
             h->tiles[k] = (n3[k] + t[k] - 1) / t[k];
         }
-        const int hz = h->D == 3 ? 3 : 0;
-        h->tile_solid.assign((size_t)h->tiles[0] * h->tiles[1] * h->tiles[2], 0);
-        if (nfluid < N) {
-            for (int tz = 0; tz < h->tiles[2]; ++tz)
-                for (int ty = 0; ty < h->tiles[1]; ++ty)
-                    for (int tx = 0; tx < h->tiles[0]; ++tx) {
-                        bool found = false;
-                        for (int dz = -hz; dz < (h->D == 3 ? t[2] + hz : 1) && !found; ++dz) {
-                            const int z = ((tz * t[2] + dz) % nz + nz) % nz;
-                            for (int dy = -3; dy < t[1] + 3 && !found; ++dy) {
-                                const int y = ((ty * t[1] + dy) % ny + ny) % ny;
-                                const uint8_t* row = solid_mask + ((long long)z * ny + y) * nx;
-                                for (int dx = -3; dx < t[0] + 3; ++dx) {
-                                    if (row[((tx * t[0] + dx) % nx + nx) % nx]) {
-                                        found = true;
-                                        break;
-                                    }
-                                }
-                            }
-                        }
-                        h->tile_solid[((size_t)tz * h->tiles[1] + ty) * h->tiles[0] + tx] = found ? 1 : 0;
-                    }
+        h->tile_solid = tile_solid_flags(solid_mask, nx, ny, nz, t, h->D);
+        if (h->D == 2 && c.precision == LBM_FP32_DEV) {
+            int tp[3] = {1, 1, 1};
+            pair_tile_shape(&tp[0], &tp[1]);
+            h->pair_solid = tile_solid_flags(solid_mask, nx, ny, nz, tp, 2);
         }
     }
 
@@ -461,6 +477,15 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             CKI(cudaStreamSynchronize(h->stream), "sync");
             h->yctas = plan.ctas;
             h->ymarch = true;
+        }
+        // FP32: the pair kernel unless the tile kernel (or the y-march) was asked for
+        if (c.precision == LBM_FP32_DEV && (c.step_kernel == LBM_KERNEL_AUTO || c.step_kernel == LBM_KERNEL_PAIR)) {
+            CKI(cudaMalloc(&h->d_pair_solid, h->pair_solid.size()), "cudaMalloc tile flags");
+            CKI(cudaMemcpyAsync(h->d_pair_solid, h->pair_solid.data(), h->pair_solid.size(), cudaMemcpyHostToDevice,
+                                h->stream),
+                "copy tile flags");
+            CKI(cudaStreamSynchronize(h->stream), "sync");
+            h->dp.pair_solid = h->d_pair_solid;
         }
     }
 #undef CKI
@@ -685,7 +710,8 @@ int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
 
 int32_t lbm_step_kernel_used(const lbm_handle* h) {
     if (!h || h->D != 2) return LBM_KERNEL_AUTO;
-    return h->ymarch ? LBM_KERNEL_YMARCH : LBM_KERNEL_TILE;
+    if (h->ymarch) return LBM_KERNEL_YMARCH;
+    return h->dp.pair_solid ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE;
 }
 
 void lbm_destroy(lbm_handle* h) {
@@ -811,6 +837,7 @@ struct lbm_batch {
     BatchItem* d_items = nullptr;
     int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
     bool ymarch = false;
+    bool pair = false;                 // FP32 pair kernel (else the tile kernel, unless y-march)
     int n_items = 0, ctas = 1, cur = 0;
     int64_t step = 0, launches = 0, nodes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -860,6 +887,7 @@ void batch_free(lbm_batch* b) {
 
 cudaError_t batch_step_kernel(lbm_batch* b, cudaStream_t s, int parity) {
     if (b->ymarch) return launch_ymarch(b->prec, parity, b->phys, b->d_items, b->d_begin, b->ctas, s);
+    if (b->pair) return launch_pair_batched(parity, b->phys, b->d_items, b->n_items, b->ctas, s);
     return launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
 }
 
@@ -958,6 +986,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     std::vector<BatchItem> items;
     std::vector<int> begin;
     b->ymarch = cfgs[0].step_kernel == LBM_KERNEL_YMARCH;
+    b->pair = !b->ymarch && b->prec == LBM_FP32_DEV &&
+              (cfgs[0].step_kernel == LBM_KERNEL_AUTO || cfgs[0].step_kernel == LBM_KERNEL_PAIR);
     if (b->ymarch) {
         // y-march runs of every instance, balanced over the resident CTAs
         std::vector<YGrid> grids;
@@ -980,6 +1010,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     } else {
         int tx, ty, tz;
         step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
+        if (b->pair) pair_tile_shape(&tx, &ty);
         for (int i = 0; i < n; ++i) {
             lbm_handle* h = b->inst[i];
             BatchInstance& d = insts[i];
@@ -995,7 +1026,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             d.kappa = h->dp.kappa;
             for (int y = 0; y < d.ny; y += ty)
                 for (int x = 0; x < d.nx; x += tx) {
-                    const size_t t = (size_t)(y / ty) * h->tiles[0] + x / tx;
+                    const size_t t = (size_t)(y / ty) * ((d.nx + tx - 1) / tx) + x / tx;
                     BatchItem it{};
                     it.nx = d.nx;
                     it.ny = d.ny;
@@ -1003,7 +1034,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
                     it.x0 = x;
                     it.y0 = y;
                     it.y1 = std::min(y + ty, d.ny);
-                    it.solid = int(h->tile_solid[t]);
+                    it.solid = int(b->pair ? h->pair_solid[t] : h->tile_solid[t]);
                     it.inst = i;
                     it.f[0] = h->f[0];
                     it.f[1] = h->f[1];
@@ -1014,7 +1045,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
                     items.push_back(it);
                 }
         }
-        const long long cap = (long long)sms * batched_ctas_per_sm(b->lat, b->prec);
+        const long long cap = (long long)sms * (b->pair ? pair_ctas_per_sm() : batched_ctas_per_sm(b->lat, b->prec));
         b->ctas = int((long long)items.size() < cap ? (long long)items.size() : cap);
     }
     b->n_items = int(items.size());
@@ -1078,7 +1109,8 @@ int64_t lbm_batch_kernel_launches(const lbm_batch* b) { return b ? b->launches :
 
 int32_t lbm_batch_step_kernel_used(const lbm_batch* b) {
     if (!b) return LBM_KERNEL_AUTO;
-    return b->ymarch ? LBM_KERNEL_YMARCH : LBM_KERNEL_TILE;
+    if (b->ymarch) return LBM_KERNEL_YMARCH;
+    return b->pair ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE;
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }

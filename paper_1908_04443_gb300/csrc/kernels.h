@@ -24,6 +24,7 @@ struct DevParams {
     const int* wall_id;          // per node: index into kappa_w (valid at wall nodes)
     const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL | T_BULK
     const uint8_t* tile_solid;   // per tile of the step kernel's grid: a solid node within the tile + 3-node halo
+    const uint8_t* pair_solid;   // the same per tile of the FP32 pair kernel; null: FP32 steps use the tile kernel
     unsigned* err;               // sticky device error flags
 };
 
@@ -71,6 +72,13 @@ cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, 
 // instance of the batch; each instance reads f[parity] and writes f[parity ^ 1].
 cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& phys, const BatchInstance* insts,
                                 const BatchItem* items, int n_items, int ctas, cudaStream_t s);
+// D2Q9 FP32 step with two nodes per thread (packed FP32x2 arithmetic) on 32 x 16 tiles: one
+// grid (tile flags p.pair_solid) or a persistent grid of `ctas` CTAs walking (instance, tile) items.
+cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cudaStream_t s);
+cudaError_t launch_pair_batched(int parity, const DevParams& phys, const BatchItem* items, int n_items, int ctas,
+                                cudaStream_t s);
+void pair_tile_shape(int* tx, int* ty);
+int pair_ctas_per_sm();
 // D2Q9 y-march step: `ctas` persistent CTAs of ymarch_threads(prec) threads; CTA c walks the runs
 // items[begin[c] .. begin[c + 1]), each reading f[parity] of its grid and writing f[parity ^ 1].
 cudaError_t launch_ymarch(int prec, int parity, const DevParams& phys, const BatchItem* items, const int* begin,

@@ -677,6 +677,7 @@ static cudaError_t dispatch(int lat, int prec, const void* fin, void* fout, cons
 }
 
 cudaError_t launch_step(int lat, int prec, const void* fin, void* fout, const DevParams& p, cudaStream_t s) {
+    if (lat == LAT_D2Q9 && prec == PREC_FP32 && p.pair_solid) return launch_pair_step(fin, fout, p, s);
     return dispatch<0>(lat, prec, fin, fout, p, nullptr, nullptr, s);
 }
 

@@ -42,18 +42,6 @@ struct YSmem {
     uint8_t type[8][TW + 8];  // cell hx at index hx + 1 (x = x0 + index - 3)
 };
 
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async(double* dst, const double* src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
-
 // One run: columns x0 .. x0 + TW - 5 (those below nx), rows yb .. ye - 1.
 template <class S, bool SOLID>
 __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restrict__ fout, const Geo& g,

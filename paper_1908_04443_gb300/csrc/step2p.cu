@@ -1,0 +1,474 @@
+// D2Q9 FP32 time step with two nodes per thread and packed FP32x2 arithmetic.
+//
+// A CTA of 32 x 8 threads owns a 32 x 16 tile; thread (lx, ly) owns the nodes (x0 + lx, y0 + ly)
+// and (x0 + lx, y0 + ly + 8).  Every per-node quantity of the pair is one float2 and the arithmetic
+// of the step (density, pseudopotential, force, velocity, MRT collision) runs on both nodes at once
+// through the packed FP32 instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn), which do two IEEE
+// single-precision operations per instruction.  The phases are those of the scalar tile kernel:
+//   0. node types of the tile + 3-node halo into shared memory (tiles holding a solid node);
+//   1. pull (Eq. 3, halfway bounce-back of Fig. 3) of the two own nodes into registers and of the
+//      tile's 1-node halo ring (one cell per thread of the first 100 threads, copied with cp.async
+//      into shared memory so that its loads are in flight with the own nodes'); density (Eq. 4)
+//      and psi (Eq. 6) into shared memory; wall cells queued; the 2-node ring where a wall needs it;
+//   2. virtual wall densities (Eqs. 16-17 with the limiter, or the constant one) and their psi;
+//   3. F_m (Eq. 5), u (Eq. 4), the MRT collision with the consistency source (Eqs. 2, 7) in the
+//      increment form f += M^-1 (m* - m), and coalesced stores of f*.
+// The arithmetic is the scalar kernels' (same operations, regrouped): results agree with them to
+// FP32 rounding, not bit for bit.
+#include <cmath>
+
+#include "kernels.h"
+#include "lattice.cuh"
+#include "tile_common.cuh"
+
+namespace lbmwet {
+
+namespace {
+
+constexpr int PTX = 32, PTY = 8, PNY = 16;   // threads x, threads y, tile rows (two per thread)
+
+// ---- packed pair arithmetic ----------------------------------------------------------------
+struct V2 {
+    float2 v;
+};
+__device__ __forceinline__ V2 bc(float a) { return {make_float2(a, a)}; }
+__device__ __forceinline__ V2 mk(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ V2 operator*(float s, V2 b) { return {__fmul2_rn(make_float2(s, s), b.v)}; }
+__device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ V2 fma2(float s, V2 b, V2 c) { return {__ffma2_rn(make_float2(s, s), b.v, c.v)}; }
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return fma2(-1.0f, b, a); }
+__device__ __forceinline__ V2 operator-(V2 a) { return -1.0f * a; }
+__device__ __forceinline__ V2 div2(V2 a, V2 b) { return mk(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
+
+// Collision constants folded with the row norms of M: a_k = (m*_k - m_k) / |row_k|^2.
+struct PairRates {
+    float ke1, ke2, ke3;    // a1 = ke1 (m1 - e_eq) + ke2 u.F + ke3 X
+    float kp1, kp2, kp3;    // a2 = kp1 (m2 - eps_eq) + kp2 u.F + kp3 X
+    float kq1, kq2;         // a4 = kq1 (m4 + rho ux) + kq2 Fx (a6 likewise)
+    float kn1, kn2;         // a7 = kn1 (m7 - rho (ux^2 - uy^2)) + kn2 (ux Fx - uy Fy); a8 = kn1 (m8 - rho ux uy) + kn2/2 (ux Fy + uy Fx)
+};
+
+PairRates make_pair_rates(const DevParams& p) {
+    PairRates r;
+    const double he = 1.0 - 0.5 * p.s_e, hp = 1.0 - 0.5 * p.s_eps, hq = 1.0 - 0.5 * p.s_q, hn = 1.0 - 0.5 * p.s_nu;
+    // row norms |row|^2: e 36, eps 36, q 12, pxx 4, pxy 4
+    r.ke1 = float(-p.s_e / 36.0);
+    r.ke2 = float(6.0 * he / 36.0);
+    r.ke3 = float(he * p.c_e / 36.0);
+    r.kp1 = float(-p.s_eps / 36.0);
+    r.kp2 = float(-6.0 * hp / 36.0);
+    r.kp3 = float(-hp * p.c_eps / 36.0);
+    r.kq1 = float(-p.s_q / 12.0);
+    r.kq2 = float(-hq / 12.0);
+    r.kn1 = float(-p.s_nu / 4.0);
+    r.kn2 = float(2.0 * hn / 4.0);
+    return r;
+}
+
+// psi of a pair (Eq. 6 with the C-S or PR pressure); a non-positive argument flags ERR_PSI on
+// the lanes in `check` and gives psi 0
+__device__ __forceinline__ V2 psi2(V2 rho, const Phys<float>& e, bool check_a, bool check_b, unsigned* err) {
+    V2 p;
+    if (e.eos_kind == 1) {
+        const V2 eta = e.b4 * rho;
+        const V2 om = bc(1.0f) - eta;
+        const V2 eta2 = eta * eta;
+        const V2 poly = fma2(eta2, bc(1.0f) - eta, bc(1.0f) + eta);   // 1 + eta + eta^2 - eta^3
+        const V2 num = (e.RT * rho) * poly;
+        const V2 den = (om * om) * om;
+        p = div2(num, den) - e.a * (rho * rho);
+    } else {
+        const V2 br = e.b * rho;
+        const V2 den2 = fma2(br, bc(2.0f) - br, bc(1.0f));           // 1 + 2 b rho - b^2 rho^2
+        p = div2(e.RT * rho, bc(1.0f) - br) - div2(e.aphi * (rho * rho), den2);
+    }
+    const V2 arg = e.two_over_G * fma2(-1.0f / 3.0f, rho, p);
+    V2 out;
+    out.v.x = arg.v.x > 0.0f ? arg.v.x * rsqrtf(arg.v.x) : 0.0f;
+    out.v.y = arg.v.y > 0.0f ? arg.v.y * rsqrtf(arg.v.y) : 0.0f;
+    if ((check_a && !(arg.v.x > 0.0f)) || (check_b && !(arg.v.y > 0.0f))) atomicOr(err, ERR_PSI);
+    return out;
+}
+
+// MRT collision (Eq. 2 with the source of Eq. 7) of a pair in deviation variables; f += M^-1 (m* - m)
+__device__ __forceinline__ void collide2(V2 (&f)[9], V2 drho, V2 rho, V2 ux, V2 uy, V2 Fx, V2 Fy, V2 X,
+                                         const PairRates& k) {
+    const V2 p13 = f[1] + f[3], p24 = f[2] + f[4], p57 = f[5] + f[7], p68 = f[6] + f[8];
+    const V2 s14 = p13 + p24, s58 = p57 + p68;
+    const V2 m7 = p13 - p24, m8 = p57 - p68;
+    const V2 m1 = fma2(-4.0f, f[0], fma2(2.0f, s58, -s14));
+    const V2 m2 = fma2(4.0f, f[0], fma2(-2.0f, s14, s58));
+    const V2 q57 = f[5] - f[7], q86 = f[8] - f[6];
+    const V2 m4 = fma2(2.0f, f[3] - f[1], q57 + q86);
+    const V2 m6 = fma2(2.0f, f[4] - f[2], q57 - q86);
+    // equilibria (deviation form) and sources
+    const V2 uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const V2 rhou2 = rho * (uxx + uyy);
+    const V2 uF = fma2(ux, Fx, uy * Fy);
+    const V2 e_eq = fma2(3.0f, rhou2, -2.0f * drho);
+    const V2 eps_eq = fma2(-3.0f, rhou2, drho);
+    const V2 a1 = fma2(k.ke3, X, fma2(k.ke2, uF, k.ke1 * (m1 - e_eq)));
+    const V2 a2 = fma2(k.kp3, X, fma2(k.kp2, uF, k.kp1 * (m2 - eps_eq)));
+    const V2 a4 = fma2(k.kq2, Fx, k.kq1 * fma2(rho, ux, m4));
+    const V2 a6 = fma2(k.kq2, Fy, k.kq1 * fma2(rho, uy, m6));
+    const V2 a7 = fma2(k.kn2, fma2(ux, Fx, -(uy * Fy)), k.kn1 * (m7 - rho * (uxx - uyy)));
+    const V2 a8 = fma2(0.5f * k.kn2, fma2(ux, Fy, uy * Fx), k.kn1 * (m8 - rho * uxy));
+    const V2 a3 = (1.0f / 6.0f) * Fx, a5 = (1.0f / 6.0f) * Fy;
+    // f += M^T diag(1/|row|^2) (m* - m)
+    const V2 b = fma2(-2.0f, a2, -a1), c = fma2(2.0f, a1, a2);
+    f[0] = fma2(4.0f, a2 - a1, f[0]);
+    const V2 r3 = fma2(-2.0f, a4, a3), r5 = fma2(-2.0f, a6, a5);
+    const V2 bp = b + a7, bm = b - a7;
+    f[1] = f[1] + (bp + r3);
+    f[3] = f[3] + (bp - r3);
+    f[2] = f[2] + (bm + r5);
+    f[4] = f[4] + (bm - r5);
+    const V2 t1 = a3 + a4, t2 = a5 + a6;
+    const V2 pp = t1 + t2, qq = t2 - t1;
+    const V2 cu = c + a8, cv = c - a8;
+    f[5] = f[5] + (cu + pp);
+    f[7] = f[7] + (cu - pp);
+    f[6] = f[6] + (cv + qq);
+    f[8] = f[8] + (cv - qq);
+}
+
+struct PairSmem {
+    static constexpr int RX = PTX + 4, RY = PNY + 4;   // density tile (2-node halo)
+    static constexpr int PX = PTX + 2, PY = PNY + 2;   // psi tile (1-node halo)
+    static constexpr int YX = PTX + 6, YY = PNY + 6;   // type tile (3-node halo)
+    static constexpr int SHELL = 2 * PX + 2 * (PY - 2);
+    uint8_t type[YY * YX];
+    float rho[RY * RX];
+    float psi[PY * PX];
+    float hst[9 * SHELL];     // the halo ring's pulled distributions, [a][ring cell]
+    short wall[PY * PX];
+    int nwall;
+};
+
+// The grid of a single-grid launch (kernel parameters); a batch passes its work record (shared
+// memory) with the same member names.  Members are read where they are used, so that nothing of
+// the grid needs a register across the tile's barriers.
+struct PairGrid {
+    int nx, ny, N;
+    const uint8_t* type;
+    const int* wall_id;
+    const double* kappa_w;
+    double kappa;
+    const void* f[2];
+};
+
+// One 32 x 16 tile with first node (x0, y0), reading g.f[parity] and writing g.f[parity ^ 1].
+// SOLID = false: no solid node within the tile + 3-node halo.  WRAP as in the scalar tile kernel:
+// 0 no periodic wrap, 1 a single wrap, 2 full modulo.
+template <bool SOLID, int WRAP, class G>
+__device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
+                                          int y0, unsigned* err, PairSmem& sm) {
+    using L = D2Q9;
+    constexpr int Q = 9, NT = PTX * PTY;
+    using Sm = PairSmem;
+    constexpr int RX = Sm::RX, PX = Sm::PX, PY = Sm::PY, YX = Sm::YX, YY = Sm::YY, SHELL = Sm::SHELL;
+    const int nx = g.nx, ny = g.ny, N = g.N;
+    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * PTX + lx;
+    const float* __restrict__ fin = static_cast<const float*>(g.f[parity]);
+    auto wr = [](int v, int n) { return WRAP == 0 ? v : (WRAP == 1 ? wrap1(v, n) : wrap_full(v, n)); };
+    auto tix = [](int cx, int cy) { return cy * YX + cx; };   // type cell of tile-relative (cx - 3, cy - 3)
+    auto rix = [](int cx, int cy) { return cy * RX + cx; };   // density cell of (cx - 2, cy - 2)
+    auto pix = [](int cx, int cy) { return cy * PX + cx; };   // psi cell of (cx - 1, cy - 1)
+
+    // 0. node types of the tile + 3-node halo; does the 1-node halo region hold a wall?
+    if (tid == 0) sm.nwall = 0;
+    bool tile_has_wall = false;
+    if constexpr (SOLID) {
+        int wall_seen = 0;
+        for (int i = tid; i < YX * YY; i += NT) {
+            const int cx = i % YX, cy = i / YX;
+            const uint8_t ty = g.type[wr(y0 + cy - 3, ny) * nx + wr(x0 + cx - 3, nx)];
+            sm.type[i] = ty;
+            if (cx >= 2 && cx < PTX + 4 && cy >= 2 && cy < PNY + 4 && (ty & T_WALL)) wall_seen = 1;
+        }
+        tile_has_wall = __syncthreads_or(wall_seen);
+    }
+    auto type_at = [&](int ti) -> uint8_t {
+        if constexpr (!SOLID) return uint8_t(T_BULK);
+        return sm.type[ti];
+    };
+    // source of every distribution streaming into node (gx, gy), handed to sink(a, pointer)
+    auto pull_src = [&](auto&& sink, int gx, int gy, int ti, uint8_t self) {
+        if constexpr (WRAP == 0) {
+            const float* p = fin + (gy * nx + gx);
+            if (!SOLID || (self & T_BULK)) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) sink(a, p + (a * N - L::ex(a) - L::ey(a) * nx));
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                    sink(a, p + (bb ? L::opp(a) * N : a * N - L::ex(a) - L::ey(a) * nx));
+                }
+            }
+        } else {
+            const int cx[3] = {wrap1(gx - 1, nx), gx, wrap1(gx + 1, nx)};
+            const int ry[3] = {wrap1(gy - 1, ny) * nx, gy * nx, wrap1(gy + 1, ny) * nx};
+            if (!SOLID || (self & T_BULK)) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) sink(a, fin + (a * N + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                    sink(a, fin + (bb ? L::opp(a) * N + ry[1] + cx[1]
+                                      : a * N + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
+                }
+            }
+        }
+    };
+
+    // 1. the halo-ring cell of this thread: its loads go out first (cp.async into shared memory)
+    using Ring = Shell<PX, PY, 1, 2>;
+    static_assert(Ring::COUNT == SHELL && SHELL <= NT, "one ring cell per thread");
+    const bool has_h = tid < SHELL;
+    uint8_t hty = uint8_t(T_SOLID);
+    int hpx = 0, hpy = 0;
+    if (has_h) {
+        int pz;
+        Ring::cell(tid, hpx, hpy, pz);
+        const int ti = tix(hpx + 2, hpy + 2);
+        hty = type_at(ti);
+        if (!(hty & T_SOLID))
+            pull_src([&](int a, const float* src) { cp_async(&sm.hst[a * SHELL + tid], src); },
+                     wr(x0 + hpx - 1, nx), wr(y0 + hpy - 1, ny), ti, hty);
+    }
+    cp_commit();
+    // the two own nodes: rows ly and ly + 8
+    const int gx = wr(x0 + lx, nx);
+    const int gya = wr(y0 + ly, ny), gyb = wr(y0 + ly + PTY, ny);
+    const int tia = tix(lx + 3, ly + 3), tib = tix(lx + 3, ly + PTY + 3);
+    const uint8_t ta = type_at(tia), tb = type_at(tib);
+    const bool fa = !(ta & T_SOLID), fb = !(tb & T_SOLID);
+    V2 f[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) f[a] = bc(0.0f);
+    if (fa) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gya, tia, ta);
+    if (fb) pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gyb, tib, tb);
+    V2 drho = f[0];
+#pragma unroll
+    for (int a = 1; a < Q; ++a) drho = drho + f[a];
+    {
+        const V2 rho = bc(ph.rho_ref) + drho;
+        const V2 ps = psi2(rho, ph, fa, fb, err);
+        sm.psi[pix(lx + 1, ly + 1)] = fa ? ps.v.x : 0.0f;
+        sm.psi[pix(lx + 1, ly + PTY + 1)] = fb ? ps.v.y : 0.0f;
+        if constexpr (SOLID) {
+            if (tile_has_wall) {
+                sm.rho[rix(lx + 2, ly + 2)] = fa ? rho.v.x : 0.0f;
+                sm.rho[rix(lx + 2, ly + PTY + 2)] = fb ? rho.v.y : 0.0f;
+            }
+            if (ta & T_WALL) sm.wall[atomicAdd(&sm.nwall, 1)] = short(pix(lx + 1, ly + 1));
+            if (tb & T_WALL) sm.wall[atomicAdd(&sm.nwall, 1)] = short(pix(lx + 1, ly + PTY + 1));
+        }
+    }
+    cp_wait<0>();
+    if (has_h) {
+        const int hpi = pix(hpx, hpy);
+        float hrho = 0.0f, hpsi = 0.0f;
+        if (!(hty & T_SOLID)) {
+            float d = sm.hst[tid];
+#pragma unroll
+            for (int a = 1; a < Q; ++a) d += sm.hst[a * SHELL + tid];
+            hrho = ph.rho_ref + d;
+            hpsi = psi2(bc(hrho), ph, true, false, err).v.x;   // the own nodes' formula
+        } else if (hty & T_WALL) {
+            sm.wall[atomicAdd(&sm.nwall, 1)] = short(hpi);
+        }
+        if (SOLID && tile_has_wall) sm.rho[rix(hpx + 1, hpy + 1)] = hrho;
+        sm.psi[hpi] = hpsi;
+    }
+    // the 2-node ring, only where Eq. 17 will need it
+    if constexpr (SOLID) {
+        if (tile_has_wall) {
+            using Ring2 = Shell<RX, PNY + 4, 1, 2>;
+            for (int k = tid; k < Ring2::COUNT; k += NT) {
+                int rx, ry, rz;
+                Ring2::cell(k, rx, ry, rz);
+                const int ti = tix(rx + 1, ry + 1);
+                const uint8_t ty = sm.type[ti];
+                float rho = 0.0f;
+                if (!(ty & T_SOLID)) {
+                    float d = 0.0f;
+                    int first = 1;
+                    pull_src(
+                        [&](int a, const float* src) {
+                            (void)a;
+                            d = first ? *src : d + *src;
+                            first = 0;
+                        },
+                        wr(x0 + rx - 2, nx), wr(y0 + ry - 2, ny), ti, ty);
+                    rho = ph.rho_ref + d;
+                }
+                sm.rho[rix(rx, ry)] = rho;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 2. wall cells of the tile + 1-node halo: virtual density and its psi
+    if constexpr (SOLID) {
+        const int nwall = sm.nwall;
+        if (nwall > 0) {
+            for (int k = tid; k < nwall; k += NT) {
+                const int i = sm.wall[k];
+                const int px = i % PX, py = i / PX;
+                const int ti = tix(px + 2, py + 2);
+                float rw;
+                if (ph.wall_kind == 1) {
+                    rw = ph.rho_w_const;
+                } else {
+                    // Eq. 17: weighted mean of the fluid neighbours' densities
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int ex = L::ex(a), ey = L::ey(a);
+                        if (!(sm.type[ti + ex + ey * YX] & T_SOLID)) {
+                            num += float(L::wf(a)) * sm.rho[rix(px + 1 + ex, py + 1 + ey)];
+                            den += float(L::wf(a));
+                        }
+                    }
+                    const float rho_ave = cdiv(num, den);
+                    const float kap = g.kappa_w ? float(g.kappa_w[g.wall_id[wr(y0 + py - 1, ny) * nx + wr(x0 + px - 1, nx)]])
+                                                : float(g.kappa);
+                    // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                    const float raw = (kap >= 0.0f) ? (1.0f + kap) * rho_ave : rho_ave + kap;
+                    rw = raw > ph.rho_l ? ph.rho_l : raw;
+                    rw = rw < ph.rho_g ? ph.rho_g : rw;
+                }
+                sm.psi[i] = psi2(bc(rw), ph, true, false, err).v.x;
+            }
+            __syncthreads();
+        }
+    }
+
+    // 3. force, velocity, collision and store of the pair
+    const bool va = x0 + lx < nx && y0 + ly < ny && fa;
+    const bool vb = x0 + lx < nx && y0 + ly + PTY < ny && fb;
+    if (!va && !vb) return;
+    const int pca = pix(lx + 1, ly + 1), pcb = pix(lx + 1, ly + PTY + 1);
+    auto psi_pair = [&](int off) { return mk(sm.psi[pca + off], sm.psi[pcb + off]); };
+    const V2 psi_c = psi_pair(0);
+    // sum_a w_a psi(x + e_a) e_a over opposite pairs: w_a e_a (psi(x + e_a) - psi(x - e_a))
+    const V2 w1 = (1.0f / 3.0f) * (psi_pair(1) - psi_pair(-1));                  // e = (1, 0)
+    const V2 w2 = (1.0f / 3.0f) * (psi_pair(PX) - psi_pair(-PX));                // e = (0, 1)
+    const V2 w5 = (1.0f / 12.0f) * (psi_pair(PX + 1) - psi_pair(-PX - 1));       // e = (1, 1)
+    const V2 w6 = (1.0f / 12.0f) * (psi_pair(PX - 1) - psi_pair(-PX + 1));       // e = (-1, 1)
+    const V2 sx = (w1 + w5) - w6, sy = (w2 + w5) + w6;
+    // Eq. 5
+    const V2 gpsi = (-ph.G) * psi_c;
+    const V2 Fmx = gpsi * sx, Fmy = gpsi * sy;
+    const V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy);
+    const V2 jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+    const V2 jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+    const V2 rho = bc(ph.rho_ref) + drho;
+    if ((va && !(rho.v.x > 0.0f)) || (vb && !(rho.v.y > 0.0f))) atomicOr(err, ERR_RHO);
+    // Eq. 4: rho u = sum e f + F/2
+    const V2 inv = div2(bc(1.0f), rho);
+    const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv;
+    const V2 X = div2(fma2(Fmx, Fmx, Fmy * Fmy), psi_c * psi_c);
+    collide2(f, drho, rho, ux, uy, Fx, Fy, X, kr);
+    const int gia = (y0 + ly) * nx + x0 + lx, gib = gia + PTY * nx;
+    float* __restrict__ fout = static_cast<float*>(const_cast<void*>(g.f[parity ^ 1]));
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (va) fout[a * N + gia] = f[a].v.x;
+        if (vb) fout[a * N + gib] = f[a].v.y;
+    }
+}
+
+template <bool SOLID, class G>
+__device__ __forceinline__ void pair_tile(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
+                                          int y0, unsigned* err, PairSmem& sm) {
+    int w;
+    if (g.nx < PTX + 8 || g.ny < PNY + 8) w = 2;
+    else w = (x0 >= 3 && x0 + PTX + 2 < g.nx && y0 >= 3 && y0 + PNY + 2 < g.ny) ? 0 : 1;
+    if (w == 0) pair_body<SOLID, 0>(g, parity, ph, kr, x0, y0, err, sm);
+    else if (w == 1) pair_body<SOLID, 1>(g, parity, ph, kr, x0, y0, err, sm);
+    else pair_body<SOLID, 2>(g, parity, ph, kr, x0, y0, err, sm);
+}
+
+#ifndef LBMWET_PAIR_MINB
+#define LBMWET_PAIR_MINB 4
+#endif
+
+__global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
+    pair_step(PairGrid g, const uint8_t* __restrict__ tile_solid, Phys<float> ph, PairRates kr, unsigned* err) {
+    __shared__ PairSmem sm;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const bool solid = tile_solid ? tile_solid[tile] != 0 : true;
+    if (solid) pair_tile<true>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm);
+    else pair_tile<false>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm);
+}
+
+// Persistent form: CTAs walk the (instance, tile) list; the next record is fetched during a tile.
+__global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
+    pair_step_batched(int parity, const BatchItem* __restrict__ items, int n_items, Phys<float> ph, PairRates kr,
+                      unsigned* err) {
+    constexpr int WORDS = int(sizeof(BatchItem) / 4);
+    __shared__ PairSmem sm;
+    __shared__ BatchItem s_item[2];
+    const int tid = threadIdx.y * PTX + threadIdx.x;
+    if (tid < WORDS && blockIdx.x < n_items)
+        reinterpret_cast<uint32_t*>(&s_item[0])[tid] = reinterpret_cast<const uint32_t*>(&items[blockIdx.x])[tid];
+    __syncthreads();
+    int slot = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem& item = s_item[slot];
+        const int next = it + gridDim.x;
+        // the next record is copied into the other slot (cp.async, no registers) during this tile
+        if (tid < WORDS && next < n_items)
+            cp_async(reinterpret_cast<float*>(&s_item[slot ^ 1]) + tid, reinterpret_cast<const float*>(&items[next]) + tid);
+        cp_commit();
+        if (item.solid) pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm);
+        else pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm);
+        cp_wait<0>();
+        __syncthreads();   // the next record is visible; this tile's threads are done with shared memory
+        slot ^= 1;
+    }
+}
+
+}  // namespace
+
+void pair_tile_shape(int* tx, int* ty) {
+    *tx = PTX;
+    *ty = PNY;
+}
+
+int pair_ctas_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_step_batched, PTX * PTY, 0) != cudaSuccess) n = 1;
+    return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cudaStream_t s) {
+    PairGrid g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.N = int(p.N);
+    g.type = p.type;
+    g.wall_id = p.wall_id;
+    g.kappa_w = p.kappa_w;
+    g.kappa = p.kappa;
+    g.f[0] = fin;
+    g.f[1] = fout;
+    dim3 grid((p.nx + PTX - 1) / PTX, (p.ny + PNY - 1) / PNY, 1);
+    pair_step<<<grid, dim3(PTX, PTY, 1), 0, s>>>(g, p.pair_solid, make_phys<float>(p), make_pair_rates(p), p.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_batched(int parity, const DevParams& p, const BatchItem* items, int n_items, int ctas,
+                                cudaStream_t s) {
+    pair_step_batched<<<ctas, dim3(PTX, PTY, 1), 0, s>>>(parity, items, n_items, make_phys<float>(p),
+                                                         make_pair_rates(p), p.err);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmwet

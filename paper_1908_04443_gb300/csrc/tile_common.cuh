@@ -131,6 +131,20 @@ struct Shell {
     }
 };
 
+// Asynchronous global -> shared copies of one element (cp.async, 4 or 8 bytes), their commit
+// groups and the wait for all but PENDING of the thread's groups.
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
 __device__ __forceinline__ int wrap_full(int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;

@@ -251,11 +251,11 @@ def lbm_kernel_launches(h) -> int:
     return int(_lib.lbm_kernel_launches(h))
 
 
-KERNEL_NAMES = {0: "auto", 1: "tile", 2: "ymarch"}
+KERNEL_NAMES = {0: "auto", 1: "tile", 2: "ymarch", 3: "pair"}
 
 
 def lbm_step_kernel_used(h) -> str:
-    """"tile" or "ymarch" (D2Q9), "auto" for D3Q19 (its z-march)."""
+    """"tile", "ymarch" or "pair" (D2Q9), "auto" for D3Q19 (its z-march)."""
     return KERNEL_NAMES[int(_lib.lbm_step_kernel_used(h))]
 
 
@@ -355,8 +355,8 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
                 rho_l=0.0, rho_g=0.0, rho_ref=0.0, body_force=(0.0, 0.0, 0.0), wall="IVD", kappa=0.0,
                 rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0), step_kernel="auto") -> lbm_config:
     """Build an lbm_config.  `shape` is the numpy shape (ny, nx) or (nz, ny, nx).  `body` is
-    ("ball", center, radius) or ("plane", wall_y) or None.  `step_kernel` is "auto", "tile" or
-    "ymarch" (D2Q9 work decomposition; results are the same)."""
+    ("ball", center, radius) or ("plane", wall_y) or None.  `step_kernel` is "auto", "tile",
+    "ymarch" or "pair" (D2Q9 work decomposition, see lbm_step_kernel in the header)."""
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
     else:
@@ -375,7 +375,7 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
     cfg.wall_kind = {"IVD": LBM_WALL_IVD, "VD": LBM_WALL_VD}[wall]
     cfg.kappa = kappa
     cfg.rho_w_const = rho_w_const
-    cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2}[step_kernel]
+    cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2, "pair": 3}[step_kernel]
     cfg.body_kind = LBM_BODY_NONE
     if body is not None:
         if body[0] == "ball":

@@ -81,6 +81,8 @@ def test_automatic_choice_and_record():
     from paper_1908_04443_gb300 import lbmwet as L
     small = drop_on_cylinder((100, 100), (50.0, 50.0), 20.0, (50.0, 95.0), 25.0)
     with small.gpu("fp32") as sim:
+        assert sim.step_kernel() == "pair"
+    with small.gpu("fp64") as sim:
         assert sim.step_kernel() == "tile"
     shape = (1024, 1024)
     big = drop_on_cylinder(shape, (512.0, 300.0), 100.0, (512.0, 470.0), 80.0, step_kernel="ymarch")
