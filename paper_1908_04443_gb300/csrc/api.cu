@@ -1,5 +1,8 @@
 // C ABI of lbmwet (see include/lbmwet.h): handle life cycle, the step driver (CUDA-graph chunks of
 // fused step kernels), observables, state transfer and checkpoints.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,6 +99,38 @@ std::vector<uint8_t> tile_solid_flags(const uint8_t* mask, int nx, int ny, int n
     return out;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// TMA tensor map of one FP32 D2Q9 distribution buffer: dimensions (x, y, direction), the pair
+// kernel's box.  False where TMA cannot address the buffer (rows not a multiple of 16 bytes).
+bool encode_pair_map(CUtensorMap* m, void* f, int nx, int ny) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || nx % 4 != 0) return false;
+    int bx, by;
+    pair_box_dims(&bx, &by);
+    const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
+    const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * cuuint64_t(ny) * 4};
+    const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 lbm_status fail(lbm_handle* h, lbm_status s, const std::string& msg) {
     if (h) h->err = msg;
     else g_init_error = msg;
@@ -147,6 +182,7 @@ lbm_status check_device_error(lbm_handle* h) {
         std::string m = "device flagged:";
         if (flags & ERR_PSI) m += " non-positive square-root argument in Eq. 6;";
         if (flags & ERR_RHO) m += " non-positive or non-finite density;";
+        if (flags & ERR_TIMEOUT) m += " a wait for a shared-memory copy gave up;";
         return fail(h, LBM_ERR_UNSTABLE, m);
     }
     return LBM_OK;
@@ -836,6 +872,7 @@ struct lbm_batch {
     BatchInstance* d_insts = nullptr;
     BatchItem* d_items = nullptr;
     int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
+    void* d_tmaps = nullptr;           // pair kernel: two TMA tensor maps per instance
     bool ymarch = false;
     bool pair = false;                 // FP32 pair kernel (else the tile kernel, unless y-march)
     int n_items = 0, ctas = 1, cur = 0;
@@ -878,6 +915,7 @@ void batch_free(lbm_batch* b) {
     cudaFree(b->d_insts);
     cudaFree(b->d_items);
     cudaFree(b->d_begin);
+    cudaFree(b->d_tmaps);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -1011,6 +1049,30 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         int tx, ty, tz;
         step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
         if (b->pair) pair_tile_shape(&tx, &ty);
+        // pair kernel: TMA tensor maps of every instance whose rows TMA can address
+        std::vector<char> has_map(n, 0);
+        if (b->pair) {
+            std::vector<CUtensorMap> maps(2 * (size_t)n);
+            bool any = false;
+            for (int i = 0; i < n; ++i) {
+                lbm_handle* h = b->inst[i];
+                has_map[i] = encode_pair_map(&maps[2 * i], h->f[0], h->cfg.nx, h->cfg.ny) &&
+                             encode_pair_map(&maps[2 * i + 1], h->f[1], h->cfg.nx, h->cfg.ny);
+                any = any || has_map[i];
+            }
+            if (any) {
+                cudaError_t e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size());
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                        cudaMemcpyHostToDevice, b->stream);
+                if (e != cudaSuccess) {
+                    const std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
+                    batch_free(b);
+                    delete b;
+                    return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+                }
+            }
+        }
         for (int i = 0; i < n; ++i) {
             lbm_handle* h = b->inst[i];
             BatchInstance& d = insts[i];
@@ -1042,6 +1104,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
                     it.wall_id = h->d_wall_id;
                     it.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
                     it.kappa = h->dp.kappa;
+                    it.tmap = has_map[i] ? static_cast<const char*>(b->d_tmaps) + 2 * sizeof(CUtensorMap) * i
+                                         : nullptr;
                     items.push_back(it);
                 }
         }
@@ -1085,6 +1149,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
     unsigned flags = 0;
     CKB(b, cudaMemcpyAsync(&flags, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
     CKB(b, cudaStreamSynchronize(b->stream));
+    if (flags & ERR_TIMEOUT) return bfail(b, LBM_ERR_CUDA, "a wait for a shared-memory copy gave up");
     if (flags) return bfail(b, LBM_ERR_UNSTABLE, "device flagged a non-positive square-root argument or density");
     return LBM_OK;
 }

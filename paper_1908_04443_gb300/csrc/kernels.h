@@ -49,6 +49,8 @@ struct BatchItem {
     const int* wall_id;
     const double* kappa_w;
     double kappa;
+    const void* tmap;               // FP32 pair kernel: the instance's two TMA tensor maps (128 bytes
+                                    // each, for f[0] and f[1]) or null
 };
 static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem is copied as 32-bit words");
 
@@ -78,6 +80,9 @@ cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cu
 cudaError_t launch_pair_batched(int parity, const DevParams& phys, const BatchItem* items, int n_items, int ctas,
                                 cudaStream_t s);
 void pair_tile_shape(int* tx, int* ty);
+// Box (x extent, y extent; all 9 directions) of the pair kernel's TMA load: a tile and the cells its
+// pulls read, with x starting 4 cells before the tile (a 16-byte boundary).
+void pair_box_dims(int* bx, int* by);
 int pair_ctas_per_sm();
 // D2Q9 y-march step: `ctas` persistent CTAs of ymarch_threads(prec) threads; CTA c walks the runs
 // items[begin[c] .. begin[c + 1]), each reading f[parity] of its grid and writing f[parity ^ 1].

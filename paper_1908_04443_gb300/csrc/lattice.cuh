@@ -18,7 +18,7 @@
 namespace lbmwet {
 
 enum : uint8_t { T_SOLID = 1, T_WALL = 2, T_NEARWALL = 4, T_BULK = 8 };  // BULK: fluid, all neighbours fluid
-enum : unsigned { ERR_PSI = 1u, ERR_RHO = 2u, ERR_NONFINITE = 4u };
+enum : unsigned { ERR_PSI = 1u, ERR_RHO = 2u, ERR_NONFINITE = 4u, ERR_TIMEOUT = 8u };
 
 struct D2Q9 {
     static constexpr int Q = 9, D = 2;

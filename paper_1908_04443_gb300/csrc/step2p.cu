@@ -134,6 +134,18 @@ __device__ __forceinline__ void collide2(V2 (&f)[9], V2 drho, V2 rho, V2 ux, V2 
     f[8] = f[8] + (cv - qq);
 }
 
+// The TMA box of a tile: every direction's values over x0 - 4 .. x0 + 35, y0 - 2 .. y0 + 17 (the
+// tile, its halo ring and the ring's upstream cells), [a][y][x].
+struct PairBox {
+    static constexpr int BX = PTX + 8, BY = PNY + 4, X0 = 4, Y0 = 2;
+    static constexpr int ELEMS = 9 * BY * BX;
+    static_assert(PTX % 4 == 0, "x0 - 4 must be a 16-byte boundary");
+};
+
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
 struct PairSmem {
     static constexpr int RX = PTX + 4, RY = PNY + 4;   // density tile (2-node halo)
     static constexpr int PX = PTX + 2, PY = PNY + 2;   // psi tile (1-node halo)
@@ -162,9 +174,15 @@ struct PairGrid {
 // One 32 x 16 tile with first node (x0, y0), reading g.f[parity] and writing g.f[parity ^ 1].
 // SOLID = false: no solid node within the tile + 3-node halo.  WRAP as in the scalar tile kernel:
 // 0 no periodic wrap, 1 a single wrap, 2 full modulo.
-template <bool SOLID, int WRAP, class G>
+// box: the tile's PairBox already in shared memory (tiles without solids and without wrap), or
+// null.  pre() runs once in every thread right after the halo ring's copies are issued; its own
+// cp.async copies form the one commit group the phase does not wait for.  hook() runs once in every
+// thread right after the barrier that ends phase 1 (the box and the halo staging are free from then
+// on).
+template <bool SOLID, int WRAP, class G, class Pre = NoHook, class Hook = NoHook>
 __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
-                                          int y0, unsigned* err, PairSmem& sm) {
+                                          int y0, unsigned* err, PairSmem& sm, const float* box = nullptr,
+                                          const Pre& pre = Pre(), const Hook& hook = Hook()) {
     using L = D2Q9;
     constexpr int Q = 9, NT = PTX * PTY;
     using Sm = PairSmem;
@@ -227,7 +245,9 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
 
     // 1. the halo-ring cell of this thread: its loads go out first (cp.async into shared memory)
     using Ring = Shell<PX, PY, 1, 2>;
+    using B = PairBox;
     static_assert(Ring::COUNT == SHELL && SHELL <= NT, "one ring cell per thread");
+    const bool boxed = !SOLID && WRAP == 0 && box != nullptr;
     const bool has_h = tid < SHELL;
     uint8_t hty = uint8_t(T_SOLID);
     int hpx = 0, hpy = 0;
@@ -236,10 +256,12 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
         Ring::cell(tid, hpx, hpy, pz);
         const int ti = tix(hpx + 2, hpy + 2);
         hty = type_at(ti);
-        if (!(hty & T_SOLID))
+        if (!boxed && !(hty & T_SOLID))
             pull_src([&](int a, const float* src) { cp_async(&sm.hst[a * SHELL + tid], src); },
                      wr(x0 + hpx - 1, nx), wr(y0 + hpy - 1, ny), ti, hty);
     }
+    cp_commit();
+    pre();
     cp_commit();
     // the two own nodes: rows ly and ly + 8
     const int gx = wr(x0 + lx, nx);
@@ -248,10 +270,18 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     const uint8_t ta = type_at(tia), tb = type_at(tib);
     const bool fa = !(ta & T_SOLID), fb = !(tb & T_SOLID);
     V2 f[Q];
+    if (boxed) {
+        // node (x, y), direction a: the value at (x - e_a, y - e_a) of the box
 #pragma unroll
-    for (int a = 0; a < Q; ++a) f[a] = bc(0.0f);
-    if (fa) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gya, tia, ta);
-    if (fb) pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gyb, tib, tb);
+        for (int a = 0; a < Q; ++a)
+            f[a] = mk(box[(a * B::BY + ly + B::Y0 - L::ey(a)) * B::BX + lx + B::X0 - L::ex(a)],
+                      box[(a * B::BY + ly + PTY + B::Y0 - L::ey(a)) * B::BX + lx + B::X0 - L::ex(a)]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = bc(0.0f);
+        if (fa) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gya, tia, ta);
+        if (fb) pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gyb, tib, tb);
+    }
     V2 drho = f[0];
 #pragma unroll
     for (int a = 1; a < Q; ++a) drho = drho + f[a];
@@ -269,14 +299,24 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
             if (tb & T_WALL) sm.wall[atomicAdd(&sm.nwall, 1)] = short(pix(lx + 1, ly + PTY + 1));
         }
     }
-    cp_wait<0>();
+    cp_wait<1>();   // the halo ring (and anything older), not pre()'s copies
     if (has_h) {
         const int hpi = pix(hpx, hpy);
         float hrho = 0.0f, hpsi = 0.0f;
         if (!(hty & T_SOLID)) {
-            float d = sm.hst[tid];
+            float h[Q];
+            if (boxed) {
+                // ring cell (x0 + hpx - 1, y0 + hpy - 1)
 #pragma unroll
-            for (int a = 1; a < Q; ++a) d += sm.hst[a * SHELL + tid];
+                for (int a = 0; a < Q; ++a)
+                    h[a] = box[(a * B::BY + hpy - 1 + B::Y0 - L::ey(a)) * B::BX + hpx - 1 + B::X0 - L::ex(a)];
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) h[a] = sm.hst[a * SHELL + tid];
+            }
+            float d = h[0];
+#pragma unroll
+            for (int a = 1; a < Q; ++a) d += h[a];
             hrho = ph.rho_ref + d;
             hpsi = psi2(bc(hrho), ph, true, false, err).v.x;   // the own nodes' formula
         } else if (hty & T_WALL) {
@@ -312,6 +352,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
         }
     }
     __syncthreads();
+    hook();
 
     // 2. wall cells of the tile + 1-node halo: virtual density and its psi
     if constexpr (SOLID) {
@@ -384,15 +425,19 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     }
 }
 
-template <bool SOLID, class G>
+__host__ __device__ __forceinline__ int pair_wrap(int x0, int y0, int nx, int ny) {
+    if (nx < PTX + 8 || ny < PNY + 8) return 2;
+    return (x0 >= 3 && x0 + PTX + 2 < nx && y0 >= 3 && y0 + PNY + 2 < ny) ? 0 : 1;
+}
+
+template <bool SOLID, class G, class Pre = NoHook, class Hook = NoHook>
 __device__ __forceinline__ void pair_tile(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
-                                          int y0, unsigned* err, PairSmem& sm) {
-    int w;
-    if (g.nx < PTX + 8 || g.ny < PNY + 8) w = 2;
-    else w = (x0 >= 3 && x0 + PTX + 2 < g.nx && y0 >= 3 && y0 + PNY + 2 < g.ny) ? 0 : 1;
-    if (w == 0) pair_body<SOLID, 0>(g, parity, ph, kr, x0, y0, err, sm);
-    else if (w == 1) pair_body<SOLID, 1>(g, parity, ph, kr, x0, y0, err, sm);
-    else pair_body<SOLID, 2>(g, parity, ph, kr, x0, y0, err, sm);
+                                          int y0, unsigned* err, PairSmem& sm, const float* box = nullptr,
+                                          const Pre& pre = Pre(), const Hook& hook = Hook()) {
+    const int w = pair_wrap(x0, y0, g.nx, g.ny);
+    if (w == 0) pair_body<SOLID, 0>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
+    else if (w == 1) pair_body<SOLID, 1>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
+    else pair_body<SOLID, 2>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
 }
 
 #ifndef LBMWET_PAIR_MINB
@@ -408,31 +453,84 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     else pair_tile<false>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm);
 }
 
-// Persistent form: CTAs walk the (instance, tile) list; the next record is fetched during a tile.
+// Polls of an mbarrier before a wait gives up (flags ERR_TIMEOUT and goes on); far above any copy's
+// latency.
+constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
+
+// Persistent form: CTAs walk the (instance, tile) list.  Work records sit in a ring of three shared
+// slots: the current tile's, the next tile's, and the one after, whose copy (cp.async) is issued
+// during this tile and not waited for until the next.  A tile without solids and without wrap, of a
+// grid with TMA tensor maps, pulls from a box that one TMA load brings into shared memory while the
+// previous tile finishes (issued right after that tile's phase 1, when the box is free).
 __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     pair_step_batched(int parity, const BatchItem* __restrict__ items, int n_items, Phys<float> ph, PairRates kr,
                       unsigned* err) {
     constexpr int WORDS = int(sizeof(BatchItem) / 4);
     __shared__ PairSmem sm;
-    __shared__ BatchItem s_item[2];
+    __shared__ alignas(128) float box[PairBox::ELEMS];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ BatchItem s_item[3];
     const int tid = threadIdx.y * PTX + threadIdx.x;
-    if (tid < WORDS && blockIdx.x < n_items)
-        reinterpret_cast<uint32_t*>(&s_item[0])[tid] = reinterpret_cast<const uint32_t*>(&items[blockIdx.x])[tid];
-    __syncthreads();
-    int slot = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const BatchItem& item = s_item[slot];
-        const int next = it + gridDim.x;
-        // the next record is copied into the other slot (cp.async, no registers) during this tile
-        if (tid < WORDS && next < n_items)
-            cp_async(reinterpret_cast<float*>(&s_item[slot ^ 1]) + tid, reinterpret_cast<const float*>(&items[next]) + tid);
-        cp_commit();
-        if (item.solid) pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm);
-        else pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm);
-        cp_wait<0>();
-        __syncthreads();   // the next record is visible; this tile's threads are done with shared memory
-        slot ^= 1;
+    const int grid = gridDim.x;
+    if (tid < WORDS) {
+        if (blockIdx.x < n_items)
+            reinterpret_cast<uint32_t*>(&s_item[0])[tid] = reinterpret_cast<const uint32_t*>(&items[blockIdx.x])[tid];
+        if (blockIdx.x + grid < n_items)
+            reinterpret_cast<uint32_t*>(&s_item[1])[tid] =
+                reinterpret_cast<const uint32_t*>(&items[blockIdx.x + grid])[tid];
     }
+    if (tid == 0) {
+        mbar_init(&bar);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto boxed = [](const BatchItem& r) {
+        return r.tmap != nullptr && !r.solid && pair_wrap(r.x0, r.y0, r.nx, r.ny) == 0;
+    };
+    auto issue = [&](const BatchItem& r) {
+        const char* maps = static_cast<const char*>(r.tmap);
+        tma_load_box(box, maps + 128 * parity, r.x0 - PairBox::X0, r.y0 - PairBox::Y0, 0, &bar,
+                     unsigned(PairBox::ELEMS * sizeof(float)));
+    };
+    unsigned phase = 0;
+    bool cur_boxed = blockIdx.x < n_items && boxed(s_item[0]);
+    if (cur_boxed && tid == 0) issue(s_item[0]);
+    int s0 = 0, s1 = 1, s2 = 2;   // ring slots of the current, next and after-next records
+    for (int it = blockIdx.x; it < n_items; it += grid) {
+        const BatchItem& item = s_item[s0];
+        const BatchItem& nxt = s_item[s1];
+        const int far = it + 2 * grid;
+        auto pre = [&]() {
+            if (tid < WORDS && far < n_items)
+                cp_async(reinterpret_cast<float*>(&s_item[s2]) + tid, reinterpret_cast<const float*>(&items[far]) + tid);
+        };
+        bool next_boxed = false;
+        auto hook = [&]() {
+            next_boxed = it + grid < n_items && boxed(nxt);
+            if (next_boxed && tid == 0) {
+                fence_proxy_async();
+                issue(nxt);
+            }
+        };
+        if (item.solid) {
+            pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm, nullptr, pre, hook);
+        } else {
+            const float* bx = nullptr;
+            if (cur_boxed) {
+                if (!mbar_wait(&bar, phase, MBAR_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+                phase ^= 1u;
+                bx = box;
+            }
+            pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
+        }
+        __syncthreads();   // this tile's threads are done with shared memory
+        const int t = s0;
+        s0 = s1;
+        s1 = s2;
+        s2 = t;
+        cur_boxed = next_boxed;
+    }
+    cp_wait<0>();
 }
 
 }  // namespace
@@ -440,6 +538,11 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
 void pair_tile_shape(int* tx, int* ty) {
     *tx = PTX;
     *ty = PNY;
+}
+
+void pair_box_dims(int* bx, int* by) {
+    *bx = PairBox::BX;
+    *by = PairBox::BY;
 }
 
 int pair_ctas_per_sm() {
