@@ -41,7 +41,11 @@ UNIT = "MLUPS"
 
 # DRAM bytes per launch of the step kernel measured by ncu on the workload below, keyed by a hash
 # of the kernel sources: when the sources change the figure is stale and reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
+    # one launch (217,851,648 + 158,635,776 bytes)
+    ("c2", "fp32", "1f945383ba1f2191"): 376487424,
+}
 
 
 def kernel_hash() -> str:
