@@ -54,6 +54,15 @@ struct BatchItem {
 };
 static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem is copied as 32-bit words");
 
+// Column and chunk of the FP32 D3Q19 step kernels (z-march and z-pair march share the per-chunk
+// solid flags); compile-time, chosen by measurement.
+#ifndef LBMWET_Z3F_X
+#define LBMWET_Z3F_X 32
+#define LBMWET_Z3F_Y 4
+#define LBMWET_Z3F_Z 32
+#define LBMWET_Z3F_MINB 3
+#endif
+
 enum Lat { LAT_D2Q9 = 0, LAT_D3Q19 = 1 };
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1 };
 
@@ -95,6 +104,9 @@ struct Geo;
 cudaError_t launch_step3d(int prec, int mode, const void* fin, void* fout, const Geo& g, const DevParams& p,
                           double* rho, double* u, cudaStream_t s);
 void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz);
+// D3Q19 FP32 step as a z-pair march (two planes per thread, packed FP32x2 arithmetic); chunk flags
+// g.tile_solid per FP32 z-march chunk.
+cudaError_t launch_zpair_step(const void* fin, void* fout, const Geo& g, const DevParams& p, cudaStream_t s);
 // Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);
 int batched_ctas_per_sm(int lat, int prec);

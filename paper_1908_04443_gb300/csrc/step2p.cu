@@ -19,6 +19,7 @@
 
 #include "kernels.h"
 #include "lattice.cuh"
+#include "pack2.cuh"
 #include "tile_common.cuh"
 
 namespace lbmwet {
@@ -26,21 +27,6 @@ namespace lbmwet {
 namespace {
 
 constexpr int PTX = 32, PTY = 8, PNY = 16;   // threads x, threads y, tile rows (two per thread)
-
-// ---- packed pair arithmetic ----------------------------------------------------------------
-struct V2 {
-    float2 v;
-};
-__device__ __forceinline__ V2 bc(float a) { return {make_float2(a, a)}; }
-__device__ __forceinline__ V2 mk(float a, float b) { return {make_float2(a, b)}; }
-__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return {__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return {__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ V2 operator*(float s, V2 b) { return {__fmul2_rn(make_float2(s, s), b.v)}; }
-__device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ V2 fma2(float s, V2 b, V2 c) { return {__ffma2_rn(make_float2(s, s), b.v, c.v)}; }
-__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return fma2(-1.0f, b, a); }
-__device__ __forceinline__ V2 operator-(V2 a) { return -1.0f * a; }
-__device__ __forceinline__ V2 div2(V2 a, V2 b) { return mk(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
 
 // Collision constants folded with the row norms of M: a_k = (m*_k - m_k) / |row_k|^2.
 struct PairRates {
@@ -65,31 +51,6 @@ PairRates make_pair_rates(const DevParams& p) {
     r.kn1 = float(-p.s_nu / 4.0);
     r.kn2 = float(2.0 * hn / 4.0);
     return r;
-}
-
-// psi of a pair (Eq. 6 with the C-S or PR pressure); a non-positive argument flags ERR_PSI on
-// the lanes in `check` and gives psi 0
-__device__ __forceinline__ V2 psi2(V2 rho, const Phys<float>& e, bool check_a, bool check_b, unsigned* err) {
-    V2 p;
-    if (e.eos_kind == 1) {
-        const V2 eta = e.b4 * rho;
-        const V2 om = bc(1.0f) - eta;
-        const V2 eta2 = eta * eta;
-        const V2 poly = fma2(eta2, bc(1.0f) - eta, bc(1.0f) + eta);   // 1 + eta + eta^2 - eta^3
-        const V2 num = (e.RT * rho) * poly;
-        const V2 den = (om * om) * om;
-        p = div2(num, den) - e.a * (rho * rho);
-    } else {
-        const V2 br = e.b * rho;
-        const V2 den2 = fma2(br, bc(2.0f) - br, bc(1.0f));           // 1 + 2 b rho - b^2 rho^2
-        p = div2(e.RT * rho, bc(1.0f) - br) - div2(e.aphi * (rho * rho), den2);
-    }
-    const V2 arg = e.two_over_G * fma2(-1.0f / 3.0f, rho, p);
-    V2 out;
-    out.v.x = arg.v.x > 0.0f ? arg.v.x * rsqrtf(arg.v.x) : 0.0f;
-    out.v.y = arg.v.y > 0.0f ? arg.v.y * rsqrtf(arg.v.y) : 0.0f;
-    if ((check_a && !(arg.v.x > 0.0f)) || (check_b && !(arg.v.y > 0.0f))) atomicOr(err, ERR_PSI);
-    return out;
 }
 
 // MRT collision (Eq. 2 with the source of Eq. 7) of a pair in deviation variables; f += M^-1 (m* - m)

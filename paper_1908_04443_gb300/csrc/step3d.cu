@@ -43,12 +43,6 @@ __device__ __forceinline__ int ring(int z, int r) {
 
 template <class S>
 struct ZShape;
-#ifndef LBMWET_Z3F_X   // column and chunk of the FP32 z-march (compile-time; chosen by measurement)
-#define LBMWET_Z3F_X 32
-#define LBMWET_Z3F_Y 4
-#define LBMWET_Z3F_Z 32
-#define LBMWET_Z3F_MINB 3
-#endif
 template <> struct ZShape<float> {
     static constexpr int X = LBMWET_Z3F_X, Y = LBMWET_Z3F_Y, Z = LBMWET_Z3F_Z, MINB = LBMWET_Z3F_MINB;
 };
@@ -308,6 +302,9 @@ void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz) {
 
 cudaError_t launch_step3d(int prec, int mode, const void* fin, void* fout, const Geo& g, const DevParams& p,
                           double* rho, double* u, cudaStream_t s) {
+#ifndef LBMWET_ZMARCH_STEP
+    if (prec == PREC_FP32 && mode == 0) return launch_zpair_step(fin, fout, g, p, s);
+#endif
     if (prec == PREC_FP64)
         return mode == 0 ? launch_z<double, 0>(fin, fout, g, p, rho, u, s) : launch_z<double, 1>(fin, fout, g, p, rho, u, s);
     return mode == 0 ? launch_z<float, 0>(fin, fout, g, p, rho, u, s) : launch_z<float, 1>(fin, fout, g, p, rho, u, s);

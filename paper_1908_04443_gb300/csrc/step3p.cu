@@ -1,0 +1,432 @@
+// D3Q19 FP32 time step as a z-pair march: the z-march of the scalar kernel with two planes per
+// iteration, each thread carrying the same (x, y) cell on two consecutive planes, so that every
+// per-node quantity is a float2 and the step's arithmetic runs on packed FP32x2 instructions.
+//
+// A CTA of TX x TY threads owns a TX x TY column and walks a chunk of z-planes.  For the lead pair
+// of planes (zl, zl + 1) it
+//   A. pulls (Eq. 3 with halfway bounce-back, Fig. 3) both planes of its own cells and of the 1-node
+//      xy halo ring (the 2-node ring too where the chunk holds solids), stores rho (Eq. 4) and, at
+//      fluid cells, psi (Eq. 6); wall cells are queued per plane;
+//   B. gives the wall cells of planes zl - 1 and zl their virtual density (Eqs. 16-17 with the
+//      limiter, or the constant one) from the densities of planes zl - 2 .. zl + 1, and its psi;
+//   C. collides planes zl - 2 and zl - 1: F_m (Eq. 5), u (Eq. 4), the MRT collision with the
+//      consistency source (Eqs. 2, 7) in the increment form f += M^-1 (m* - m), coalesced stores.
+// Rings indexed by the absolute plane: own distributions 4 planes, densities 4, psi 8, node types
+// 8, wall queues 4.  Results equal the scalar z-march's up to FP32 rounding (operations regrouped).
+#include <cmath>
+
+#include "kernels.h"
+#include "lattice.cuh"
+#include "pack2.cuh"
+#include "tile_common.cuh"
+
+namespace lbmwet {
+
+namespace {
+
+#ifndef LBMWET_ZP_MINB   // resident CTAs per SM of the z-pair march (chosen by measurement)
+#define LBMWET_ZP_MINB 3
+#endif
+// column and chunk: the FP32 z-march's (the per-chunk solid flags are shared)
+constexpr int ZTX = LBMWET_Z3F_X, ZTY = LBMWET_Z3F_Y, ZCH = LBMWET_Z3F_Z;
+static_assert(ZCH % 2 == 0, "planes are marched in pairs");
+
+// D3Q19 collision constants folded with the row norms of the d'Humieres basis:
+// a_k = (m*_k - m_k) / |row_k|^2, |row|^2 = (19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24,
+// 4, 4, 4, 8, 8, 8).
+struct Rates3P {
+    float k1e, k2e, k3e;     // a1 = k1e (m1 - e_eq) + k2e u.F + k3e X
+    float k1p, k2p, k3p;     // a2 = k1p (m2 - eps_eq) + k2p u.F + k3p X
+    float kq1, kq2;          // a4 = kq1 (m4 + 2/3 rho ux) + kq2 Fx (a6, a8 likewise)
+    float kn9, kh9;          // a9 = kn9 (m9 - 3pxx_eq) + kh9 S3xx
+    float kp10, kh10;        // a10 = kp10 (m10 + 3pxx_eq / 2) + kh10 S3xx
+    float kn11, kh11;        // a11 = kn11 (m11 - pww_eq) + kh11 Sww
+    float kp12, kh12;        // a12 = kp12 (m12 + pww_eq / 2) + kh12 Sww
+    float kn13, kh13;        // a13 = kn13 (m13 - rho ux uy) + kh13 (ux Fy + uy Fx) (a14, a15 likewise)
+    float km;                // a16 = km m16 (a17, a18 likewise)
+};
+
+Rates3P make_rates3p(const DevParams& p) {
+    const double he = 1.0 - 0.5 * p.s_e, hp = 1.0 - 0.5 * p.s_eps, hq = 1.0 - 0.5 * p.s_q;
+    const double hn = 1.0 - 0.5 * p.s_nu, hpi = 1.0 - 0.5 * p.s_pi;
+    Rates3P r;
+    r.k1e = float(-p.s_e / 2394.0);
+    r.k2e = float(38.0 * he / 2394.0);
+    r.k3e = float(he * p.c_e / 2394.0);
+    r.k1p = float(-p.s_eps / 252.0);
+    r.k2p = float(-11.0 * hp / 252.0);
+    r.k3p = float(-hp * p.c_eps / 252.0);
+    r.kq1 = float(-p.s_q / 40.0);
+    r.kq2 = float(-hq * (2.0 / 3.0) / 40.0);
+    r.kn9 = float(-p.s_nu / 36.0);
+    r.kh9 = float(hn / 36.0);
+    r.kp10 = float(-p.s_pi / 72.0);
+    r.kh10 = float(-0.5 * hpi / 72.0);
+    r.kn11 = float(-p.s_nu / 12.0);
+    r.kh11 = float(hn / 12.0);
+    r.kp12 = float(-p.s_pi / 24.0);
+    r.kh12 = float(-0.5 * hpi / 24.0);
+    r.kn13 = float(-p.s_nu / 4.0);
+    r.kh13 = float(hn / 4.0);
+    r.km = float(-p.s_m / 8.0);
+    return r;
+}
+
+// MRT collision (d'Humieres D3Q19, source of Eq. 7 as in collide_d3q19) of a pair; f += M^-1 (m* - m)
+__device__ __forceinline__ void collide3p(V2 (&f)[19], V2 drho, V2 rho, V2 ux, V2 uy, V2 uz, V2 Fx, V2 Fy, V2 Fz, V2 X,
+                                          const Rates3P& k) {
+    // moments of the non-conserved rows
+    const V2 ax = f[1] + f[2], ay = f[3] + f[4], az = f[5] + f[6];
+    const V2 d12 = f[1] - f[2], d34 = f[3] - f[4], d56 = f[5] - f[6];
+    const V2 p78 = f[7] + f[8], p910 = f[9] + f[10], p1112 = f[11] + f[12], p1314 = f[13] + f[14];
+    const V2 p1516 = f[15] + f[16], p1718 = f[17] + f[18];
+    const V2 q78 = f[7] - f[8], q910 = f[9] - f[10], q1112 = f[11] - f[12], q1314 = f[13] - f[14];
+    const V2 q1516 = f[15] - f[16], q1718 = f[17] - f[18];
+    const V2 exy = p78 + p910, exz = p1112 + p1314, eyz = p1516 + p1718;
+    const V2 s16 = (ax + ay) + az, s718 = (exy + exz) + eyz;
+    const V2 m1 = fma2(-30.0f, f[0], fma2(8.0f, s718, -11.0f * s16));
+    const V2 m2 = fma2(12.0f, f[0], fma2(-4.0f, s16, s718));
+    const V2 m4 = fma2(-4.0f, d12, (q78 + q910) + (q1112 + q1314));
+    const V2 m6 = fma2(-4.0f, d34, (q78 - q910) + (q1516 + q1718));
+    const V2 m8 = fma2(-4.0f, d56, (q1112 - q1314) + (q1516 - q1718));
+    const V2 exyz = exy + exz;
+    const V2 ayz = ay + az;
+    const V2 m9 = fma2(2.0f, ax, fma2(-2.0f, eyz, exyz - ayz));
+    const V2 m10 = fma2(-4.0f, ax, fma2(2.0f, ayz, fma2(-2.0f, eyz, exyz)));
+    const V2 m11 = (ay - az) + (exy - exz);
+    const V2 m12 = fma2(2.0f, az - ay, exy - exz);
+    const V2 m13 = p78 - p910, m14 = p1516 - p1718, m15 = p1112 - p1314;
+    const V2 m16 = (q78 + q910) - (q1112 + q1314);
+    const V2 m17 = (q910 - q78) + (q1516 + q1718);
+    const V2 m18 = (q1112 - q1314) - (q1516 - q1718);
+    // equilibria (deviation form) and sources
+    const V2 uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const V2 u2 = (uxx + uyy) + uzz;
+    const V2 rhou2 = rho * u2;
+    const V2 uF = fma2(ux, Fx, fma2(uy, Fy, uz * Fz));
+    const V2 e_eq = fma2(19.0f, rhou2, -11.0f * drho);
+    const V2 eps_eq = fma2(-5.5f, rhou2, 3.0f * drho);
+    const V2 a1 = fma2(k.k3e, X, fma2(k.k2e, uF, k.k1e * (m1 - e_eq)));
+    const V2 a2 = fma2(k.k3p, X, fma2(k.k2p, uF, k.k1p * (m2 - eps_eq)));
+    const V2 a4 = fma2(k.kq2, Fx, k.kq1 * fma2(2.0f / 3.0f, rho * ux, m4));
+    const V2 a6 = fma2(k.kq2, Fy, k.kq1 * fma2(2.0f / 3.0f, rho * uy, m6));
+    const V2 a8 = fma2(k.kq2, Fz, k.kq1 * fma2(2.0f / 3.0f, rho * uz, m8));
+    const V2 p3xx = rho * fma2(3.0f, uxx, -u2);
+    const V2 uyFy = uy * Fy, uzFz = uz * Fz;
+    const V2 S3xx = 2.0f * fma2(2.0f * ux, Fx, -(uyFy + uzFz));
+    const V2 a9 = fma2(k.kh9, S3xx, k.kn9 * (m9 - p3xx));
+    const V2 a10 = fma2(k.kh10, S3xx, k.kp10 * fma2(0.5f, p3xx, m10));
+    const V2 pww = rho * (uyy - uzz);
+    const V2 Sww = 2.0f * (uyFy - uzFz);
+    const V2 a11 = fma2(k.kh11, Sww, k.kn11 * (m11 - pww));
+    const V2 a12 = fma2(k.kh12, Sww, k.kp12 * fma2(0.5f, pww, m12));
+    const V2 a13 = fma2(k.kh13, fma2(ux, Fy, uy * Fx), k.kn13 * (m13 - rho * (ux * uy)));
+    const V2 a14 = fma2(k.kh13, fma2(uy, Fz, uz * Fy), k.kn13 * (m14 - rho * (uy * uz)));
+    const V2 a15 = fma2(k.kh13, fma2(ux, Fz, uz * Fx), k.kn13 * (m15 - rho * (ux * uz)));
+    const V2 a16 = k.km * m16, a17 = k.km * m17, a18 = k.km * m18;
+    const V2 a3 = 0.1f * Fx, a5 = 0.1f * Fy, a7 = 0.1f * Fz;
+    // f += M^T diag(1/|row|^2) (m* - m), columns of M per velocity
+    f[0] = fma2(-30.0f, a1, fma2(12.0f, a2, f[0]));
+    const V2 axis = fma2(-11.0f, a1, -4.0f * a2);
+    const V2 a910 = fma2(-2.0f, a10, a9);                       // a9 - 2 a10
+    const V2 axx = fma2(2.0f, a910, axis);                      // axis + 2 a9 - 4 a10
+    const V2 r34 = fma2(-4.0f, a4, a3), r56 = fma2(-4.0f, a6, a5), r78 = fma2(-4.0f, a8, a7);
+    f[1] = f[1] + (axx + r34);
+    f[2] = f[2] + (axx - r34);
+    const V2 a1112 = fma2(-2.0f, a12, a11);                     // a11 - 2 a12
+    const V2 ayy = (axis - a910) + a1112;
+    const V2 azz = (axis - a910) - a1112;
+    f[3] = f[3] + (ayy + r56);
+    f[4] = f[4] + (ayy - r56);
+    f[5] = f[5] + (azz + r78);
+    f[6] = f[6] + (azz - r78);
+    const V2 edge = fma2(8.0f, a1, a2);
+    const V2 b910 = a9 + a10, b1112 = a11 + a12;
+    const V2 exy0 = (edge + b910) + b1112, exz0 = (edge + b910) - b1112;
+    const V2 eyz0 = fma2(-2.0f, b910, edge);
+    const V2 t34 = a3 + a4, t56 = a5 + a6, t78 = a7 + a8;
+    const V2 g1 = t34 + t56, g2 = t34 - t56;
+    const V2 h1 = a16 - a17, h2 = a16 + a17;
+    f[7] = f[7] + ((exy0 + a13) + (g1 + h1));
+    f[8] = f[8] + ((exy0 + a13) - (g1 + h1));
+    f[9] = f[9] + ((exy0 - a13) + (g2 + h2));
+    f[10] = f[10] + ((exy0 - a13) - (g2 + h2));
+    const V2 g3 = t34 + t78, g4 = t34 - t78;
+    const V2 h3 = a18 - a16, h4 = a16 + a18;
+    f[11] = f[11] + ((exz0 + a15) + (g3 + h3));
+    f[12] = f[12] + ((exz0 + a15) - (g3 + h3));
+    f[13] = f[13] + ((exz0 - a15) + (g4 - h4));
+    f[14] = f[14] + ((exz0 - a15) - (g4 - h4));
+    const V2 g5 = t56 + t78, g6 = t56 - t78;
+    const V2 h5 = a17 - a18, h6 = a17 + a18;
+    f[15] = f[15] + ((eyz0 + a14) + (g5 + h5));
+    f[16] = f[16] + ((eyz0 + a14) - (g5 + h5));
+    f[17] = f[17] + ((eyz0 - a14) + (g6 + h6));
+    f[18] = f[18] + ((eyz0 - a14) - (g6 + h6));
+}
+
+template <int TX, int TY>
+struct ZPSmem {
+    static constexpr int YX = TX + 6, YY = TY + 6;   // type planes (3-node xy halo)
+    static constexpr int RX = TX + 4, RY = TY + 4;   // density planes (2-node xy halo)
+    static constexpr int PX = TX + 2, PY = TY + 2;   // psi planes (1-node xy halo)
+    float f[4][19][TY * TX];
+    float rho[4][RY * RX];
+    float psi[8][PY * PX];
+    uint8_t type[8][YY * YX];
+    short wq[4][PY * PX];
+    int nw[4];
+};
+
+template <bool SOLID>
+__device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float* __restrict__ fout, const Geo& g,
+                                            const Phys<float>& ph, const Rates3P& kr, int x0, int y0, int zb,
+                                            unsigned* err, ZPSmem<ZTX, ZTY>& sm) {
+    using L = D3Q19;
+    constexpr int Q = 19, TX = ZTX, TY = ZTY, NT = TX * TY;
+    using Sm = ZPSmem<TX, TY>;
+    constexpr int YX = Sm::YX, YY = Sm::YY, RX = Sm::RX, RY = Sm::RY, PX = Sm::PX, PY = Sm::PY;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N, nxy = nx * ny;
+    const int ze = min(zb + ZCH, nz);
+    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
+    const bool small = nx < TX + 8 || ny < TY + 8 || nz < 8;
+    auto wx = [&](int v) { return small ? wrap_full(v, nx) : wrap1(v, nx); };
+    auto wy = [&](int v) { return small ? wrap_full(v, ny) : wrap1(v, ny); };
+    auto wz = [&](int v) { return small ? wrap_full(v, nz) : wrap1(v, nz); };
+
+    auto load_types = [&](int z) {
+        if constexpr (SOLID) {
+            uint8_t* dst = sm.type[z & 7];
+            const int gz = wz(z);
+            for (int i = tid; i < YX * YY; i += NT) dst[i] = g.type[gz * nxy + wy(y0 + i / YX - 3) * nx + wx(x0 + i % YX - 3)];
+        }
+    };
+    auto type_at = [&](int z, int ti) -> uint8_t {
+        if constexpr (!SOLID) return uint8_t(T_BULK);
+        return sm.type[z & 7][ti];
+    };
+    // sources of node (gx, gy, gz) of plane z (type cell ti): sink(a, pointer)
+    auto pull_src = [&](auto&& sink, int gx, int gy, int gz, int z, int ti, uint8_t self) {
+        const int cx[3] = {wrap1(gx - 1, nx), gx, wrap1(gx + 1, nx)};
+        const int ry[3] = {wrap1(gy - 1, ny) * nx, gy * nx, wrap1(gy + 1, ny) * nx};
+        const int pz[3] = {wrap1(gz - 1, nz) * nxy, gz * nxy, wrap1(gz + 1, nz) * nxy};
+        if (!SOLID || (self & T_BULK)) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                sink(a, fin + (a * N + pz[1 - L::ez(a)] + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
+        } else {
+            const uint8_t* tm = sm.type[(z - 1) & 7];
+            const uint8_t* t0 = sm.type[z & 7];
+            const uint8_t* tp = sm.type[(z + 1) & 7];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                const uint8_t* tz = ez > 0 ? tm : (ez < 0 ? tp : t0);   // upstream plane is z - ez
+                const bool bb = (tz[ti - ex - ey * YX] & T_SOLID) != 0;
+                sink(a, fin + (bb ? L::opp(a) * N + pz[1] + ry[1] + cx[1] : a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]));
+            }
+        }
+    };
+    // pull both planes (zl, zl + 1) of the xy cell (hx, hy) of the density plane; f0/f1: keep the
+    // distributions of the own cell (index own) in the ring
+    auto do_pair = [&](int zl, int hx, int hy, bool want_psi, int own, bool keep0, bool keep1) {
+        const int gx = wx(x0 + hx - 2), gy = wy(y0 + hy - 2);
+        const int ti = (hy + 1) * YX + hx + 1;
+        const uint8_t t0 = type_at(zl, ti), t1 = type_at(zl + 1, ti);
+        const bool fl0 = !(t0 & T_SOLID), fl1 = !(t1 & T_SOLID);
+        V2 h[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) h[a] = bc(0.0f);
+        if (fl0) pull_src([&](int a, const float* src) { h[a].v.x = *src; }, gx, gy, wz(zl), zl, ti, t0);
+        if (fl1) pull_src([&](int a, const float* src) { h[a].v.y = *src; }, gx, gy, wz(zl + 1), zl + 1, ti, t1);
+        V2 d = h[0];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) d = d + h[a];
+        const V2 rho = bc(ph.rho_ref) + d;
+        if (own >= 0) {
+            if (keep0) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) sm.f[zl & 3][a][own] = h[a].v.x;
+            }
+            if (keep1) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) sm.f[(zl + 1) & 3][a][own] = h[a].v.y;
+            }
+        }
+        if constexpr (SOLID) {   // densities are read only by Eq. 17
+            const int ri = hy * RX + hx;
+            sm.rho[zl & 3][ri] = fl0 ? rho.v.x : 0.0f;
+            sm.rho[(zl + 1) & 3][ri] = fl1 ? rho.v.y : 0.0f;
+        }
+        if (want_psi) {
+            const int pi = (hy - 1) * PX + hx - 1;
+            const V2 ps = psi2(rho, ph, fl0, fl1, err);
+            sm.psi[zl & 7][pi] = fl0 ? ps.v.x : 0.0f;
+            sm.psi[(zl + 1) & 7][pi] = fl1 ? ps.v.y : 0.0f;
+            if (SOLID && (t0 & T_WALL)) sm.wq[zl & 3][atomicAdd(&sm.nw[zl & 3], 1)] = short(pi);
+            if (SOLID && (t1 & T_WALL)) sm.wq[(zl + 1) & 3][atomicAdd(&sm.nw[(zl + 1) & 3], 1)] = short(pi);
+        }
+    };
+
+    // prologue: type planes zb - 3 .. zb, empty wall queues of the first lead pair
+    for (int z = zb - 3; z <= zb; ++z) load_types(z);
+    if (tid == 0) sm.nw[(zb - 2) & 3] = sm.nw[(zb - 1) & 3] = 0;
+    __syncthreads();
+
+    for (int zl = zb - 2; zl <= ze + 1; zl += 2) {
+        // A. the lead pair: own cells, the 1-node xy halo ring, the 2-node ring near solids
+        do_pair(zl, lx + 2, ly + 2, true, tid, zl >= zb && zl < ze, zl + 1 >= zb && zl + 1 < ze);
+        using Ring1 = Shell<PX, PY, 1, 2>;
+        for (int k = tid; k < Ring1::COUNT; k += NT) {
+            int px, py, pz;
+            Ring1::cell(k, px, py, pz);
+            do_pair(zl, px + 1, py + 1, true, -1, false, false);
+        }
+        if constexpr (SOLID) {
+            using Ring2 = Shell<RX, RY, 1, 2>;
+            for (int k = tid; k < Ring2::COUNT; k += NT) {
+                int rx, ry, rz;
+                Ring2::cell(k, rx, ry, rz);
+                do_pair(zl, rx, ry, false, -1, false, false);
+            }
+        }
+        __syncthreads();
+
+        // B. wall cells of planes zl - 1 and zl
+        if constexpr (SOLID) {
+            bool any = false;
+            for (int zw = zl - 1; zw <= zl; ++zw) {
+                const int nwb = sm.nw[zw & 3];
+                if (zw < zb - 1 || zw > ze || nwb == 0) continue;
+                any = true;
+                const short* q = sm.wq[zw & 3];
+                for (int k = tid; k < nwb; k += NT) {
+                    const int i = q[k];
+                    const int px = i % PX, py = i / PX;
+                    const int rc = (py + 1) * RX + px + 1, tc = (py + 2) * YX + px + 2;
+                    float rw;
+                    if (ph.wall_kind == 1) {
+                        rw = ph.rho_w_const;
+                    } else {
+                        // Eq. 17: weighted mean of the fluid neighbours' densities
+                        float num = 0.0f, den = 0.0f;
+#pragma unroll
+                        for (int a = 1; a < Q; ++a) {
+                            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                            if (!(sm.type[(zw + ez) & 7][tc + ex + ey * YX] & T_SOLID)) {
+                                num += float(L::wf(a)) * sm.rho[(zw + ez) & 3][rc + ex + ey * RX];
+                                den += float(L::wf(a));
+                            }
+                        }
+                        const float rho_ave = cdiv(num, den);
+                        const float kap = g.kappa_w
+                                              ? float(g.kappa_w[g.wall_id[wz(zw) * nxy + wy(y0 + py - 1) * nx + wx(x0 + px - 1)]])
+                                              : float(g.kappa);
+                        // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                        const float raw = (kap >= 0.0f) ? (1.0f + kap) * rho_ave : rho_ave + kap;
+                        rw = raw > ph.rho_l ? ph.rho_l : raw;
+                        rw = rw < ph.rho_g ? ph.rho_g : rw;
+                    }
+                    sm.psi[zw & 7][i] = psi2(bc(rw), ph, true, false, err).v.x;
+                }
+            }
+            if (any) __syncthreads();
+        }
+
+        // C. collide planes zl - 2 and zl - 1
+        const int zc = zl - 2;
+        const bool va0 = zc >= zb && zc < ze, va1 = zc + 1 >= zb && zc + 1 < ze;
+        if ((va0 || va1) && x0 + lx < nx && y0 + ly < ny) {
+            const int ti = (ly + 3) * YX + lx + 3;
+            const bool fl0 = va0 && !(type_at(zc, ti) & T_SOLID), fl1 = va1 && !(type_at(zc + 1, ti) & T_SOLID);
+            if (fl0 || fl1) {
+                V2 f[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a) f[a] = mk(sm.f[zc & 3][a][tid], sm.f[(zc + 1) & 3][a][tid]);
+                const int pc = (ly + 1) * PX + lx + 1;
+                auto psi_at = [&](int dz, int off) {
+                    return mk(sm.psi[(zc + dz) & 7][pc + off], sm.psi[(zc + 1 + dz) & 7][pc + off]);
+                };
+                const V2 psi_c = psi_at(0, 0);
+                // sum_a w_a psi(x + e_a) e_a over opposite pairs: w_a e_a (psi(x + e_a) - psi(x - e_a))
+                V2 sx = bc(0.0f), sy = bc(0.0f), sz = bc(0.0f);
+#pragma unroll
+                for (int a = 1; a < Q; ++a) {
+                    if (L::opp(a) < a) continue;
+                    const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                    const int off = ex + ey * PX;
+                    const V2 wd = float(L::wf(a)) * (psi_at(ez, off) - psi_at(-ez, -off));
+                    if (ex) sx = ex > 0 ? sx + wd : sx - wd;
+                    if (ey) sy = ey > 0 ? sy + wd : sy - wd;
+                    if (ez) sz = ez > 0 ? sz + wd : sz - wd;
+                }
+                // Eq. 5
+                const V2 gpsi = (-ph.G) * psi_c;
+                const V2 Fmx = gpsi * sx, Fmy = gpsi * sy, Fmz = gpsi * sz;
+                const V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy), Fz = Fmz + bc(ph.fz);
+                V2 drho = f[0];
+#pragma unroll
+                for (int a = 1; a < Q; ++a) drho = drho + f[a];
+                const V2 jx = ((f[1] - f[2]) + (f[7] - f[8])) + ((f[9] - f[10]) + (f[11] - f[12])) + (f[13] - f[14]);
+                const V2 jy = ((f[3] - f[4]) + (f[7] - f[8])) + ((f[10] - f[9]) + (f[15] - f[16])) + (f[17] - f[18]);
+                const V2 jz = ((f[5] - f[6]) + (f[11] - f[12])) + ((f[14] - f[13]) + (f[15] - f[16])) + (f[18] - f[17]);
+                const V2 rho = bc(ph.rho_ref) + drho;
+                if ((fl0 && !(rho.v.x > 0.0f)) || (fl1 && !(rho.v.y > 0.0f))) atomicOr(err, ERR_RHO);
+                // Eq. 4: rho u = sum e f + F/2
+                const V2 inv = div2(bc(1.0f), rho);
+                const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv, uz = fma2(0.5f, Fz, jz) * inv;
+                const V2 X = div2(fma2(Fmx, Fmx, fma2(Fmy, Fmy, Fmz * Fmz)), psi_c * psi_c);
+                collide3p(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, kr);
+                const int gi = zc * nxy + (y0 + ly) * nx + x0 + lx;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    if (fl0) fout[a * N + gi] = f[a].v.x;
+                    if (fl1) fout[a * N + gi + nxy] = f[a].v.y;
+                }
+            }
+        }
+        // type planes of the next lead pair's pulls; empty its wall queues
+        load_types(zl + 3);
+        load_types(zl + 4);
+        if (tid == 0) sm.nw[(zl + 2) & 3] = sm.nw[(zl + 3) & 3] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
+    zpair_step(const float* __restrict__ fin, float* __restrict__ fout, Geo g, Phys<float> ph, Rates3P kr,
+               unsigned* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
+    const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
+    if (solid) zpair_chunk<true>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+    else zpair_chunk<false>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+}
+
+}  // namespace
+
+void zpair_tile_shape(int* tx, int* ty, int* tz) {
+    *tx = ZTX;
+    *ty = ZTY;
+    *tz = ZCH;
+}
+
+cudaError_t launch_zpair_step(const void* fin, void* fout, const Geo& g, const DevParams& p, cudaStream_t s) {
+    constexpr size_t bytes = sizeof(ZPSmem<ZTX, ZTY>);
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(zpair_step, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    dim3 grid((p.nx + ZTX - 1) / ZTX, (p.ny + ZTY - 1) / ZTY, (p.nz + ZCH - 1) / ZCH);
+    zpair_step<<<grid, dim3(ZTX, ZTY, 1), bytes, s>>>(static_cast<const float*>(fin), static_cast<float*>(fout), g,
+                                                      make_phys<float>(p), make_rates3p(p), p.err);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmwet

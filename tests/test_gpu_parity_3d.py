@@ -69,3 +69,29 @@ def test_sphere_60_steps_fp64_and_fp32():
         o32, rho32, _ = sim.observables(fields=True)
     assert np.max(np.abs(rho32[fl] - rho_ref[fl])) < 1e-4 * l
     assert abs(o32.theta_deg - th) < 0.5
+
+
+@pytest.mark.parametrize("shape,c,R,dc,r,kw", [
+    ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(kappa=0.2)),
+    ((21, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(kappa=-0.03)),   # odd plane count
+    ((70, 16, 40), (20.0, 8.0, 30.0), 5.0, (20.0, 8.0, 40.0), 6.0, dict(kappa=0.1)),      # 3 chunks, last of 6
+    ((5, 6, 7), (3.0, 3.0, 2.0), 1.0, (3.0, 3.0, 3.5), 1.5, dict(kappa=0.2)),              # smaller than a column
+    ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(wall="VD", rho_w_const=0.1)),
+    ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(body_force=(2e-6, -1e-6, 3e-6))),
+])
+def test_one_step_d3q19_fp32(shape, c, R, dc, r, kw):
+    """FP32 deviation storage (the z-pair march): one step against the oracle from a common state;
+    2e-6 of the largest distribution bounds the FP32 rounding carried through one collision."""
+    case = sphere_case(shape=shape, c=c, R=R, dc=dc, r=r, **kw)
+    case.rho_ref = case.bounds()[0]
+    s1, ref = _one_step(case, "fp32")
+    assert np.max(np.abs(s1 - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+def test_per_wall_node_kappa_3d_fp32():
+    case = sphere_case()
+    geo = lbm.Geometry(case.mask, "D3Q19")
+    case.kappa = np.random.default_rng(9).uniform(-0.03, 0.3, len(geo.wall_flat))
+    case.rho_ref = case.bounds()[0]
+    s1, ref = _one_step(case, "fp32")
+    assert np.max(np.abs(s1 - ref)) <= 2e-6 * np.max(np.abs(ref))
