@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("step.cu", "step2p.cu", "step2d.cu", "step3d.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):
+    for f in ("step2p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the pair kernel's sources
         with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
