@@ -198,6 +198,21 @@ def cpu_baseline(wl_name: str, target_s: float = 15.0):
 # our arm
 # ---------------------------------------------------------------------------------------------
 
+def slowest_rank_ms(local_ms, dist, torch, device):
+    """The timed region's length on the slowest rank (max over ranks; the local value without a
+    process group)."""
+    if dist is None:
+        return local_ms
+    t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, nodes_per_rank, steps, total_ms):
+    """Whole-job MLUPS of `world` replicas, each updating `nodes_per_rank` nodes `steps` times."""
+    return world * nodes_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -423,11 +438,8 @@ def run_ours(args):
     step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     total_ms = sum(step_ms)
     launches = run.launches() - launches0
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = slowest_rank_ms(total_ms, dist, torch, "cuda")
+    value = job_rate(world, nodes, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
 
     # roofline of the step kernel: algorithmic bytes (read + write of every distribution once)
