@@ -43,8 +43,8 @@ UNIT = "MLUPS"
 # of the kernel sources: when the sources change the figure is stale and reported as null.
 NCU_TRAFFIC = {
     # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
-    # one launch (217,851,648 + 158,635,776 bytes)
-    ("c2", "fp32", "1f945383ba1f2191"): 376487424,
+    # one launch (217,154,048 + 158,667,520 bytes)
+    ("c2", "fp32", "b35459da4d67bfe0"): 375821568,
 }
 
 
@@ -320,13 +320,19 @@ def adjoint_ratio(L, torch, stream, steps=2000, ckpt=100):
                     "the checkpointed forward pass", "grad_norm": float(np.linalg.norm(g))}
 
 
-def device_rate(L, torch, stream, name, steps, flush):
+def device_rate(L, torch, stream, name, steps, flush, precision=None):
     """Device-timed MLUPS and HBM-roofline fraction of another workload (same protocol as the
-    headline: L2 flushed before each timed step, CUDA events around each step)."""
-    wls, precision, label = workload(name)
+    headline: L2 flushed before each timed step, CUDA events around each step); `precision`
+    overrides the workload's."""
+    wls, prec0, label = workload(name)
+    precision = precision or prec0
+    if precision != prec0:
+        label = label.replace("_fp32", "") + "_" + precision
     e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
-    e.T = wls[0].t_over_tc * L.lbm_critical_temperature(e)
+    e.T = (wls[0].t_over_tc if wls else 0.6) * L.lbm_critical_temperature(e)
     rho_g, rho_l = L.lbm_coexistence(e)
+    if wls is None:
+        wls = c2_sweep(rho_l, rho_g)
     if name == "c4":
         for wl in wls:
             if wl.kappa < 0:
@@ -362,7 +368,8 @@ def device_rate(L, torch, stream, name, steps, flush):
     return {"workload": label, "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 5),
             "l2": "flushed before each timed step" if use_flush else "inputs larger than L2, no flush",
             "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT, "achieved_gbs": round(gbs, 1),
-            "frac_of_measured_hbm": round(gbs / peak, 4)}
+            "frac_of_measured_hbm": round(gbs / peak, 4),
+            "bound": "hbm" if precision == "fp32" else "fp64 pipe (GB300 FP64 is far below its FP32 rate)"}
 
 
 def run_ours(args):
@@ -398,6 +405,7 @@ def run_ours(args):
     lattice = wls[0].lattice
     cfgs = [make_cfg(L, wl, precision, rho_g, rho_l) for wl in wls]
     masks = [wl.mask() for wl in wls]
+    fluid = int(sum(int((m == 0).sum()) for m in masks))
     rho0s = [wl.rho0(rho_l, rho_g) for wl in wls]
     nodes = sum(wl.nodes for wl in wls)
     stream = torch.cuda.Stream()
@@ -494,6 +502,8 @@ def run_ours(args):
     others = None
     if not args.no_extras and args.workload == "c2":
         others = {w: device_rate(L, torch, stream, w, steps, flush) for w, steps in (("c3", 10), ("c4", 20))}
+        if args.workload == "c2":
+            others["c2_fp64"] = device_rate(L, torch, stream, "c2", 10, flush, precision="fp64")
 
     # end to end through the public API with host buffers: init from host arrays, K calls of the
     # stepping entry point with one step each (each reads back the 4-byte device status), then the
@@ -530,6 +540,8 @@ def run_ours(args):
                        "l2": ("flushed before every timed step (2 x L2 buffer rewrite, outside the events)"
                               if use_flush else f"inputs larger than L2: {state_bytes / 1e6:.0f} MB of "
                               f"distributions vs {l2 / 1e6:.0f} MB of L2, no flush")},
+            "fluid_only": {"value": round(value * fluid / nodes, 1), "unit": UNIT,
+                           "note": "the same rate counting fluid nodes only (solid nodes are skipped)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "wall_s_timed_region": round(t_wall, 4),
             "kernel_hash": khash}
