@@ -1239,59 +1239,84 @@ extern "C" lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, d
     const int64_t every = h->rec_every, n = h->rec_steps;
     const int64_t nck = (int64_t)h->ckpt.size();
     const size_t es = h->prec == LBM_FP64 ? sizeof(double) : sizeof(float);
-    // segment buffers: slot 0 receives a copy of the segment's checkpoint, slots 1.. the recomputed
-    // states; one CUDA graph per (segment length, adjoint-buffer parity) replays a whole segment
-    void* seg = nullptr;
+    // Two segment buffers: slot 0 of a buffer receives a copy of a segment's checkpoint, slots 1.. the
+    // recomputed states.  Pass t reverses segment nck - t (recomputed by pass t - 1) and, on a second
+    // branch of the same CUDA graph, recomputes segment nck - 1 - t into the other buffer: the two
+    // branches share no data, so the recomputation hides behind the latency-bound reverse kernels.
+    // The checkpoint copy is issued before the graph, which therefore depends only on the two segment
+    // lengths, the adjoint-buffer parity and the buffer index, and is reused across passes.
+    void* seg[2] = {nullptr, nullptr};
     void* mu[2] = {nullptr, nullptr};
     void* scratch = nullptr;
     double* dk = nullptr;
-    cudaStream_t cap = nullptr;
-    std::vector<std::pair<std::pair<int64_t, int>, cudaGraphExec_t>> graphs;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    struct Key {
+        int64_t rev_len, rec_len;
+        int par, rec_buf;
+    };
+    std::vector<std::pair<Key, cudaGraphExec_t>> graphs;
     lbm_status st = LBM_OK;
-    cudaError_t e = cudaMalloc(&seg, h->fbytes * (size_t)every);
+    cudaError_t e = cudaMalloc(&seg[0], h->fbytes * (size_t)every);
+    if (e == cudaSuccess && nck > 1) e = cudaMalloc(&seg[1], h->fbytes * (size_t)every);
     if (e == cudaSuccess) e = cudaMalloc(&mu[0], h->fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&mu[1], h->fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&scratch, es * adjoint_scratch_elems(h->N));
     if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(double) * (nw ? nw : 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double) * (nw ? nw : 1), h->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
     AdjointScratch w{scratch};
     int cur = 0;
     if (e == cudaSuccess) e = launch_adjoint_final(h->prec, drho_final_dev, mu[cur], h->dp, h->stream);
-    auto slot = [&](int64_t i) { return static_cast<void*>(static_cast<char*>(seg) + (size_t)i * h->fbytes); };
-    auto enqueue_segment = [&](int64_t len, int par, cudaStream_t s) -> cudaError_t {
-        cudaError_t r = cudaSuccess;
-        for (int64_t i = 0; i + 1 < len && r == cudaSuccess; ++i)
-            r = launch_step(h->lat, h->prec, slot(i), slot(i + 1), h->dp, s);
-        int c2 = par;
-        for (int64_t i = len - 1; i >= 0 && r == cudaSuccess; --i) {
-            r = launch_adjoint_step(h->prec, slot(i), mu[c2], mu[c2 ^ 1], h->dp, w, dk, s);
+    auto slot = [&](int b, int64_t i) {
+        return static_cast<void*>(static_cast<char*>(seg[b]) + (size_t)i * h->fbytes);
+    };
+    auto seg_len = [&](int64_t c) { return c >= 0 && c < nck ? std::min(every, n - c * every) : int64_t(0); };
+    // one graph: reverse rev_len steps in buffer rec_buf ^ 1 || recompute rec_len - 1 steps in rec_buf
+    auto capture = [&](const Key& k, cudaGraphExec_t* ex) -> cudaError_t {
+        cudaGraph_t g = nullptr;
+        cudaError_t r0 = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (r0 != cudaSuccess) return r0;
+        cudaError_t r = cudaEventRecord(fork, cap);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(cap2, fork, 0);
+        for (int64_t i = 0; i + 1 < k.rec_len && r == cudaSuccess; ++i)
+            r = launch_step(h->lat, h->prec, slot(k.rec_buf, i), slot(k.rec_buf, i + 1), h->dp, cap2);
+        int c2 = k.par;
+        for (int64_t i = k.rev_len - 1; i >= 0 && r == cudaSuccess; --i) {
+            r = launch_adjoint_step(h->prec, slot(k.rec_buf ^ 1, i), mu[c2], mu[c2 ^ 1], h->dp, w, dk, cap);
             c2 ^= 1;
         }
+        if (r == cudaSuccess) r = cudaEventRecord(join, cap2);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(cap, join, 0);
+        cudaError_t r1 = cudaStreamEndCapture(cap, &g);
+        if (r == cudaSuccess) r = r1;
+        if (r == cudaSuccess) r = cudaGraphInstantiate(ex, g, 0);
+        if (g) cudaGraphDestroy(g);
         return r;
     };
-    for (int64_t c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
-        const int64_t len = std::min(every, n - c * every);
-        e = cudaMemcpyAsync(slot(0), h->ckpt[c], h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+    for (int64_t t = 0; t <= nck && e == cudaSuccess; ++t) {
+        // the buffer of pass t's recomputation; with one segment only buffer 0 exists and t = 1 only reverses
+        const Key k{seg_len(nck - t), seg_len(nck - 1 - t), cur, int(t & 1)};
+        if (k.rec_len > 0)
+            e = cudaMemcpyAsync(slot(k.rec_buf, 0), h->ckpt[nck - 1 - t], h->fbytes, cudaMemcpyDeviceToDevice,
+                                h->stream);
         if (e != cudaSuccess) break;
         cudaGraphExec_t ex = nullptr;
         for (auto& kv : graphs)
-            if (kv.first.first == len && kv.first.second == cur) ex = kv.second;
+            if (kv.first.rev_len == k.rev_len && kv.first.rec_len == k.rec_len && kv.first.par == k.par &&
+                kv.first.rec_buf == k.rec_buf)
+                ex = kv.second;
         if (!ex) {
-            cudaGraph_t g = nullptr;
-            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            e = capture(k, &ex);
             if (e != cudaSuccess) break;
-            cudaError_t r = enqueue_segment(len, cur, cap);
-            e = cudaStreamEndCapture(cap, &g);
-            if (r != cudaSuccess) e = r;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (e != cudaSuccess) break;
-            graphs.push_back({{len, cur}, ex});
+            graphs.push_back({k, ex});
         }
         e = cudaGraphLaunch(ex, h->stream);
-        if (len % 2) cur ^= 1;
-        h->launches += (len - 1) + 5 * len;
+        if (k.rev_len % 2) cur ^= 1;
+        h->launches += (k.rec_len > 0 ? k.rec_len - 1 : 0) + 2 * k.rev_len;
     }
     if (e == cudaSuccess && nw)
         e = cudaMemcpyAsync(dkappa_host, dk, sizeof(double) * nw, cudaMemcpyDeviceToHost, h->stream);
@@ -1299,7 +1324,11 @@ extern "C" lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, d
     if (e != cudaSuccess) st = cuda_fail(h, e, "adjoint");
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     if (cap) cudaStreamDestroy(cap);
-    cudaFree(seg);
+    if (cap2) cudaStreamDestroy(cap2);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    cudaFree(seg[0]);
+    cudaFree(seg[1]);
     cudaFree(mu[0]);
     cudaFree(mu[1]);
     cudaFree(scratch);

@@ -11,8 +11,8 @@
 //      limiter, or the constant one) from the densities of planes zl - 2 .. zl + 1, and its psi;
 //   C. collides planes zl - 2 and zl - 1: F_m (Eq. 5), u (Eq. 4), the MRT collision with the
 //      consistency source (Eqs. 2, 7) in the increment form f += M^-1 (m* - m), coalesced stores.
-// Rings indexed by the absolute plane: own distributions 4 planes, densities 4, psi 8, node types
-// 8, wall queues 4.  Results equal the scalar z-march's up to FP32 rounding (operations regrouped).
+// Rings indexed by the absolute plane: densities 4 planes, psi 8, node types 8, wall queues 4 (and,
+// with LBMWET_ZP_REPULL = 0, the own distributions, 4 planes).  Results equal the scalar z-march's up to FP32 rounding (operations regrouped).
 #include <cmath>
 
 #include "kernels.h"
@@ -24,8 +24,15 @@ namespace lbmwet {
 
 namespace {
 
+// LBMWET_ZP_REPULL = 1: the collision pulls its pair of planes again (from L2, where the lead pull
+// left them one iteration earlier) instead of keeping a 39 KB ring of them in shared memory; the
+// smaller footprint leaves more of the SM's memory to L1 and one more CTA resident.  Measured on
+// the 256^3 sphere: 22.4 GLUPS (4 CTAs per SM) against 22.1 for the ring (3 CTAs per SM).
+#ifndef LBMWET_ZP_REPULL
+#define LBMWET_ZP_REPULL 1
+#endif
 #ifndef LBMWET_ZP_MINB   // resident CTAs per SM of the z-pair march (chosen by measurement)
-#define LBMWET_ZP_MINB 3
+#define LBMWET_ZP_MINB (LBMWET_ZP_REPULL ? 4 : 3)
 #endif
 // column and chunk: the FP32 z-march's (the per-chunk solid flags are shared)
 constexpr int ZTX = LBMWET_Z3F_X, ZTY = LBMWET_Z3F_Y, ZCH = LBMWET_Z3F_Z;
@@ -170,7 +177,7 @@ struct ZPSmem {
     static constexpr int YX = TX + 6, YY = TY + 6;   // type planes (3-node xy halo)
     static constexpr int RX = TX + 4, RY = TY + 4;   // density planes (2-node xy halo)
     static constexpr int PX = TX + 2, PY = TY + 2;   // psi planes (1-node xy halo)
-    float f[4][19][TY * TX];
+    float f[LBMWET_ZP_REPULL ? 1 : 4][19][LBMWET_ZP_REPULL ? 1 : TY * TX];
     float rho[4][RY * RX];
     float psi[8][PY * PX];
     uint8_t type[8][YY * YX];
@@ -243,14 +250,16 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
 #pragma unroll
         for (int a = 1; a < Q; ++a) d = d + h[a];
         const V2 rho = bc(ph.rho_ref) + d;
-        if (own >= 0) {
-            if (keep0) {
+        if constexpr (!LBMWET_ZP_REPULL) {
+            if (own >= 0) {
+                if (keep0) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) sm.f[zl & 3][a][own] = h[a].v.x;
-            }
-            if (keep1) {
+                    for (int a = 0; a < Q; ++a) sm.f[zl & 3][a][own] = h[a].v.x;
+                }
+                if (keep1) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) sm.f[(zl + 1) & 3][a][own] = h[a].v.y;
+                    for (int a = 0; a < Q; ++a) sm.f[(zl + 1) & 3][a][own] = h[a].v.y;
+                }
             }
         }
         if constexpr (SOLID) {   // densities are read only by Eq. 17
@@ -341,8 +350,20 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
             const bool fl0 = va0 && !(type_at(zc, ti) & T_SOLID), fl1 = va1 && !(type_at(zc + 1, ti) & T_SOLID);
             if (fl0 || fl1) {
                 V2 f[Q];
+#if LBMWET_ZP_REPULL
+#pragma unroll
+                for (int a = 0; a < Q; ++a) f[a] = bc(0.0f);
+                {
+                    const int gx = x0 + lx, gy = y0 + ly;
+                    if (fl0) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gy, zc, zc, ti, type_at(zc, ti));
+                    if (fl1)
+                        pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gy, zc + 1, zc + 1, ti,
+                                 type_at(zc + 1, ti));
+                }
+#else
 #pragma unroll
                 for (int a = 0; a < Q; ++a) f[a] = mk(sm.f[zc & 3][a][tid], sm.f[(zc + 1) & 3][a][tid]);
+#endif
                 const int pc = (ly + 1) * PX + lx + 1;
                 auto psi_at = [&](int dz, int off) {
                     return mk(sm.psi[(zc + dz) & 7][pc + off], sm.psi[(zc + 1 + dz) & 7][pc + off]);
