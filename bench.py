@@ -9,12 +9,13 @@ time step).  One bench step is one lattice Boltzmann time step of every grid.  M
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c2|c2single|c1|c3|c4] [--precision fp32|fp64]
 
-Timing: W untimed steps, then K steps, each bracketed by CUDA events on the stream the step kernel
-is launched on.  When the distributions of the workload fit in twice the L2 size, the L2 cache is
-flushed (a 2 x L2-sized buffer is rewritten) before every timed step, outside the events; larger
-workloads (the default sweep: 415 MB) run back to back.  Under torchrun (N > 1) every rank
-runs an independent replica of the workload (no data-path collective): value = N x nodes x K / the
-slowest rank's time.  --impl reference times the FP64 CPU oracle on the same workload.
+Timing: W untimed steps, then K steps timed with CUDA events on the stream the step kernel is
+launched on.  When the distributions of the workload fit in twice the L2 size, the L2 cache is
+flushed (a 2 x L2-sized buffer is rewritten) before every timed step, outside the events that
+bracket each step; larger workloads (the default sweep: 415 MB) run the K steps back to back
+between one pair of events.  Under torchrun (N > 1) every rank runs an independent replica of the
+workload (no data-path collective): value = N x nodes x K / the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the same workload.
 """
 from __future__ import annotations
 
@@ -432,19 +433,27 @@ def run_ours(args):
             # a bounded spin (torch's sleep kernel) holds the stream while the host enqueues every
             # timed step, so that no event interval includes host launch latency
             torch.cuda._sleep(int(2e6 + 4e5 * args.steps))
-            for k in range(args.steps):
-                if use_flush:
+            if use_flush:
+                for k in range(args.steps):
                     flush.zero_()                  # evict the state from L2 (outside the events)
-                starts[k].record(stream)
-                run.enqueue(1)
-                ends[k].record(stream)
+                    starts[k].record(stream)
+                    run.enqueue(1)
+                    ends[k].record(stream)
+            else:
+                # state larger than L2: the K steps run back to back between one pair of events
+                starts[0].record(stream)
+                for k in range(args.steps):
+                    run.enqueue(1)
+                ends[0].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     run.step(0)                                    # reads the device error flag
     if dist is not None:
         dist.barrier()
-    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    if use_flush:
+        total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    else:
+        total_ms = starts[0].elapsed_time(ends[0])
     launches = run.launches() - launches0
     total_ms = slowest_rank_ms(total_ms, dist, torch, "cuda")
     value = job_rate(world, nodes, args.steps, total_ms)

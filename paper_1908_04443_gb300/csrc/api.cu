@@ -869,6 +869,7 @@ struct lbm_batch {
     int lat = 0, prec = 0;
     DevParams phys{};
     unsigned* d_err = nullptr;
+    unsigned* d_sched = nullptr;       // pair kernel: tile-claim counters (zero between launches)
     BatchInstance* d_insts = nullptr;
     BatchItem* d_items = nullptr;
     int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
@@ -912,6 +913,7 @@ void batch_free(lbm_batch* b) {
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->d_err);
+    cudaFree(b->d_sched);
     cudaFree(b->d_insts);
     cudaFree(b->d_items);
     cudaFree(b->d_begin);
@@ -925,7 +927,7 @@ void batch_free(lbm_batch* b) {
 
 cudaError_t batch_step_kernel(lbm_batch* b, cudaStream_t s, int parity) {
     if (b->ymarch) return launch_ymarch(b->prec, parity, b->phys, b->d_items, b->d_begin, b->ctas, s);
-    if (b->pair) return launch_pair_batched(parity, b->phys, b->d_items, b->n_items, b->ctas, s);
+    if (b->pair) return launch_pair_batched(parity, b->phys, b->d_items, b->n_items, b->ctas, b->d_sched, s);
     return launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
 }
 
@@ -1115,6 +1117,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     b->n_items = int(items.size());
     b->phys = b->inst[0]->dp;
     cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sched, 0, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
     if (e == cudaSuccess && b->ymarch) e = cudaMalloc(&b->d_begin, sizeof(int) * begin.size());

@@ -41,7 +41,7 @@ struct BatchInstance {
 // One work item of the batched tile kernel (a tile of an instance) or of the y-march (a run of rows
 // y0 .. y1 - 1 of a column block), with everything it needs (one contiguous record, so that a CTA
 // fetches the next item with one load per lane).
-struct BatchItem {
+struct alignas(16) BatchItem {
     int nx, ny, N, x0, y0, solid;   // solid: a solid node lies within the item's box + 3-node halo
     int inst, y1;
     const void* f[2];
@@ -52,7 +52,7 @@ struct BatchItem {
     const void* tmap;               // FP32 pair kernel: the instance's two TMA tensor maps (128 bytes
                                     // each, for f[0] and f[1]) or null
 };
-static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem is copied as 32-bit words");
+static_assert(sizeof(BatchItem) % 16 == 0, "BatchItem is copied as 32-bit words or 16-byte chunks");
 
 // Column and chunk of the FP32 D3Q19 step kernels (z-march and z-pair march share the per-chunk
 // solid flags); compile-time, chosen by measurement.
@@ -84,10 +84,12 @@ cudaError_t launch_set_state(int lat, int prec, void* fout, const DevParams& p, 
 cudaError_t launch_step_batched(int lat, int prec, int parity, const DevParams& phys, const BatchInstance* insts,
                                 const BatchItem* items, int n_items, int ctas, cudaStream_t s);
 // D2Q9 FP32 step with two nodes per thread (packed FP32x2 arithmetic) on 32 x 16 tiles: one
-// grid (tile flags p.pair_solid) or a persistent grid of `ctas` CTAs walking (instance, tile) items.
+// grid (tile flags p.pair_solid) or a persistent grid of `ctas` CTAs walking (instance, tile) items,
+// claimed dynamically through `sched` (two device counters, zero before the first launch; the
+// kernel leaves them zero).
 cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cudaStream_t s);
 cudaError_t launch_pair_batched(int parity, const DevParams& phys, const BatchItem* items, int n_items, int ctas,
-                                cudaStream_t s);
+                                unsigned* sched, cudaStream_t s);
 void pair_tile_shape(int* tx, int* ty);
 // Box (x extent, y extent; all 9 directions) of the pair kernel's TMA load: a tile and the cells its
 // pulls read, with x starting 4 cells before the tile (a 16-byte boundary).

@@ -135,11 +135,10 @@ struct PairGrid {
 // One 32 x 16 tile with first node (x0, y0), reading g.f[parity] and writing g.f[parity ^ 1].
 // SOLID = false: no solid node within the tile + 3-node halo.  WRAP as in the scalar tile kernel:
 // 0 no periodic wrap, 1 a single wrap, 2 full modulo.
-// box: the tile's PairBox already in shared memory (tiles without solids and without wrap), or
-// null.  pre() runs once in every thread right after the halo ring's copies are issued; its own
-// cp.async copies form the one commit group the phase does not wait for.  hook() runs once in every
-// thread right after the barrier that ends phase 1 (the box and the halo staging are free from then
-// on).
+// box: the tile's PairBox already in shared memory, or null (pulls from global memory).  pre() runs
+// once in every thread right after the halo ring's copies are issued; its own cp.async copies form
+// the one commit group the phase does not wait for.  hook() runs once in every thread right after
+// the barrier that ends phase 1 (the box and the halo staging are free from then on).
 template <bool SOLID, int WRAP, class G, class Pre = NoHook, class Hook = NoHook>
 __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
                                           int y0, unsigned* err, PairSmem& sm, const float* box = nullptr,
@@ -204,11 +203,26 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
         }
     };
 
+    // the same from the box: node at box cell (bx, by) of tile-relative type cell ti
+    using B = PairBox;
+    auto box_src = [&](auto&& sink, int bx, int by, int ti, uint8_t self) {
+        if (!SOLID || (self & T_BULK)) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) sink(a, box[(a * B::BY + by - L::ey(a)) * B::BX + bx - L::ex(a)]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                sink(a, bb ? box[(L::opp(a) * B::BY + by) * B::BX + bx]
+                           : box[(a * B::BY + by - L::ey(a)) * B::BX + bx - L::ex(a)]);
+            }
+        }
+    };
+
     // 1. the halo-ring cell of this thread: its loads go out first (cp.async into shared memory)
     using Ring = Shell<PX, PY, 1, 2>;
-    using B = PairBox;
     static_assert(Ring::COUNT == SHELL && SHELL <= NT, "one ring cell per thread");
-    const bool boxed = !SOLID && WRAP == 0 && box != nullptr;
+    const bool boxed = box != nullptr;
     const bool has_h = tid < SHELL;
     uint8_t hty = uint8_t(T_SOLID);
     int hpx = 0, hpy = 0;
@@ -231,7 +245,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     const uint8_t ta = type_at(tia), tb = type_at(tib);
     const bool fa = !(ta & T_SOLID), fb = !(tb & T_SOLID);
     V2 f[Q];
-    if (boxed) {
+    if (boxed && !SOLID) {
         // node (x, y), direction a: the value at (x - e_a, y - e_a) of the box
 #pragma unroll
         for (int a = 0; a < Q; ++a)
@@ -240,8 +254,13 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     } else {
 #pragma unroll
         for (int a = 0; a < Q; ++a) f[a] = bc(0.0f);
-        if (fa) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gya, tia, ta);
-        if (fb) pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gyb, tib, tb);
+        if (boxed) {
+            if (fa) box_src([&](int a, float v) { f[a].v.x = v; }, lx + B::X0, ly + B::Y0, tia, ta);
+            if (fb) box_src([&](int a, float v) { f[a].v.y = v; }, lx + B::X0, ly + PTY + B::Y0, tib, tb);
+        } else {
+            if (fa) pull_src([&](int a, const float* src) { f[a].v.x = *src; }, gx, gya, tia, ta);
+            if (fb) pull_src([&](int a, const float* src) { f[a].v.y = *src; }, gx, gyb, tib, tb);
+        }
     }
     V2 drho = f[0];
 #pragma unroll
@@ -268,9 +287,8 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
             float h[Q];
             if (boxed) {
                 // ring cell (x0 + hpx - 1, y0 + hpy - 1)
-#pragma unroll
-                for (int a = 0; a < Q; ++a)
-                    h[a] = box[(a * B::BY + hpy - 1 + B::Y0 - L::ey(a)) * B::BX + hpx - 1 + B::X0 - L::ex(a)];
+                box_src([&](int a, float v) { h[a] = v; }, hpx - 1 + B::X0, hpy - 1 + B::Y0, tix(hpx + 2, hpy + 2),
+                        hty);
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) h[a] = sm.hst[a * SHELL + tid];
@@ -418,19 +436,29 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
 // latency.
 constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
 
-// Persistent form: CTAs walk the (instance, tile) list.  Work records sit in a ring of three shared
-// slots: the current tile's, the next tile's, and the one after, whose copy (cp.async) is issued
-// during this tile and not waited for until the next.  A tile without solids and without wrap, of a
-// grid with TMA tensor maps, pulls from a box that one TMA load brings into shared memory while the
-// previous tile finishes (issued right after that tile's phase 1, when the box is free).
+// Persistent form with dynamic tile scheduling.  CTA b starts with items b and b + gridDim.x; every
+// further item is claimed from a global counter (sched[0]), so that a CTA slowed by costly tiles
+// (walls, periodic edges, ragged columns) simply takes fewer of them, and items are taken in list
+// order (the tiles in flight stay neighbours in memory).  Work records sit in a ring of three
+// shared slots: the current tile's, the next tile's and the one after.  Thread 0 claims the one
+// after at the end of the previous tile (few registers are live there), and early in phase 1 it
+// publishes the index and copies that record with 16-byte cp.async copies that the next tile waits
+// for.  Every tile of a grid with TMA tensor maps (row length a multiple of 4 nodes) away from the
+// periodic edges pulls from a box that one TMA load brings into shared memory while the previous
+// tile finishes (issued right after that tile's phase 1, when the box is free).  One claim is made
+// per tile processed; the last CTA to finish resets the counter for the next launch (sched[1]
+// counts finished CTAs).
 __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     pair_step_batched(int parity, const BatchItem* __restrict__ items, int n_items, Phys<float> ph, PairRates kr,
-                      unsigned* err) {
-    constexpr int WORDS = int(sizeof(BatchItem) / 4);
+                      unsigned* err, unsigned* sched) {
+    constexpr int WORDS = int(sizeof(BatchItem) / 4), CHUNKS = int(sizeof(BatchItem) / 16);
+    static_assert(sizeof(BatchItem) % 16 == 0, "records are copied in 16-byte chunks");
+    using B = PairBox;
     __shared__ PairSmem sm;
-    __shared__ alignas(128) float box[PairBox::ELEMS];
+    __shared__ alignas(128) float box[B::ELEMS];
     __shared__ alignas(8) uint64_t bar;
     __shared__ BatchItem s_item[3];
+    __shared__ int s_idx[3];   // item index held by each record slot (n_items or more: none)
     const int tid = threadIdx.y * PTX + threadIdx.x;
     const int grid = gridDim.x;
     if (tid < WORDS) {
@@ -440,50 +468,55 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
             reinterpret_cast<uint32_t*>(&s_item[1])[tid] =
                 reinterpret_cast<const uint32_t*>(&items[blockIdx.x + grid])[tid];
     }
+    unsigned claim = 0;   // thread 0: the claim for the record two tiles ahead
     if (tid == 0) {
+        s_idx[0] = blockIdx.x;
+        s_idx[1] = blockIdx.x + grid;
+        if (blockIdx.x < n_items) claim = atomicAdd(sched, 1u);
         mbar_init(&bar);
         fence_mbar_init();
     }
     __syncthreads();
-    auto boxed = [](const BatchItem& r) {
-        return r.tmap != nullptr && !r.solid && pair_wrap(r.x0, r.y0, r.nx, r.ny) == 0;
-    };
+    auto boxed = [](const BatchItem& r) { return r.tmap != nullptr && pair_wrap(r.x0, r.y0, r.nx, r.ny) == 0; };
     auto issue = [&](const BatchItem& r) {
-        const char* maps = static_cast<const char*>(r.tmap);
-        tma_load_box(box, maps + 128 * parity, r.x0 - PairBox::X0, r.y0 - PairBox::Y0, 0, &bar,
-                     unsigned(PairBox::ELEMS * sizeof(float)));
+        fence_proxy_async();
+        tma_load_box(box, static_cast<const char*>(r.tmap) + 128 * parity, r.x0 - B::X0, r.y0 - B::Y0, 0, &bar,
+                     unsigned(B::ELEMS * sizeof(float)));
     };
     unsigned phase = 0;
     bool cur_boxed = blockIdx.x < n_items && boxed(s_item[0]);
     if (cur_boxed && tid == 0) issue(s_item[0]);
     int s0 = 0, s1 = 1, s2 = 2;   // ring slots of the current, next and after-next records
-    for (int it = blockIdx.x; it < n_items; it += grid) {
+    for (int it = blockIdx.x; it < n_items;) {
         const BatchItem& item = s_item[s0];
         const BatchItem& nxt = s_item[s1];
-        const int far = it + 2 * grid;
         auto pre = [&]() {
-            if (tid < WORDS && far < n_items)
-                cp_async(reinterpret_cast<float*>(&s_item[s2]) + tid, reinterpret_cast<const float*>(&items[far]) + tid);
+            if (tid == 0) {
+                const int far = 2 * grid + int(claim);
+                s_idx[s2] = far;
+                if (far < n_items) {
+#pragma unroll
+                    for (int c = 0; c < CHUNKS; ++c)
+                        cp_async16(reinterpret_cast<float*>(&s_item[s2]) + 4 * c,
+                                   reinterpret_cast<const float*>(&items[far]) + 4 * c);
+                }
+            }
         };
         bool next_boxed = false;
         auto hook = [&]() {
-            next_boxed = it + grid < n_items && boxed(nxt);
-            if (next_boxed && tid == 0) {
-                fence_proxy_async();
-                issue(nxt);
-            }
+            next_boxed = s_idx[s1] < n_items && boxed(nxt);
+            if (next_boxed && tid == 0) issue(nxt);
         };
-        if (item.solid) {
-            pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm, nullptr, pre, hook);
-        } else {
-            const float* bx = nullptr;
-            if (cur_boxed) {
-                if (!mbar_wait(&bar, phase, MBAR_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
-                phase ^= 1u;
-                bx = box;
-            }
-            pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
+        const float* bx = nullptr;
+        if (cur_boxed) {
+            if (!mbar_wait(&bar, phase, MBAR_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+            phase ^= 1u;
+            bx = box;
         }
+        if (item.solid) pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
+        else pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
+        it = s_idx[s1];
+        if (tid == 0 && it < n_items) claim = atomicAdd(sched, 1u);   // for the tile after `it`'s next
         __syncthreads();   // this tile's threads are done with shared memory
         const int t = s0;
         s0 = s1;
@@ -492,6 +525,14 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
         cur_boxed = next_boxed;
     }
     cp_wait<0>();
+    if (tid == 0) {
+        // every claim of this CTA has returned; the last CTA to get here resets the counters
+        __threadfence();
+        if (atomicAdd(sched + 1, 1u) == unsigned(grid) - 1u) {
+            atomicExch(sched, 0u);
+            atomicExch(sched + 1, 0u);
+        }
+    }
 }
 
 }  // namespace
@@ -529,9 +570,9 @@ cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cu
 }
 
 cudaError_t launch_pair_batched(int parity, const DevParams& p, const BatchItem* items, int n_items, int ctas,
-                                cudaStream_t s) {
+                                unsigned* sched, cudaStream_t s) {
     pair_step_batched<<<ctas, dim3(PTX, PTY, 1), 0, s>>>(parity, items, n_items, make_phys<float>(p),
-                                                         make_pair_rates(p), p.err);
+                                                         make_pair_rates(p), p.err, sched);
     return cudaGetLastError();
 }
 

@@ -131,8 +131,8 @@ struct Shell {
     }
 };
 
-// Asynchronous global -> shared copies of one element (cp.async, 4 or 8 bytes), their commit
-// groups and the wait for all but PENDING of the thread's groups.
+// Asynchronous global -> shared copies (cp.async) of one element (4 or 8 bytes) or of 16 bytes,
+// their commit groups and the wait for all but PENDING of the thread's groups.
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
@@ -140,6 +140,11 @@ __device__ __forceinline__ void cp_async(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async(double* dst, const double* src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+// 16 bytes (both addresses 16-byte aligned), not kept in L1
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int PENDING>

@@ -100,11 +100,16 @@ def test_batch_member_rules():
 @pytest.mark.parametrize("kernel", ["tile", "pair"])
 def test_batch_wide_grids_equal_single_runs(kernel):
     """FP32 batches of grids with interior tiles (no periodic wrap) as well as edge and wall tiles:
-    every instance evolves exactly as the grid stepped alone."""
+    every instance evolves exactly as the grid stepped alone.  The pair kernel pulls every tile of a
+    grid whose rows are a multiple of 4 nodes long from a shared-memory box (TMA for interior tiles,
+    cp.async at wrapped coordinates for edge tiles, a grid narrower than the box included) and the
+    other grids from global memory; the grid stepped alone pulls from global memory."""
     from paper_1908_04443_gb300 import lbmwet as L
     a = drop_on_cylinder((96, 256), (128.0, 30.0), 14.0, (128.0, 58.0), 15.0, kappa=0.15, step_kernel=kernel)
     b = drop_on_cylinder((120, 200), (60.0, 50.0), 18.0, (60.0, 86.0), 19.0, kappa=-0.02, step_kernel=kernel)
-    cases = [a, b]
+    c = drop_on_cylinder((30, 36), (18.0, 10.0), 5.0, (18.0, 22.0), 6.5, kappa=0.1, step_kernel=kernel)
+    d = drop_on_cylinder((50, 98), (3.0, 25.0), 9.0, (3.0, 40.0), 9.0, kappa=0.05, step_kernel=kernel)
+    cases = [a, b, c, d]
     for cs in cases:
         cs.rho_ref = cs.bounds()[0]
     bt = _batch(cases, "fp32")
