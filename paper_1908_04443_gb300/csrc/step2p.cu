@@ -5,7 +5,8 @@
 // of the step (density, pseudopotential, force, velocity, MRT collision) runs on both nodes at once
 // through the packed FP32 instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn), which do two IEEE
 // single-precision operations per instruction.  The phases are those of the scalar tile kernel:
-//   0. node types of the tile + 3-node halo into shared memory (tiles holding a solid node);
+//   0. node types of the tile + 3-node halo into shared memory (tiles holding a solid node; a batch
+//      copies them during the previous tile);
 //   1. pull (Eq. 3, halfway bounce-back of Fig. 3) of the two own nodes into registers and of the
 //      tile's 1-node halo ring (one cell per thread of the first 100 threads, copied with cp.async
 //      into shared memory so that its loads are in flight with the own nodes'); density (Eq. 4)
@@ -95,10 +96,20 @@ __device__ __forceinline__ void collide2(V2 (&f)[9], V2 drho, V2 rho, V2 ux, V2 
     f[8] = f[8] + (cv - qq);
 }
 
-// The TMA box of a tile: every direction's values over x0 - 4 .. x0 + 35, y0 - 2 .. y0 + 17 (the
-// tile, its halo ring and the ring's upstream cells), [a][y][x].
+// LBMWET_PAIR_BOX_RING2 = 1: the box also holds the rows the 2-node density ring of a wall tile pulls
+// from, so that the ring comes from the box instead of global memory (2.9 KB more shared memory per
+// CTA; 4 CTAs still fit the 164 KB shared-memory carveout, so L1 keeps 64 KB).  Measured on the
+// 600 x 400 sweep: 0.759 of the HBM roofline against 0.751 without it.
+#ifndef LBMWET_PAIR_BOX_RING2
+#define LBMWET_PAIR_BOX_RING2 1
+#endif
+
+// The TMA box of a tile: every direction's values over x0 - 4 .. x0 + 35, y0 - Y0 .. y0 + 15 + Y0
+// (the tile, its halo ring and the ring's upstream cells; with LBMWET_PAIR_BOX_RING2 the 2-node ring
+// and its upstream cells), [a][y][x].
 struct PairBox {
-    static constexpr int BX = PTX + 8, BY = PNY + 4, X0 = 4, Y0 = 2;
+    static constexpr int BX = PTX + 8, BY = PNY + (LBMWET_PAIR_BOX_RING2 ? 6 : 4), X0 = 4,
+                         Y0 = LBMWET_PAIR_BOX_RING2 ? 3 : 2;
     static constexpr int ELEMS = 9 * BY * BX;
     static_assert(PTX % 4 == 0, "x0 - 4 must be a 16-byte boundary");
 };
@@ -110,12 +121,11 @@ struct NoHook {
 struct PairSmem {
     static constexpr int RX = PTX + 4, RY = PNY + 4;   // density tile (2-node halo)
     static constexpr int PX = PTX + 2, PY = PNY + 2;   // psi tile (1-node halo)
-    static constexpr int YX = PTX + 6, YY = PNY + 6;   // type tile (3-node halo)
+    static constexpr int YX = PTX + 8, YY = PNY + 6;   // type tile: x0 - 4 .. x0 + 35, 3-node halo in y
     static constexpr int SHELL = 2 * PX + 2 * (PY - 2);
-    uint8_t type[YY * YX];
+    uint8_t type[2][YY * YX];   // two buffers: a batch copies the next tile's types during this tile
     float rho[RY * RX];
     float psi[PY * PX];
-    float hst[9 * SHELL];     // the halo ring's pulled distributions, [a][ring cell]
     short wall[PY * PX];
     int nwall;
 };
@@ -141,8 +151,8 @@ struct PairGrid {
 // the barrier that ends phase 1 (the box and the halo staging are free from then on).
 template <bool SOLID, int WRAP, class G, class Pre = NoHook, class Hook = NoHook>
 __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
-                                          int y0, unsigned* err, PairSmem& sm, const float* box = nullptr,
-                                          const Pre& pre = Pre(), const Hook& hook = Hook()) {
+                                          int y0, unsigned* err, PairSmem& sm, float* hst, const float* box,
+                                          int tbuf, bool ty_ready, const Pre& pre, const Hook& hook) {
     using L = D2Q9;
     constexpr int Q = 9, NT = PTX * PTY;
     using Sm = PairSmem;
@@ -151,26 +161,33 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * PTX + lx;
     const float* __restrict__ fin = static_cast<const float*>(g.f[parity]);
     auto wr = [](int v, int n) { return WRAP == 0 ? v : (WRAP == 1 ? wrap1(v, n) : wrap_full(v, n)); };
-    auto tix = [](int cx, int cy) { return cy * YX + cx; };   // type cell of tile-relative (cx - 3, cy - 3)
+    auto tix = [](int cx, int cy) { return cy * YX + cx + 1; };   // type cell of tile-relative (cx - 3, cy - 3)
+    uint8_t* const tyb = sm.type[tbuf];
     auto rix = [](int cx, int cy) { return cy * RX + cx; };   // density cell of (cx - 2, cy - 2)
     auto pix = [](int cx, int cy) { return cy * PX + cx; };   // psi cell of (cx - 1, cy - 1)
 
-    // 0. node types of the tile + 3-node halo; does the 1-node halo region hold a wall?
+    // 0. node types of the tile + 3-node halo (unless already in tyb); does the 1-node halo region
+    // hold a wall?
     if (tid == 0) sm.nwall = 0;
     bool tile_has_wall = false;
     if constexpr (SOLID) {
         int wall_seen = 0;
         for (int i = tid; i < YX * YY; i += NT) {
-            const int cx = i % YX, cy = i / YX;
-            const uint8_t ty = g.type[wr(y0 + cy - 3, ny) * nx + wr(x0 + cx - 3, nx)];
-            sm.type[i] = ty;
-            if (cx >= 2 && cx < PTX + 4 && cy >= 2 && cy < PNY + 4 && (ty & T_WALL)) wall_seen = 1;
+            const int cx = i % YX, cy = i / YX;   // node (x0 + cx - 4, y0 + cy - 3)
+            uint8_t ty;
+            if (ty_ready) {
+                ty = tyb[i];
+            } else {
+                ty = g.type[wr(y0 + cy - 3, ny) * nx + wr(x0 + cx - 4, nx)];
+                tyb[i] = ty;
+            }
+            if (cx >= 3 && cx < PTX + 5 && cy >= 2 && cy < PNY + 4 && (ty & T_WALL)) wall_seen = 1;
         }
         tile_has_wall = __syncthreads_or(wall_seen);
     }
     auto type_at = [&](int ti) -> uint8_t {
         if constexpr (!SOLID) return uint8_t(T_BULK);
-        return sm.type[ti];
+        return tyb[ti];
     };
     // source of every distribution streaming into node (gx, gy), handed to sink(a, pointer)
     auto pull_src = [&](auto&& sink, int gx, int gy, int ti, uint8_t self) {
@@ -182,7 +199,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                    const bool bb = (tyb[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
                     sink(a, p + (bb ? L::opp(a) * N : a * N - L::ex(a) - L::ey(a) * nx));
                 }
             }
@@ -195,7 +212,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                    const bool bb = (tyb[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
                     sink(a, fin + (bb ? L::opp(a) * N + ry[1] + cx[1]
                                       : a * N + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
                 }
@@ -212,7 +229,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
         } else {
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                const bool bb = (sm.type[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
+                const bool bb = (tyb[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
                 sink(a, bb ? box[(L::opp(a) * B::BY + by) * B::BX + bx]
                            : box[(a * B::BY + by - L::ey(a)) * B::BX + bx - L::ex(a)]);
             }
@@ -232,7 +249,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
         const int ti = tix(hpx + 2, hpy + 2);
         hty = type_at(ti);
         if (!boxed && !(hty & T_SOLID))
-            pull_src([&](int a, const float* src) { cp_async(&sm.hst[a * SHELL + tid], src); },
+            pull_src([&](int a, const float* src) { cp_async(&hst[a * SHELL + tid], src); },
                      wr(x0 + hpx - 1, nx), wr(y0 + hpy - 1, ny), ti, hty);
     }
     cp_commit();
@@ -291,7 +308,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
                         hty);
             } else {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) h[a] = sm.hst[a * SHELL + tid];
+                for (int a = 0; a < Q; ++a) h[a] = hst[a * SHELL + tid];
             }
             float d = h[0];
 #pragma unroll
@@ -312,18 +329,28 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
                 int rx, ry, rz;
                 Ring2::cell(k, rx, ry, rz);
                 const int ti = tix(rx + 1, ry + 1);
-                const uint8_t ty = sm.type[ti];
+                const uint8_t ty = tyb[ti];
                 float rho = 0.0f;
                 if (!(ty & T_SOLID)) {
                     float d = 0.0f;
                     int first = 1;
-                    pull_src(
-                        [&](int a, const float* src) {
-                            (void)a;
-                            d = first ? *src : d + *src;
-                            first = 0;
-                        },
-                        wr(x0 + rx - 2, nx), wr(y0 + ry - 2, ny), ti, ty);
+                    if (LBMWET_PAIR_BOX_RING2 && boxed) {
+                        box_src(
+                            [&](int a, float v) {
+                                (void)a;
+                                d = first ? v : d + v;
+                                first = 0;
+                            },
+                            rx - 2 + B::X0, ry - 2 + B::Y0, ti, ty);
+                    } else {
+                        pull_src(
+                            [&](int a, const float* src) {
+                                (void)a;
+                                d = first ? *src : d + *src;
+                                first = 0;
+                            },
+                            wr(x0 + rx - 2, nx), wr(y0 + ry - 2, ny), ti, ty);
+                    }
                     rho = ph.rho_ref + d;
                 }
                 sm.rho[rix(rx, ry)] = rho;
@@ -350,7 +377,7 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
 #pragma unroll
                     for (int a = 1; a < Q; ++a) {
                         const int ex = L::ex(a), ey = L::ey(a);
-                        if (!(sm.type[ti + ex + ey * YX] & T_SOLID)) {
+                        if (!(tyb[ti + ex + ey * YX] & T_SOLID)) {
                             num += float(L::wf(a)) * sm.rho[rix(px + 1 + ex, py + 1 + ey)];
                             den += float(L::wf(a));
                         }
@@ -409,14 +436,17 @@ __host__ __device__ __forceinline__ int pair_wrap(int x0, int y0, int nx, int ny
     return (x0 >= 3 && x0 + PTX + 2 < nx && y0 >= 3 && y0 + PNY + 2 < ny) ? 0 : 1;
 }
 
+// hst: shared memory for the halo ring's pulled distributions, [a][ring cell] (9 * SHELL floats),
+// used when box is null
 template <bool SOLID, class G, class Pre = NoHook, class Hook = NoHook>
 __device__ __forceinline__ void pair_tile(const G& g, int parity, const Phys<float>& ph, const PairRates& kr, int x0,
-                                          int y0, unsigned* err, PairSmem& sm, const float* box = nullptr,
-                                          const Pre& pre = Pre(), const Hook& hook = Hook()) {
+                                          int y0, unsigned* err, PairSmem& sm, float* hst, const float* box = nullptr,
+                                          int tbuf = 0, bool ty_ready = false, const Pre& pre = Pre(),
+                                          const Hook& hook = Hook()) {
     const int w = pair_wrap(x0, y0, g.nx, g.ny);
-    if (w == 0) pair_body<SOLID, 0>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
-    else if (w == 1) pair_body<SOLID, 1>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
-    else pair_body<SOLID, 2>(g, parity, ph, kr, x0, y0, err, sm, box, pre, hook);
+    if (w == 0) pair_body<SOLID, 0>(g, parity, ph, kr, x0, y0, err, sm, hst, box, tbuf, ty_ready, pre, hook);
+    else if (w == 1) pair_body<SOLID, 1>(g, parity, ph, kr, x0, y0, err, sm, hst, box, tbuf, ty_ready, pre, hook);
+    else pair_body<SOLID, 2>(g, parity, ph, kr, x0, y0, err, sm, hst, box, tbuf, ty_ready, pre, hook);
 }
 
 #ifndef LBMWET_PAIR_MINB
@@ -426,10 +456,11 @@ __device__ __forceinline__ void pair_tile(const G& g, int parity, const Phys<flo
 __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     pair_step(PairGrid g, const uint8_t* __restrict__ tile_solid, Phys<float> ph, PairRates kr, unsigned* err) {
     __shared__ PairSmem sm;
+    __shared__ float hst[9 * PairSmem::SHELL];
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     const bool solid = tile_solid ? tile_solid[tile] != 0 : true;
-    if (solid) pair_tile<true>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm);
-    else pair_tile<false>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm);
+    if (solid) pair_tile<true>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm, hst);
+    else pair_tile<false>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm, hst);
 }
 
 // Polls of an mbarrier before a wait gives up (flags ERR_TIMEOUT and goes on); far above any copy's
@@ -445,9 +476,11 @@ constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
 // publishes the index and copies that record with 16-byte cp.async copies that the next tile waits
 // for.  Every tile of a grid with TMA tensor maps (row length a multiple of 4 nodes) away from the
 // periodic edges pulls from a box that one TMA load brings into shared memory while the previous
-// tile finishes (issued right after that tile's phase 1, when the box is free).  One claim is made
-// per tile processed; the last CTA to finish resets the counter for the next launch (sched[1]
-// counts finished CTAs).
+// tile finishes (issued right after that tile's phase 1, when the box is free); such a tile holding
+// a solid node also gets its node types copied (cp.async) into the other type buffer meanwhile, and
+// takes its 2-node density ring from the box.  A tile without a box stages its halo ring in the
+// box's memory, which keeps the CTA under the 40 KB that lets 4 CTAs share a 164 KB carveout.  One claim is made per tile processed; the last CTA to
+// finish resets the counter for the next launch (sched[1] counts finished CTAs).
 __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     pair_step_batched(int parity, const BatchItem* __restrict__ items, int n_items, Phys<float> ph, PairRates kr,
                       unsigned* err, unsigned* sched) {
@@ -456,6 +489,7 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     using B = PairBox;
     __shared__ PairSmem sm;
     __shared__ alignas(128) float box[B::ELEMS];
+    static_assert(B::ELEMS >= 9 * PairSmem::SHELL, "the halo staging of unboxed tiles fits in the box");
     __shared__ alignas(8) uint64_t bar;
     __shared__ BatchItem s_item[3];
     __shared__ int s_idx[3];   // item index held by each record slot (n_items or more: none)
@@ -477,16 +511,21 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
         fence_mbar_init();
     }
     __syncthreads();
-    auto boxed = [](const BatchItem& r) { return r.tmap != nullptr && pair_wrap(r.x0, r.y0, r.nx, r.ny) == 0; };
+    // 1: the tile pulls from a TMA box, 0: from global memory
+    auto box_kind = [](const BatchItem& r) -> int {
+        return r.tmap != nullptr && pair_wrap(r.x0, r.y0, r.nx, r.ny) == 0 ? 1 : 0;
+    };
     auto issue = [&](const BatchItem& r) {
         fence_proxy_async();
         tma_load_box(box, static_cast<const char*>(r.tmap) + 128 * parity, r.x0 - B::X0, r.y0 - B::Y0, 0, &bar,
                      unsigned(B::ELEMS * sizeof(float)));
     };
     unsigned phase = 0;
-    bool cur_boxed = blockIdx.x < n_items && boxed(s_item[0]);
-    if (cur_boxed && tid == 0) issue(s_item[0]);
+    int cur_kind = blockIdx.x < n_items ? box_kind(s_item[0]) : 0;
+    if (cur_kind == 1 && tid == 0) issue(s_item[0]);
     int s0 = 0, s1 = 1, s2 = 2;   // ring slots of the current, next and after-next records
+    int tbuf = 0;                 // type buffer of the current tile
+    bool ty_ready = false;        // its types were copied during the previous tile
     for (int it = blockIdx.x; it < n_items;) {
         const BatchItem& item = s_item[s0];
         const BatchItem& nxt = s_item[s1];
@@ -502,27 +541,48 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
                 }
             }
         };
-        bool next_boxed = false;
+        int next_kind = 0;
+        bool next_types = false;
         auto hook = [&]() {
-            next_boxed = s_idx[s1] < n_items && boxed(nxt);
-            if (next_boxed && tid == 0) issue(nxt);
+            next_kind = s_idx[s1] < n_items ? box_kind(nxt) : 0;
+            if (next_kind == 1 && tid == 0) issue(nxt);
+            // an interior tile holding a solid: its node types (rows y0 - 3 .. y0 + 18, columns x0 - 4 ..
+            // x0 + 35, all inside the grid; rows start on 4-byte boundaries since nx % 4 == 0) into the
+            // other type buffer, 4 bytes per copy
+            next_types = next_kind == 1 && nxt.solid;
+            if (next_types) {
+                constexpr int CW = PairSmem::YX / 4;
+                if (tid < PairSmem::YY * CW) {
+                    const int r = tid / CW, c = tid % CW;
+                    cp_async(reinterpret_cast<float*>(&sm.type[tbuf ^ 1][r * PairSmem::YX + 4 * c]),
+                             reinterpret_cast<const float*>(nxt.type + (size_t)(nxt.y0 - 3 + r) * nxt.nx + nxt.x0 -
+                                                            4 + 4 * c));
+                }
+                cp_commit();
+            }
         };
-        const float* bx = nullptr;
-        if (cur_boxed) {
+        if (cur_kind == 1) {
             if (!mbar_wait(&bar, phase, MBAR_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
             phase ^= 1u;
-            bx = box;
         }
-        if (item.solid) pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
-        else pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm, bx, pre, hook);
+        const float* bx = cur_kind != 0 ? box : nullptr;
+        // a tile without a box stages its halo ring in the box's memory (no load targets it meanwhile:
+        // the next tile's TMA load is issued after this tile's phase 1)
+        if (item.solid)
+            pair_tile<true>(item, parity, ph, kr, item.x0, item.y0, err, sm, box, bx, tbuf, ty_ready, pre, hook);
+        else
+            pair_tile<false>(item, parity, ph, kr, item.x0, item.y0, err, sm, box, bx, tbuf, ty_ready, pre, hook);
         it = s_idx[s1];
         if (tid == 0 && it < n_items) claim = atomicAdd(sched, 1u);   // for the tile after `it`'s next
+        if (next_types) cp_wait<0>();   // the next tile's types (published by the barrier below)
         __syncthreads();   // this tile's threads are done with shared memory
+        if (next_types) tbuf ^= 1;
+        ty_ready = next_types;
         const int t = s0;
         s0 = s1;
         s1 = s2;
         s2 = t;
-        cur_boxed = next_boxed;
+        cur_kind = next_kind;
     }
     cp_wait<0>();
     if (tid == 0) {
