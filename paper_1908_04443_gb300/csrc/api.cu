@@ -117,13 +117,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 
 // TMA tensor map of one FP32 D2Q9 distribution buffer: dimensions (x, y, direction), the pair
 // kernel's box.  False where TMA cannot address the buffer (rows not a multiple of 16 bytes).
-bool encode_pair_map(CUtensorMap* m, void* f, int nx, int ny) {
+// f: a distribution buffer with row pitch fp and direction stride fs (nodes; multiples of 4)
+bool encode_pair_map(CUtensorMap* m, void* f, int nx, int ny, int fp, long long fs) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
-    if (!enc || nx % 4 != 0) return false;
+    if (!enc || fp % 4 != 0 || fs % 4 != 0) return false;
     int bx, by;
     pair_box_dims(&bx, &by);
     const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
-    const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * cuuint64_t(ny) * 4};
+    const cuuint64_t strides[2] = {cuuint64_t(fp) * 4, cuuint64_t(fs) * 4};
     const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 9};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -384,7 +385,10 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     }
 
     const size_t ssize = c.precision == LBM_FP64 ? sizeof(double) : sizeof(float);
-    h->fbytes = ssize * h->Q * (size_t)N;
+    // distributions: 2D rows padded to a multiple of 4 nodes (16-byte rows for TMA in FP32)
+    const int fpitch = h->D == 2 ? (nx + 3) / 4 * 4 : nx;
+    const long long fstride = (long long)fpitch * ny * nz;
+    h->fbytes = ssize * h->Q * (size_t)fstride;
     auto oom = [&](cudaError_t e, const char* what) {
         std::string m = std::string(what) + ": " + cudaGetErrorString(e);
         free_all(h);
@@ -405,6 +409,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     const size_t nw = h->wall_nodes.size();
     CKI(cudaMalloc(&h->d_kappa, sizeof(double) * (nw ? nw : 1)), "cudaMalloc kappa");
     CKI(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "memset err");
+    CKI(cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream), "memset f");   // padding included
     CKI(cudaMemsetAsync(h->f[1], 0, h->fbytes, h->stream), "memset f");
     CKI(cudaMemcpyAsync(h->d_wall_id, wall_id.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream), "copy wall_id");
     {
@@ -433,6 +438,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.ny = ny;
     p.nz = nz;
     p.N = N;
+    p.fp = fpitch;
+    p.fs = fstride;
     p.eos_kind = c.eos.kind;
     p.RT = c.eos.R * c.eos.T;
     p.a = c.eos.a;
@@ -499,6 +506,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             YGrid grid{nx, ny, h->mask.data(), BatchItem{}};
             grid.proto.f[0] = h->f[0];
             grid.proto.f[1] = h->f[1];
+            grid.proto.fp = fpitch;
+            grid.proto.fs = int(fstride);
             grid.proto.type = h->d_type;
             grid.proto.wall_id = h->d_wall_id;
             grid.proto.kappa_w = h->d_kappa;   // holds the scalar kappa at every wall node unless set per node
@@ -1037,6 +1046,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             g.proto.inst = i;
             g.proto.f[0] = h->f[0];
             g.proto.f[1] = h->f[1];
+            g.proto.fp = h->dp.fp;
+            g.proto.fs = int(h->dp.fs);
             g.proto.type = h->d_type;
             g.proto.wall_id = h->d_wall_id;
             g.proto.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
@@ -1058,8 +1069,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             bool any = false;
             for (int i = 0; i < n; ++i) {
                 lbm_handle* h = b->inst[i];
-                has_map[i] = encode_pair_map(&maps[2 * i], h->f[0], h->cfg.nx, h->cfg.ny) &&
-                             encode_pair_map(&maps[2 * i + 1], h->f[1], h->cfg.nx, h->cfg.ny);
+                has_map[i] = encode_pair_map(&maps[2 * i], h->f[0], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs) &&
+                             encode_pair_map(&maps[2 * i + 1], h->f[1], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs);
                 any = any || has_map[i];
             }
             if (any) {
@@ -1082,6 +1093,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             d.ny = h->cfg.ny;
             d.nz = h->cfg.nz;
             d.N = int(h->N);
+            d.fp = h->dp.fp;
+            d.fs = int(h->dp.fs);
             d.f[0] = h->f[0];
             d.f[1] = h->f[1];
             d.type = h->d_type;
@@ -1095,6 +1108,8 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
                     it.nx = d.nx;
                     it.ny = d.ny;
                     it.N = d.N;
+                    it.fp = d.fp;
+                    it.fs = d.fs;
                     it.x0 = x;
                     it.y0 = y;
                     it.y1 = std::min(y + ty, d.ny);

@@ -11,6 +11,11 @@ namespace lbmwet {
 struct DevParams {
     int nx, ny, nz;
     long long N;                 // nodes
+    // Distributions f[a][z][y][x] live at a * fs + (z * ny + y) * fp + x: 2D rows are padded to a
+    // multiple of 4 nodes (16 bytes in FP32) so that every grid has TMA tensor maps; per-node arrays
+    // (types, wall ids, fields) are not padded.
+    int fp;                      // row pitch of the distributions (nodes)
+    long long fs;                // stride between directions (nodes)
     int eos_kind;                // 0 PR, 1 CS
     double RT, a, b, aphi;       // EOS: R*T, a, b, a*phi(T) (PR)
     double two_over_G, G;        // Eq. 6 and Eq. 5
@@ -32,6 +37,7 @@ struct DevParams {
 // sigma, limiter bounds, body force, wall scheme) is shared by the batch.
 struct BatchInstance {
     int nx, ny, nz, N;
+    int fp, fs;                // distribution row pitch and direction stride
     void* f[2];                // the instance's two distribution buffers
     const uint8_t* type;
     const int* wall_id;
@@ -44,6 +50,7 @@ struct BatchInstance {
 struct alignas(16) BatchItem {
     int nx, ny, N, x0, y0, solid;   // solid: a solid node lies within the item's box + 3-node halo
     int inst, y1;
+    int fp, fs;                     // distribution row pitch and direction stride
     const void* f[2];
     const uint8_t* type;
     const int* wall_id;

@@ -91,6 +91,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     constexpr int RX = T::RX, RY = T::RY, RZ = T::RZ, PX = T::PX, PY = T::PY, PZ = T::PZ;
     constexpr int YX = T::YX, YY = T::YY, YZ = T::YZ, HZ = T::HZ, PZH = T::PZH, YZH = T::YZH;
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
+    const int fp = g.fp, fs = g.fs;   // distribution row pitch and direction stride
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     auto wrapc = [](int v, int n) { return WRAP == 0 ? v : (WRAP == 1 ? wrap1(v, n) : wrap_full(v, n)); };
     auto wx = [&](int v) { return wrapc(v, nx); };
@@ -126,20 +127,20 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     auto pull = [&](C (&f)[Q], int gx, int gy, int gz, int ti, uint8_t self) {
         if constexpr (WRAP == 0) {
             // every upstream node at a constant offset from the node itself
-            const int nxy = nx * ny;
-            const S* p = fin + ((gz * ny + gy) * nx + gx);
+            const int fpy = fp * ny;
+            const S* p = fin + ((gz * ny + gy) * fp + gx);
             if (!SOLID || (self & T_BULK)) {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-                    f[a] = C(p[a * N - ex - ey * nx - ez * nxy]);
+                    f[a] = C(p[a * fs - ex - ey * fp - ez * fpy]);
                 }
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
                     const bool bb = (sm.type[ti - ex - ey * YX - ez * YX * YY] & T_SOLID) != 0;
-                    f[a] = C(p[bb ? L::opp(a) * N : a * N - ex - ey * nx - ez * nxy]);
+                    f[a] = C(p[bb ? L::opp(a) * fs : a * fs - ex - ey * fp - ez * fpy]);
                 }
             }
             return;
@@ -147,13 +148,13 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         const int xm = wrap1(gx - 1, nx), xp = wrap1(gx + 1, nx);
         const int ym = wrap1(gy - 1, ny), yp = wrap1(gy + 1, ny);
         const int cx[3] = {xm, gx, xp};
-        const int ry[3] = {ym * nx, gy * nx, yp * nx};
+        const int ry[3] = {ym * fp, gy * fp, yp * fp};
         int pz[3];
         if (D == 3) {
-            const int nxy = nx * ny;
-            pz[0] = wrap1(gz - 1, nz) * nxy;
-            pz[1] = gz * nxy;
-            pz[2] = wrap1(gz + 1, nz) * nxy;
+            const int fpy = fp * ny;
+            pz[0] = wrap1(gz - 1, nz) * fpy;
+            pz[1] = gz * fpy;
+            pz[2] = wrap1(gz + 1, nz) * fpy;
         } else {
             pz[0] = pz[1] = pz[2] = 0;
         }
@@ -162,7 +163,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-                f[a] = C(fin[a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
+                f[a] = C(fin[a * fs + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
             }
         } else {
             // next to a solid: one load per direction, the bounce-back source chosen by address
@@ -170,7 +171,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
             for (int a = 0; a < Q; ++a) {
                 const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
                 const bool bb = (sm.type[ti - ex - ey * YX - ez * YX * YY] & T_SOLID) != 0;
-                f[a] = C(fin[bb ? L::opp(a) * N + gi : a * N + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
+                f[a] = C(fin[bb ? L::opp(a) * fs + gi : a * fs + pz[1 - ez] + ry[1 - ey] + cx[1 - ex]]);
             }
         }
     };
@@ -178,7 +179,8 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     // 1a. the tile's own node
     const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
     const int gx = wx(x0 + lx), gy = wy(y0 + ly), gz = wz(z0 + lz);
-    const int gi = (gz * ny + gy) * nx + gx;
+    const int gi = (gz * ny + gy) * nx + gx;   // node index (per-node arrays)
+    const int fi = (gz * ny + gy) * fp + gx;   // distribution index
     const int my_ti = tix(lx + 3, ly + 3, lz + YZH);
     const uint8_t my_type = type_at(my_ti);
     const bool my_fluid = !(my_type & T_SOLID);
@@ -387,7 +389,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
         collide_d3q19<C>(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, ph.r);
     }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) fout[a * N + gi] = S(f[a]);
+    for (int a = 0; a < Q; ++a) fout[a * fs + fi] = S(f[a]);
 }
 
 // Tile shapes per lattice and precision (one thread per node).
@@ -491,6 +493,8 @@ __global__ void __launch_bounds__(TileShape<L, S>::X* TileShape<L, S>::Y* TileSh
         g.ny = item.ny;
         g.nz = 1;
         g.N = item.N;
+        g.fp = item.fp;
+        g.fs = item.fs;
         g.type = item.type;
         g.tile_solid = nullptr;
         g.wall_id = item.wall_id;
@@ -535,14 +539,15 @@ template <class L, class S, bool FROM_FEQ>
 __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double* __restrict__ src0,
                                 const double* __restrict__ src1) {
     constexpr int Q = L::Q;
-    const long long N = p.N;
+    const long long N = p.N, fs = p.fs;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
-        if (p.type[g] & T_SOLID) {
-            for (int b = 0; b < Q; ++b) fout[(long long)b * N + g] = S(0);
-            continue;
-        }
         int x, y, z;
         coords(g, p.nx, p.ny, x, y, z);
+        const long long fg = ((long long)z * p.ny + y) * p.fp + x;   // distribution index of node g
+        if (p.type[g] & T_SOLID) {
+            for (int b = 0; b < Q; ++b) fout[b * fs + fg] = S(0);
+            continue;
+        }
         for (int b = 0; b < Q; ++b) {
             const int tx = wrap1(x + L::ex(b), p.nx), ty = wrap1(y + L::ey(b), p.ny);
             const int tz = (L::D == 3) ? wrap1(z + L::ez(b), p.nz) : 0;
@@ -566,7 +571,7 @@ __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double*
             } else {
                 v = src0[(long long)a * N + src];
             }
-            fout[(long long)b * N + g] = S(v - L::w(b) * p.rho_ref);
+            fout[b * fs + fg] = S(v - L::w(b) * p.rho_ref);
         }
     }
 }
@@ -574,7 +579,7 @@ __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double*
 template <class L, class S>
 __global__ void get_state_kernel(const S* __restrict__ fin, DevParams p, double* __restrict__ fpost) {
     constexpr int Q = L::Q;
-    const long long N = p.N;
+    const long long N = p.N, fs = p.fs;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
         if (p.type[g] & T_SOLID) {
             for (int a = 0; a < Q; ++a) fpost[(long long)a * N + g] = 0.0;
@@ -582,13 +587,15 @@ __global__ void get_state_kernel(const S* __restrict__ fin, DevParams p, double*
         }
         int x, y, z;
         coords(g, p.nx, p.ny, x, y, z);
+        const long long fg = ((long long)z * p.ny + y) * p.fp + x;
         for (int a = 0; a < Q; ++a) {
             const int sx = wrap1(x - L::ex(a), p.nx), sy = wrap1(y - L::ey(a), p.ny);
             const int sz = (L::D == 3) ? wrap1(z - L::ez(a), p.nz) : 0;
             const long long s = ((long long)sz * p.ny + sy) * p.nx + sx;
+            const long long fsrc = ((long long)sz * p.ny + sy) * p.fp + sx;
             double v;
-            if (p.type[s] & T_SOLID) v = double(fin[(long long)L::opp(a) * N + g]);
-            else v = double(fin[(long long)a * N + s]);
+            if (p.type[s] & T_SOLID) v = double(fin[L::opp(a) * fs + fg]);
+            else v = double(fin[a * fs + fsrc]);
             fpost[(long long)a * N + g] = v + L::w(a) * p.rho_ref;
         }
     }
@@ -648,6 +655,8 @@ static Geo geo_of(const DevParams& p) {
     g.ny = p.ny;
     g.nz = p.nz;
     g.N = int(p.N);
+    g.fp = p.fp;
+    g.fs = int(p.fs);
     g.type = p.type;
     g.tile_solid = p.tile_solid;
     g.wall_id = p.wall_id;

@@ -52,7 +52,8 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
     constexpr int Q = 9, TW = YShape<S>::TW;
     constexpr int LAG = SOLID ? 2 : 1;      // rows between pull and collision
     constexpr int AHEAD = SOLID ? 1 : 2;    // rows of pulls in flight
-    const int nx = g.nx, ny = g.ny, N = g.N;
+    const int nx = g.nx, ny = g.ny;
+    const int fp = g.fp, fs = g.fs;   // distribution row pitch and direction stride
     const int hx = threadIdx.x, ti = hx + 1;
     const bool small = nx < TW + 8 || ny < 8;
     auto wx = [&](int v) { return small ? wrap_full(v, nx) : wrap1(v, nx); };
@@ -74,13 +75,13 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
     auto issue = [&](int y) {
         if (active) {
             const int gy = wy(y);
-            const int r[3] = {wrap1(gy - 1, ny) * nx, gy * nx, wrap1(gy + 1, ny) * nx};
+            const int r[3] = {wrap1(gy - 1, ny) * fp, gy * fp, wrap1(gy + 1, ny) * fp};
             S* dst = &sm.f[y & 3][0][hx];
             uint8_t self = uint8_t(T_BULK);
             if constexpr (SOLID) self = sm.type[y & 7][ti];
             if (!SOLID || (self & T_BULK)) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) cp_async(dst + a * TW, fin + a * N + r[1 - L::ey(a)] + col[1 - L::ex(a)]);
+                for (int a = 0; a < Q; ++a) cp_async(dst + a * TW, fin + a * fs + r[1 - L::ey(a)] + col[1 - L::ex(a)]);
             } else if (!(self & T_SOLID)) {
                 // next to a solid: a link whose upstream node is solid brings back the cell's own
                 // outgoing population (halfway bounce-back)
@@ -88,7 +89,7 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
                 for (int a = 0; a < Q; ++a) {
                     const int ex = L::ex(a), ey = L::ey(a);
                     const bool bb = (sm.type[(y - ey) & 7][ti - ex] & T_SOLID) != 0;
-                    cp_async(dst + a * TW, fin + (bb ? L::opp(a) * N + r[1] + gx : a * N + r[1 - ey] + col[1 - ex]));
+                    cp_async(dst + a * TW, fin + (bb ? L::opp(a) * fs + r[1] + gx : a * fs + r[1 - ey] + col[1 - ex]));
                 }
             }
         }
@@ -197,9 +198,9 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
             const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv;
             const C X = cdiv(Fmx * Fmx + Fmy * Fmy, psi_c * psi_c);
             collide_d2q9<C>(f, drho, rho, ux, uy, Fx, Fy, X, ph.r);
-            const int gi = yc * nx + gx;
+            const int fi = yc * fp + gx;
 #pragma unroll
-            for (int a = 0; a < Q; ++a) fout[a * N + gi] = S(f[a]);
+            for (int a = 0; a < Q; ++a) fout[a * fs + fi] = S(f[a]);
         }
         load_types(yl + 3);
     }
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(YShape<S>::TW, YShape<S>::MINB)
         g.ny = item.ny;
         g.nz = 1;
         g.N = item.N;
+        g.fp = item.fp;
+        g.fs = item.fs;
         g.type = item.type;
         g.tile_solid = nullptr;
         g.wall_id = item.wall_id;

@@ -135,6 +135,7 @@ struct PairSmem {
 // the grid needs a register across the tile's barriers.
 struct PairGrid {
     int nx, ny, N;
+    int fp, fs;   // distribution row pitch and direction stride
     const uint8_t* type;
     const int* wall_id;
     const double* kappa_w;
@@ -157,7 +158,8 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     constexpr int Q = 9, NT = PTX * PTY;
     using Sm = PairSmem;
     constexpr int RX = Sm::RX, PX = Sm::PX, PY = Sm::PY, YX = Sm::YX, YY = Sm::YY, SHELL = Sm::SHELL;
-    const int nx = g.nx, ny = g.ny, N = g.N;
+    const int nx = g.nx, ny = g.ny;
+    const int fp = g.fp, fs = g.fs;   // distribution row pitch and direction stride
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * PTX + lx;
     const float* __restrict__ fin = static_cast<const float*>(g.f[parity]);
     auto wr = [](int v, int n) { return WRAP == 0 ? v : (WRAP == 1 ? wrap1(v, n) : wrap_full(v, n)); };
@@ -192,29 +194,29 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     // source of every distribution streaming into node (gx, gy), handed to sink(a, pointer)
     auto pull_src = [&](auto&& sink, int gx, int gy, int ti, uint8_t self) {
         if constexpr (WRAP == 0) {
-            const float* p = fin + (gy * nx + gx);
+            const float* p = fin + (gy * fp + gx);
             if (!SOLID || (self & T_BULK)) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) sink(a, p + (a * N - L::ex(a) - L::ey(a) * nx));
+                for (int a = 0; a < Q; ++a) sink(a, p + (a * fs - L::ex(a) - L::ey(a) * fp));
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     const bool bb = (tyb[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
-                    sink(a, p + (bb ? L::opp(a) * N : a * N - L::ex(a) - L::ey(a) * nx));
+                    sink(a, p + (bb ? L::opp(a) * fs : a * fs - L::ex(a) - L::ey(a) * fp));
                 }
             }
         } else {
             const int cx[3] = {wrap1(gx - 1, nx), gx, wrap1(gx + 1, nx)};
-            const int ry[3] = {wrap1(gy - 1, ny) * nx, gy * nx, wrap1(gy + 1, ny) * nx};
+            const int ry[3] = {wrap1(gy - 1, ny) * fp, gy * fp, wrap1(gy + 1, ny) * fp};
             if (!SOLID || (self & T_BULK)) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) sink(a, fin + (a * N + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
+                for (int a = 0; a < Q; ++a) sink(a, fin + (a * fs + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     const bool bb = (tyb[ti - L::ex(a) - L::ey(a) * YX] & T_SOLID) != 0;
-                    sink(a, fin + (bb ? L::opp(a) * N + ry[1] + cx[1]
-                                      : a * N + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
+                    sink(a, fin + (bb ? L::opp(a) * fs + ry[1] + cx[1]
+                                      : a * fs + ry[1 - L::ey(a)] + cx[1 - L::ex(a)]));
                 }
             }
         }
@@ -422,12 +424,12 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv;
     const V2 X = div2(fma2(Fmx, Fmx, Fmy * Fmy), psi_c * psi_c);
     collide2(f, drho, rho, ux, uy, Fx, Fy, X, kr);
-    const int gia = (y0 + ly) * nx + x0 + lx, gib = gia + PTY * nx;
+    const int gia = (y0 + ly) * fp + x0 + lx, gib = gia + PTY * fp;   // distribution indices
     float* __restrict__ fout = static_cast<float*>(const_cast<void*>(g.f[parity ^ 1]));
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        if (va) fout[a * N + gia] = f[a].v.x;
-        if (vb) fout[a * N + gib] = f[a].v.y;
+        if (va) fout[a * fs + gia] = f[a].v.x;
+        if (vb) fout[a * fs + gib] = f[a].v.y;
     }
 }
 
@@ -546,10 +548,10 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
         auto hook = [&]() {
             next_kind = s_idx[s1] < n_items ? box_kind(nxt) : 0;
             if (next_kind == 1 && tid == 0) issue(nxt);
-            // an interior tile holding a solid: its node types (rows y0 - 3 .. y0 + 18, columns x0 - 4 ..
-            // x0 + 35, all inside the grid; rows start on 4-byte boundaries since nx % 4 == 0) into the
-            // other type buffer, 4 bytes per copy
-            next_types = next_kind == 1 && nxt.solid;
+            // an interior tile holding a solid, of a grid whose rows are a multiple of 4 nodes: its node
+            // types (rows y0 - 3 .. y0 + 18, columns x0 - 4 .. x0 + 35, all inside the grid; every row
+            // segment starts on a 4-byte boundary) into the other type buffer, 4 bytes per copy
+            next_types = next_kind == 1 && nxt.solid && (nxt.nx & 3) == 0;
             if (next_types) {
                 constexpr int CW = PairSmem::YX / 4;
                 if (tid < PairSmem::YY * CW) {
@@ -618,6 +620,8 @@ cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cu
     g.nx = p.nx;
     g.ny = p.ny;
     g.N = int(p.N);
+    g.fp = p.fp;
+    g.fs = int(p.fs);
     g.type = p.type;
     g.wall_id = p.wall_id;
     g.kappa_w = p.kappa_w;

@@ -283,21 +283,34 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
     __syncthreads();
 
     for (int zl = zb - 2; zl <= ze + 1; zl += 2) {
-        // A. the lead pair: own cells, the 1-node xy halo ring, the 2-node ring near solids
-        do_pair(zl, lx + 2, ly + 2, true, tid, zl >= zb && zl < ze, zl + 1 >= zb && zl + 1 < ze);
+        // A. the lead pair: own cells, the 1-node xy halo ring, the 2-node ring near solids.  One
+        // loop over the thread's cells keeps a single copy of the pull code in the kernel.
         using Ring1 = Shell<PX, PY, 1, 2>;
-        for (int k = tid; k < Ring1::COUNT; k += NT) {
-            int px, py, pz;
-            Ring1::cell(k, px, py, pz);
-            do_pair(zl, px + 1, py + 1, true, -1, false, false);
-        }
-        if constexpr (SOLID) {
-            using Ring2 = Shell<RX, RY, 1, 2>;
-            for (int k = tid; k < Ring2::COUNT; k += NT) {
-                int rx, ry, rz;
-                Ring2::cell(k, rx, ry, rz);
-                do_pair(zl, rx, ry, false, -1, false, false);
+        using Ring2 = Shell<RX, RY, 1, 2>;
+        constexpr int N1 = (Ring1::COUNT + NT - 1) / NT, N2 = SOLID ? (Ring2::COUNT + NT - 1) / NT : 0;
+#pragma unroll 1
+        for (int c = 0; c < 1 + N1 + N2; ++c) {
+            int hx, hy, own = -1;
+            bool want_psi = true;
+            if (c == 0) {
+                hx = lx + 2;
+                hy = ly + 2;
+                own = tid;
+            } else if (c <= N1) {
+                const int k = tid + (c - 1) * NT;
+                if (k >= Ring1::COUNT) continue;
+                int px, py, pz;
+                Ring1::cell(k, px, py, pz);
+                hx = px + 1;
+                hy = py + 1;
+            } else {
+                const int k = tid + (c - 1 - N1) * NT;
+                if (k >= Ring2::COUNT) continue;
+                int pz;
+                Ring2::cell(k, hx, hy, pz);
+                want_psi = false;
             }
+            do_pair(zl, hx, hy, want_psi, own, own >= 0 && zl >= zb && zl < ze, own >= 0 && zl + 1 >= zb && zl + 1 < ze);
         }
         __syncthreads();
 

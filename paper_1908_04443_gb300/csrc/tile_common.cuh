@@ -50,6 +50,7 @@ Phys<C> make_phys(const DevParams& p) {
 // geometry of one grid
 struct Geo {
     int nx, ny, nz, N;
+    int fp, fs;   // distributions: row pitch (>= nx) and stride between directions (>= fp * ny * nz)
     const uint8_t* type;
     const uint8_t* tile_solid;   // per tile (single-grid kernel) or null
     const int* wall_id;
