@@ -385,8 +385,10 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     }
 
     const size_t ssize = c.precision == LBM_FP64 ? sizeof(double) : sizeof(float);
-    // distributions: 2D rows padded to a multiple of 4 nodes (16-byte rows for TMA in FP32)
-    const int fpitch = h->D == 2 ? (nx + 3) / 4 * 4 : nx;
+    // distributions: 2D rows padded to a multiple of 32 nodes (128-byte rows in FP32: TMA needs
+    // 16-byte row strides, and a row that starts a cache line keeps a warp's 32 consecutive nodes in
+    // one line)
+    const int fpitch = h->D == 2 ? (nx + 31) / 32 * 32 : nx;
     const long long fstride = (long long)fpitch * ny * nz;
     h->fbytes = ssize * h->Q * (size_t)fstride;
     auto oom = [&](cudaError_t e, const char* what) {

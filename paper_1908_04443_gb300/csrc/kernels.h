@@ -12,8 +12,8 @@ struct DevParams {
     int nx, ny, nz;
     long long N;                 // nodes
     // Distributions f[a][z][y][x] live at a * fs + (z * ny + y) * fp + x: 2D rows are padded to a
-    // multiple of 4 nodes (16 bytes in FP32) so that every grid has TMA tensor maps; per-node arrays
-    // (types, wall ids, fields) are not padded.
+    // multiple of 32 nodes (128 bytes in FP32) so that every grid has TMA tensor maps and every row
+    // starts a cache line; per-node arrays (types, wall ids, fields) are not padded.
     int fp;                      // row pitch of the distributions (nodes)
     long long fs;                // stride between directions (nodes)
     int eos_kind;                // 0 PR, 1 CS

@@ -476,13 +476,14 @@ constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
 // shared slots: the current tile's, the next tile's and the one after.  Thread 0 claims the one
 // after at the end of the previous tile (few registers are live there), and early in phase 1 it
 // publishes the index and copies that record with 16-byte cp.async copies that the next tile waits
-// for.  Every tile of a grid with TMA tensor maps (row length a multiple of 4 nodes) away from the
-// periodic edges pulls from a box that one TMA load brings into shared memory while the previous
-// tile finishes (issued right after that tile's phase 1, when the box is free); such a tile holding
-// a solid node also gets its node types copied (cp.async) into the other type buffer meanwhile, and
-// takes its 2-node density ring from the box.  A tile without a box stages its halo ring in the
-// box's memory, which keeps the CTA under the 40 KB that lets 4 CTAs share a 164 KB carveout.  One claim is made per tile processed; the last CTA to
-// finish resets the counter for the next launch (sched[1] counts finished CTAs).
+// for.  Every tile away from the periodic edges of a grid with TMA tensor maps (every 2D grid: the
+// distribution rows are padded to 128 bytes) pulls from a box that one TMA load brings into shared
+// memory while the previous tile finishes (issued right after that tile's phase 1, when the box is
+// free); such a tile holding a solid node also gets its node types copied (cp.async) into the other
+// type buffer meanwhile, and takes its 2-node density ring from the box.  A tile without a box
+// stages its halo ring in the box's memory, which keeps the CTA under the 40 KB that lets 4 CTAs
+// share a 164 KB carveout.  One claim is made per tile processed; the last CTA to finish resets the
+// counter for the next launch (sched[1] counts finished CTAs).
 __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     pair_step_batched(int parity, const BatchItem* __restrict__ items, int n_items, Phys<float> ph, PairRates kr,
                       unsigned* err, unsigned* sched) {

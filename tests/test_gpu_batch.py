@@ -100,10 +100,9 @@ def test_batch_member_rules():
 @pytest.mark.parametrize("kernel", ["tile", "pair"])
 def test_batch_wide_grids_equal_single_runs(kernel):
     """FP32 batches of grids with interior tiles (no periodic wrap) as well as edge and wall tiles:
-    every instance evolves exactly as the grid stepped alone.  The pair kernel pulls every tile of a
-    grid whose rows are a multiple of 4 nodes long from a shared-memory box (TMA for interior tiles,
-    cp.async at wrapped coordinates for edge tiles, a grid narrower than the box included) and the
-    other grids from global memory; the grid stepped alone pulls from global memory."""
+    every instance evolves exactly as the grid stepped alone.  The pair kernel pulls the interior
+    tiles of every grid from a TMA box in shared memory and edge tiles and grids narrower than a box
+    from global memory; the grid stepped alone pulls from global memory."""
     from paper_1908_04443_gb300 import lbmwet as L
     a = drop_on_cylinder((96, 256), (128.0, 30.0), 14.0, (128.0, 58.0), 15.0, kappa=0.15, step_kernel=kernel)
     b = drop_on_cylinder((120, 200), (60.0, 50.0), 18.0, (60.0, 86.0), 19.0, kappa=-0.02, step_kernel=kernel)
@@ -127,7 +126,7 @@ def test_batch_wide_grids_equal_single_runs(kernel):
 
 def test_batch_row_padding_residues():
     """Grid widths of every residue mod 4 (81, 82, 83, 84 columns): the distributions' rows are padded
-    to a multiple of 4 nodes, so every grid has TMA tensor maps and its interior tiles pull from a
+    to a multiple of 32 nodes, so every grid has TMA tensor maps and its interior tiles pull from a
     box.  Each instance evolves exactly as the grid stepped alone, and one batched step agrees with
     the FP64 oracle."""
     from paper_1908_04443_gb300 import lbmwet as L
