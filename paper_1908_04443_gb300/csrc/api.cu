@@ -74,28 +74,28 @@ namespace {
 // touches (the full tile, including cells of a ragged tile that wrap past the grid edge, plus a
 // 3-node halo; no z halo in 2D)?  Tiles without one skip the node-type staging.
 std::vector<uint8_t> tile_solid_flags(const uint8_t* mask, int nx, int ny, int nz, const int t[3], int D) {
+    const int n[3] = {nx, ny, nz};
     const int tiles[3] = {(nx + t[0] - 1) / t[0], (ny + t[1] - 1) / t[1], (nz + t[2] - 1) / t[2]};
-    const int hz = D == 3 ? 3 : 0;
-    std::vector<uint8_t> out((size_t)tiles[0] * tiles[1] * tiles[2], 0);
-    for (int tz = 0; tz < tiles[2]; ++tz)
-        for (int ty = 0; ty < tiles[1]; ++ty)
-            for (int tx = 0; tx < tiles[0]; ++tx) {
-                bool found = false;
-                for (int dz = -hz; dz < (D == 3 ? t[2] + hz : 1) && !found; ++dz) {
-                    const int z = ((tz * t[2] + dz) % nz + nz) % nz;
-                    for (int dy = -3; dy < t[1] + 3 && !found; ++dy) {
-                        const int y = ((ty * t[1] + dy) % ny + ny) % ny;
-                        const uint8_t* row = mask + ((long long)z * ny + y) * nx;
-                        for (int dx = -3; dx < t[0] + 3; ++dx) {
-                            if (row[((tx * t[0] + dx) % nx + nx) % nx]) {
-                                found = true;
-                                break;
-                            }
-                        }
-                    }
-                }
-                out[((size_t)tz * tiles[1] + ty) * tiles[0] + tx] = found ? 1 : 0;
+    const int halo[3] = {3, 3, D == 3 ? 3 : 0};
+    // per axis and coordinate: the tiles whose box (tile + halo, wrapped) covers it
+    std::vector<std::vector<int>> cover[3];
+    for (int d = 0; d < 3; ++d) {
+        cover[d].assign(n[d], {});
+        for (int k = 0; k < tiles[d]; ++k)
+            for (int o = -halo[d]; o < t[d] + halo[d]; ++o) {
+                std::vector<int>& c = cover[d][((k * t[d] + o) % n[d] + n[d]) % n[d]];
+                if (c.empty() || c.back() != k) c.push_back(k);
             }
+    }
+    std::vector<uint8_t> out((size_t)tiles[0] * tiles[1] * tiles[2], 0);
+    const long long N = (long long)nx * ny * nz;
+    for (long long g = 0; g < N; ++g) {
+        if (!mask[g]) continue;
+        const int x = int(g % nx), y = int((g / nx) % ny), z = int(g / ((long long)nx * ny));
+        for (int kz : cover[2][z])
+            for (int ky : cover[1][y])
+                for (int kx : cover[0][x]) out[((size_t)kz * tiles[1] + ky) * tiles[0] + kx] = 1;
+    }
     return out;
 }
 
@@ -418,18 +418,18 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         std::vector<double> kap(nw ? nw : 1, c.kappa);
         if (kappa_per_wall)
             for (size_t i = 0; i < nw; ++i) kap[i] = kappa_per_wall[i];
+        // (a copy from pageable memory has left the host buffer when the call returns)
         CKI(cudaMemcpyAsync(h->d_kappa, kap.data(), sizeof(double) * kap.size(), cudaMemcpyHostToDevice, h->stream),
             "copy kappa");
-        CKI(cudaStreamSynchronize(h->stream), "sync");
     }
-    // node classification on the device from the mask
+    // node classification on the device from the mask (stream-ordered scratch: no device-wide
+    // synchronisation for its allocation and release)
     {
         uint8_t* d_mask = nullptr;
-        CKI(cudaMalloc(&d_mask, N), "cudaMalloc mask");
+        CKI(cudaMallocAsync(reinterpret_cast<void**>(&d_mask), N, h->stream), "cudaMalloc mask");
         e = cudaMemcpyAsync(d_mask, solid_mask, N, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = launch_classify(h->lat, d_mask, h->d_type, nx, ny, nz, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(d_mask);
+        cudaFreeAsync(d_mask, h->stream);
         if (e != cudaSuccess) return oom(e, "classify");
         h->launches += 1;
     }
@@ -478,7 +478,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     {
         double* d_rho0 = nullptr;
         double* d_u0 = nullptr;
-        CKI(cudaMalloc(&d_rho0, sizeof(double) * N), "cudaMalloc rho0");
+        CKI(cudaMallocAsync(reinterpret_cast<void**>(&d_rho0), sizeof(double) * N, h->stream), "cudaMalloc rho0");
         std::vector<double> r0;
         const double* src = rho0;
         if (!rho0) {
@@ -487,14 +487,14 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         }
         e = cudaMemcpyAsync(d_rho0, src, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess && u0) {
-            e = cudaMalloc(&d_u0, sizeof(double) * N * h->D);
+            e = cudaMallocAsync(reinterpret_cast<void**>(&d_u0), sizeof(double) * N * h->D, h->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_u0, u0, sizeof(double) * N * h->D, cudaMemcpyHostToDevice, h->stream);
         }
         if (e == cudaSuccess) e = launch_init(h->lat, h->prec, h->f[0], p, d_rho0, d_u0, h->stream);
+        cudaFreeAsync(d_rho0, h->stream);
+        if (d_u0) cudaFreeAsync(d_u0, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(d_rho0);
-        cudaFree(d_u0);
         if (e != cudaSuccess) return oom(e, "initial state");
         h->launches += 1;
     }
@@ -531,7 +531,6 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             CKI(cudaMemcpyAsync(h->d_pair_solid, h->pair_solid.data(), h->pair_solid.size(), cudaMemcpyHostToDevice,
                                 h->stream),
                 "copy tile flags");
-            CKI(cudaStreamSynchronize(h->stream), "sync");
             h->dp.pair_solid = h->d_pair_solid;
         }
     }

@@ -90,10 +90,19 @@ const double GL_W[8] = {0.1894506104550685, 0.1826034150449236, 0.16915651939500
 
 double critical_temperature(const EosHost& e) {
     if (e.kind == 0) return 0.0778 * e.a / (0.45724 * e.b * e.R);
-    // C-S: the temperature at which min_rho dp/drho = 0
+    // C-S: the temperature at which min_rho dp/drho = 0, a few milliseconds of scans and bisection;
+    // remembered for the last (a, b, R) of this thread, since a batch initialises many grids with
+    // one equation of state
+    thread_local double last_a = -1.0, last_b = -1.0, last_R = -1.0, last_tc = 0.0;
+    if (e.a == last_a && e.b == last_b && e.R == last_R) return last_tc;
     double lo = 1e-12, hi = 1.0;
     while (min_dp(e, hi, 0.0, nullptr) < 0) hi *= 2.0;
-    return bisect([&](double T) { return min_dp(e, T, 0.0, nullptr); }, lo, hi);
+    const double tc = bisect([&](double T) { return min_dp(e, T, 0.0, nullptr); }, lo, hi);
+    last_a = e.a;
+    last_b = e.b;
+    last_R = e.R;
+    last_tc = tc;
+    return tc;
 }
 
 double eos_pressure(const EosHost& e, double rho) {
@@ -103,7 +112,31 @@ double eos_pressure(const EosHost& e, double rho) {
 
 double eos_aphi(const EosHost& e) { return e.kind == 0 ? e.a * pr_phi(e) : e.a; }
 
+namespace {
+bool coexistence_solve(const EosHost& e, double* rho_g, double* rho_l);
+}
+
+// The Maxwell construction is tens of milliseconds of root finding and quadrature: remembered for
+// the last EOS (kind and every constant) of this thread, since a batch initialises many grids with
+// one equation of state.
 bool coexistence(const EosHost& e, double* rho_g, double* rho_l) {
+    thread_local bool have = false, last_ok = false;
+    thread_local EosHost last{};
+    thread_local double last_g = 0.0, last_l = 0.0;
+    if (!(have && e.kind == last.kind && e.a == last.a && e.b == last.b && e.R == last.R && e.T == last.T &&
+          e.omega == last.omega)) {
+        last_ok = coexistence_solve(e, &last_g, &last_l);
+        last = e;
+        have = true;
+    }
+    *rho_g = last_g;
+    *rho_l = last_l;
+    return last_ok;
+}
+
+namespace {
+
+bool coexistence_solve(const EosHost& e, double* rho_g, double* rho_l) {
     const double T = e.T;
     const double aphi = e.kind == 0 ? e.a * pr_phi(e) : 0.0;
     double rm;
@@ -148,5 +181,7 @@ bool coexistence(const EosHost& e, double* rho_g, double* rho_l) {
     roots(ps, rho_g, rho_l);
     return std::isfinite(*rho_g) && std::isfinite(*rho_l) && *rho_g < *rho_l;
 }
+
+}  // namespace
 
 }  // namespace lbmwet
