@@ -49,6 +49,26 @@ NCU_TRAFFIC = {
 }
 
 
+# FP64 floating-point operations per node update of the FP64 batched tile kernel
+# (fused_step_batched<D2Q9, double>) on the 600 x 400 sweep, from ncu: (2 x DFMA + DADD + DMUL thread
+# instructions of one launch) / nodes = (2 x 478,996,920 + 503,049,168 + 231,630,840) / 5,760,000;
+# keyed by a hash of the tile kernel's sources.
+FP64_FLOPS_PER_NODE = {
+    ("c2", "a349d2cec445c427"): 293.86,
+}
+# FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
+# SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+
+
+def tile_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the tile kernel's sources
+        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in ("step2p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the pair kernel's sources
@@ -366,11 +386,20 @@ def device_rate(L, torch, stream, name, steps, flush, precision=None):
         with open(pk_path) as fh:
             peak = json.load(fh).get("hbm_gbs", peak)
     gbs = bytes_per_lu(wls[0].lattice, precision) * nodes / (ms * 1e-3) / 1e9
-    return {"workload": label, "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 5),
-            "l2": "flushed before each timed step" if use_flush else "inputs larger than L2, no flush",
-            "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT, "achieved_gbs": round(gbs, 1),
-            "frac_of_measured_hbm": round(gbs / peak, 4),
-            "bound": "hbm" if precision == "fp32" else "fp64 pipe (GB300 FP64 is far below its FP32 rate)"}
+    out = {"workload": label, "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 5),
+           "l2": "flushed before each timed step" if use_flush else "inputs larger than L2, no flush",
+           "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT, "achieved_gbs": round(gbs, 1),
+           "frac_of_measured_hbm": round(gbs / peak, 4), "bound": "hbm"}
+    if precision == "fp64":
+        # GB300's FP64 rate is far below its FP32 rate: the FP64 step is bound by the FP64 pipe
+        fpn = FP64_FLOPS_PER_NODE.get((name, tile_kernel_hash()))
+        out["bound"] = "alu"
+        out["alu_roofline"] = {
+            "flops_per_node": fpn, "unit": "GFLOP/s", "peak": round(FP64_PEAK_GFLOPS, 1),
+            "peak_source": "derived: 152 SMs x 4 FP64 flops per SM per clock x 2.07 GHz (1.25 TFLOP/s nominal)",
+            "achieved": None if fpn is None else round(fpn * nodes / (ms * 1e-3) / 1e9, 1),
+            "frac": None if fpn is None else round(fpn * nodes / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, 4)}
+    return out
 
 
 def run_ours(args):
