@@ -47,6 +47,9 @@ def brute_step(f, solid, params):
         if fluid(c):
             psi[c] = psi_of(rho[c])
             continue
+        if params.wall == "SF":          # Martys-Chen: no virtual density, psi = 0 on solids
+            psi[c] = 0.0
+            continue
         num = den = 0.0
         touching = False
         for a in range(1, q):
@@ -80,6 +83,10 @@ def brute_step(f, solid, params):
             Fm += lat.WF[a] * psi[_wrap(plus(c, lat.E[a]), dims)] * lat.E[a]
         Fm = -params.G * psi[cc] * Fm
         F = Fm + np.asarray(params.body_force[:d])
+        if params.wall == "SF":          # Eq. 8: adhesion to the solid neighbours
+            for a in range(1, q):
+                if not fluid(plus(c, lat.E[a])):
+                    F = F - params.Gw * rho[cc] * lat.WF[a] * lat.E[a]
         fv = np.array([at(f[a], c) for a in range(q)])
         r = rho[cc]
         u = (lat.E.T.astype(float) @ fv + 0.5 * F) / r

@@ -1,6 +1,7 @@
 """Physics pins of the oracle's time step: brute force on tiny grids, exact mass conservation,
 mirror symmetry, Maxwell coexistence of a flat interface, the Poiseuille closed form with magic
-MRT rates, the Laplace law, and the flat-wall contact angle of the standard IVD case."""
+MRT rates, the Laplace law, the flat-wall contact angle of the standard IVD case, and the adhesion
+force of the solid-fluid interaction scheme (Eq. 8) in closed form."""
 import numpy as np
 import pytest
 
@@ -26,6 +27,8 @@ def _params(name, eos, g, l, **kw):
     ("D2Q9", (8, 8), 0.0, "VD"),
     ("D3Q19", (6, 6, 5), 0.2, "IVD"),
     ("D3Q19", (5, 6, 6), -0.05, "IVD"),
+    ("D2Q9", (8, 8), 0.0, "SF"),
+    ("D3Q19", (6, 6, 5), 0.0, "SF"),
 ])
 def test_brute_force_agreement(name, shape, kappa, wall):
     rng = np.random.default_rng(5)
@@ -38,7 +41,7 @@ def test_brute_force_agreement(name, shape, kappa, wall):
     geo = lbm.Geometry(mask, name)
     rho0 = rng.uniform(G07 * 2, L07 * 0.9, shape)
     u0 = rng.uniform(-0.01, 0.01, (geo.lat.d,) + shape)
-    p = _params(name, CS07, G07, L07, kappa=kappa, wall=wall, rho_w_const=0.2,
+    p = _params(name, CS07, G07, L07, kappa=kappa, wall=wall, rho_w_const=0.2, Gw=-0.03,
                 body_force=(1e-5, -2e-5, 3e-6), s_e=0.7, s_eps=1.2, s_q=1.15, s_nu=1.4, s_pi=1.05, s_m=1.3)
     f = lbm.init_state(rho0, geo, u0)
     f = f * (1 + 0.02 * rng.uniform(-1, 1, f.shape))
@@ -155,3 +158,67 @@ def test_flat_wall_angles():
         thetas.append(th)
     assert thetas[0] < thetas[1] < thetas[2]
     assert abs(thetas[1] - 90.0) < 12.0
+
+
+def _sf_adhesion(mask, lattice, rho0=0.2, Gw=-0.05):
+    """The adhesion force of Eq. 8 at every node of a uniform fluid at rest: F - F_m - F_body."""
+    geo = lbm.Geometry(mask, lattice)
+    p = _params(lattice, CS07, G07, L07, wall="SF", Gw=Gw, body_force=(1e-4, -2e-4, 3e-4))
+    f = lbm.init_state(np.full(mask.shape, rho0), geo)
+    rho, psi, Fm, F, u = lbm.macroscopic(f, geo, p)
+    body = np.asarray(p.body_force[:geo.lat.d]).reshape((-1,) + (1,) * mask.ndim)
+    return np.where(geo.fluid, F - Fm - body, 0.0), geo, p
+
+
+@pytest.mark.parametrize("lattice,shape", [("D2Q9", (12, 10)), ("D3Q19", (5, 12, 6))])
+def test_sf_adhesion_flat_wall_closed_form(lattice, shape):
+    """Eq. 8 next to a flat wall (solid rows y = 0, 1, periodic): the solid neighbours of the first
+    fluid row lie along e_y = -1 with weights summing to 1/2 in both lattices (1/3 + 2/12 in D2Q9,
+    1/6 + 4/12 in D3Q19), so F_ads,y = -G_w rho (-1/2) = G_w rho / 2 there; the last fluid row (its
+    solid neighbours wrap to y = 0) gets -G_w rho / 2; no tangential component; zero from the second
+    fluid row on."""
+    mask = np.zeros(shape, np.uint8)
+    if len(shape) == 2:
+        mask[0:2, :] = 1
+    else:
+        mask[:, 0:2, :] = 1
+    rho0, Gw = 0.2, -0.05
+    Fa, geo, p = _sf_adhesion(mask, lattice, rho0, Gw)
+    y_axis = 1
+    ny = shape[-2]
+    row = lambda y: (Fa[(slice(None),) + ((slice(None),) * (len(shape) - 2)) + (y, slice(None))])
+    first, last = row(2), row(ny - 1)
+    assert np.allclose(first[y_axis], Gw * rho0 / 2, rtol=0, atol=1e-15)
+    assert np.allclose(last[y_axis], -Gw * rho0 / 2, rtol=0, atol=1e-15)
+    for i in range(geo.lat.d):
+        if i != y_axis:
+            assert np.max(np.abs(Fa[i])) < 1e-15
+    for y in range(3, ny - 1):
+        assert np.max(np.abs(row(y))) < 1e-15
+
+
+def test_sf_adhesion_single_solid_node():
+    """One solid node at (5, 5): each fluid neighbour feels -G_w rho w_a e_a toward it, e.g. the node
+    at (6, 6) (the solid node lies along e_7 = (-1, -1), w = 1/12) gets G_w rho / 12 (1, 1), and the
+    node at (6, 5) (along e_3 = (-1, 0), w = 1/3) gets G_w rho / 3 (1, 0)."""
+    mask = np.zeros((11, 11), np.uint8)
+    mask[5, 5] = 1
+    rho0, Gw = 0.3, 0.07
+    Fa, geo, p = _sf_adhesion(mask, "D2Q9", rho0, Gw)
+    assert np.allclose(Fa[:, 6, 6], [Gw * rho0 / 12, Gw * rho0 / 12], rtol=0, atol=1e-16)
+    assert np.allclose(Fa[:, 5, 6], [Gw * rho0 / 3, 0.0], rtol=0, atol=1e-16)
+    assert np.allclose(Fa[:, 4, 4], [-Gw * rho0 / 12, -Gw * rho0 / 12], rtol=0, atol=1e-16)
+    far = np.ones((11, 11), bool)
+    far[4:7, 4:7] = False
+    assert np.max(np.abs(Fa[:, far])) < 1e-16
+
+
+def test_sf_mass_conservation():
+    """The adhesion force changes momentum, never mass: FP64 mass drift over 100 steps of the C1
+    geometry with the SF scheme stays at round-off."""
+    wl = W.c1_parity_cylinder()
+    geo = lbm.Geometry(wl.mask(), "D2Q9")
+    p = _params("D2Q9", CS07, G07, L07, wall="SF", Gw=-0.02)
+    f0 = lbm.init_state(wl.rho0(L07, G07), geo)
+    f = lbm.run(f0, geo, p, 100)
+    assert abs(f.sum() / f0.sum() - 1) < 1e-12
