@@ -60,8 +60,11 @@ typedef enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 } lbm_eos_kind;
 
 /* Wall schemes.  IVD: Eqs. 16-17 with the limiter rho_g <= rho_w <= rho_l (Sec. III.B), the
  * parameter in the unified form kappa >= 0 -> phi = 1 + kappa, kappa < 0 -> drho = -kappa.
- * VD: the constant virtual density rho_w_const of Benzi et al. (Sec. II.B). */
-typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1 } lbm_wall_kind;
+ * VD: the constant virtual density rho_w_const of Benzi et al. (Sec. II.B).
+ * SF: the solid-fluid interaction of Martys and Chen (Eq. 8): psi = 0 on solid nodes and the
+ * adhesion force F_ads = -Gw rho(x) sum_a w_a s(x + e_a) e_a added to the force of every fluid
+ * node (Gw < 0 wets, Gw > 0 repels); the consistency term of Eq. 7 keeps F_m of Eq. 5 alone. */
+typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1, LBM_WALL_SF = 2 } lbm_wall_kind;
 
 /* Solid body used for the contact-angle observable.  BALL: a circle (2D) / sphere (3D) of
  * radius body_radius about body_center, wall at body_radius + 1/2 (halfway bounce-back).
@@ -107,6 +110,7 @@ typedef struct {
     double drop_hint[3];        /* a point inside the drop: interface points are unwrapped to the
                                    periodic image nearest to it                                  */
     int32_t step_kernel;        /* lbm_step_kernel (D2Q9; D3Q19 always uses its z-march)         */
+    double Gw;                  /* SF adhesion parameter (Eq. 8)                                 */
 } lbm_config;
 
 typedef struct {

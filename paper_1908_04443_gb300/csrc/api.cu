@@ -304,7 +304,9 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         (c.lattice == LBM_D3Q19 && (!rate_ok(c.s_pi) || !rate_ok(c.s_m))))
         return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
     if (!(c.G != 0.0) || !std::isfinite(c.G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
-    if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD) return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
+    if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD && c.wall_kind != LBM_WALL_SF)
+        return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
+    if (c.wall_kind == LBM_WALL_SF && !std::isfinite(c.Gw)) return fail(nullptr, LBM_ERR_ARG, "Gw must be finite");
     if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH &&
         c.step_kernel != LBM_KERNEL_PAIR)
         return fail(nullptr, LBM_ERR_ARG, "unknown step kernel");
@@ -468,6 +470,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.wall_kind = c.wall_kind;
     p.kappa = c.kappa;
     p.rho_w_const = c.rho_w_const;
+    p.Gw = c.wall_kind == LBM_WALL_SF ? c.Gw : 0.0;
     p.kappa_w = kappa_per_wall ? h->d_kappa : nullptr;
     p.wall_id = h->d_wall_id;
     p.type = h->d_type;
@@ -914,7 +917,7 @@ bool same_physics(const lbm_config& a, const lbm_config& b) {
            a.G == b.G && a.sigma == b.sigma && a.s_rho == b.s_rho && a.s_e == b.s_e && a.s_eps == b.s_eps &&
            a.s_j == b.s_j && a.s_q == b.s_q && a.s_nu == b.s_nu && a.s_pi == b.s_pi && a.s_m == b.s_m &&
            a.rho_l == b.rho_l && a.rho_g == b.rho_g && a.rho_ref == b.rho_ref && a.body_force[0] == b.body_force[0] &&
-           a.body_force[1] == b.body_force[1] && a.body_force[2] == b.body_force[2] && a.wall_kind == b.wall_kind &&
+           a.body_force[1] == b.body_force[1] && a.body_force[2] == b.body_force[2] && a.wall_kind == b.wall_kind && a.Gw == b.Gw &&
            a.rho_w_const == b.rho_w_const;
 }
 

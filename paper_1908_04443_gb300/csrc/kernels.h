@@ -23,8 +23,9 @@ struct DevParams {
     double c_e, c_eps;           // consistency coefficients of the e and eps rows
     double rho_l, rho_g, rho_ref;
     double fx, fy, fz;           // body force
-    int wall_kind;               // 0 IVD, 1 VD
+    int wall_kind;               // 0 IVD, 1 VD, 2 SF (solid-fluid interaction, Eq. 8)
     double kappa, rho_w_const;
+    double Gw;                   // SF adhesion parameter
     const double* kappa_w;       // per wall node (device) or null
     const int* wall_id;          // per node: index into kappa_w (valid at wall nodes)
     const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL | T_BULK

@@ -252,9 +252,10 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     }
     __syncthreads();
 
-    // 2. wall nodes of the tile + 1-node halo: virtual density and its psi
+    // 2. wall nodes of the tile + 1-node halo: virtual density and its psi (the solid-fluid
+    //    interaction scheme keeps psi = 0 on solids)
     const int nwall = SOLID ? sm.nwall : 0;
-    if (SOLID && nwall > 0) {
+    if (SOLID && nwall > 0 && ph.wall_kind != 2) {
         for (int k = tid; k < nwall; k += NT) {
             const int i = sm.wall[k];
             const int px = i % PX, t = i / PX, py = t % PY, pz = t / PY;
@@ -262,7 +263,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
             const int ti = tix(px + 2, py + 2, pz + (YZH - PZH));
             C rw;
             if (ph.wall_kind == 1) {
-                rw = ph.rho_w_const;
+                rw = ph.wall_param;
             } else {
                 // Eq. 17: weighted mean of the fluid neighbours' densities
                 C num = C(0), den = C(0);
@@ -339,7 +340,27 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     }
     // Eq. 5
     const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy, Fmz = -ph.G * psi_c * sz;
-    const C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
+    // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+    C Fax = C(0), Fay = C(0), Faz = C(0);
+    if constexpr (SOLID) {
+        if (tile_solid && ph.wall_kind == 2 && !(my_type & T_BULK)) {
+            C ax = C(0), ay = C(0), az = C(0);
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                if (sm.type[my_ti + ex + ey * YX + ez * YX * YY] & T_SOLID) {
+                    if (ex) ax += C(L::wf(a) * ex);
+                    if (ey) ay += C(L::wf(a) * ey);
+                    if (D == 3 && ez) az += C(L::wf(a) * ez);
+                }
+            }
+            const C gr = -ph.wall_param * (ph.rho_ref + my_drho);
+            Fax = gr * ax;
+            Fay = gr * ay;
+            Faz = gr * az;
+        }
+    }
+    const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy, Fz = (Fmz + Faz) + ph.fz;
     const C drho = my_drho;   // sum of f in the order of the pull's density
     C jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll

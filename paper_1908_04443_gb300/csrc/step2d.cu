@@ -118,6 +118,8 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
             const C rho = ph.rho_ref + drho;
             if constexpr (SOLID) sm.rho[yl & 3][hx] = rho;
             sm.psi[yl & 7][hx] = psi_checked(rho, ph, err);
+        } else if (active) {
+            sm.psi[yl & 7][hx] = C(0);   // a solid cell: wall cells get their psi in phase B (not with SF)
         }
         int walls_now = 0;
         if constexpr (SOLID) {
@@ -132,10 +134,11 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
         if constexpr (SOLID) {
             if (walls_prev) {
                 const int yw = yl - 1;
-                if (inner && (sm.type[yw & 7][ti] & T_WALL)) {
+                // (the solid-fluid interaction scheme keeps psi = 0 on solids)
+                if (inner && ph.wall_kind != 2 && (sm.type[yw & 7][ti] & T_WALL)) {
                     C rw;
                     if (ph.wall_kind == 1) {
-                        rw = ph.rho_w_const;
+                        rw = ph.wall_param;
                     } else {
                         // Eq. 17: weighted mean of the fluid neighbours' densities
                         C num = C(0), den = C(0);
@@ -183,7 +186,6 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
             }
             // Eq. 5
             const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy;
-            const C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy;
             C drho = C(0), jx = C(0), jy = C(0);
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
@@ -192,6 +194,25 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
                 if (L::ey(a)) jy += C(L::ey(a)) * f[a];
             }
             const C rho = ph.rho_ref + drho;
+            // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+            C Fax = C(0), Fay = C(0);
+            if constexpr (SOLID) {
+                if (ph.wall_kind == 2 && !(sm.type[yc & 7][ti] & T_BULK)) {
+                    C ax = C(0), ay = C(0);
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int ex = L::ex(a), ey = L::ey(a);
+                        if (sm.type[(yc + ey) & 7][ti + ex] & T_SOLID) {
+                            if (ex) ax += C(L::wf(a) * ex);
+                            if (ey) ay += C(L::wf(a) * ey);
+                        }
+                    }
+                    const C gr = -ph.wall_param * rho;
+                    Fax = gr * ax;
+                    Fay = gr * ay;
+                }
+            }
+            const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy;
             if (!(rho > C(0))) atomicOr(err, ERR_RHO);
             // Eq. 4: rho u = sum e f + F/2
             const C inv = cdiv(C(1), rho);

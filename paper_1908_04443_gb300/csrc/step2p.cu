@@ -365,14 +365,14 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     // 2. wall cells of the tile + 1-node halo: virtual density and its psi
     if constexpr (SOLID) {
         const int nwall = sm.nwall;
-        if (nwall > 0) {
+        if (nwall > 0 && ph.wall_kind != 2) {   // the solid-fluid interaction scheme keeps psi = 0 on solids
             for (int k = tid; k < nwall; k += NT) {
                 const int i = sm.wall[k];
                 const int px = i % PX, py = i / PX;
                 const int ti = tix(px + 2, py + 2);
                 float rw;
                 if (ph.wall_kind == 1) {
-                    rw = ph.rho_w_const;
+                    rw = ph.wall_param;
                 } else {
                     // Eq. 17: weighted mean of the fluid neighbours' densities
                     float num = 0.0f, den = 0.0f;
@@ -414,7 +414,30 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     // Eq. 5
     const V2 gpsi = (-ph.G) * psi_c;
     const V2 Fmx = gpsi * sx, Fmy = gpsi * sy;
-    const V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy);
+    // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+    V2 Fax = bc(0.0f), Fay = bc(0.0f);
+    if constexpr (SOLID) {
+        if (ph.wall_kind == 2 && !((ta & tb) & T_BULK)) {
+            float axa = 0.0f, aya = 0.0f, axb = 0.0f, ayb = 0.0f;
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                const int ex = L::ex(a), ey = L::ey(a), off = ex + ey * YX;
+                const float w = float(L::wf(a));
+                if (tyb[tia + off] & T_SOLID) {
+                    if (ex) axa += w * float(ex);
+                    if (ey) aya += w * float(ey);
+                }
+                if (tyb[tib + off] & T_SOLID) {
+                    if (ex) axb += w * float(ex);
+                    if (ey) ayb += w * float(ey);
+                }
+            }
+            const V2 gr = (-ph.wall_param) * (bc(ph.rho_ref) + drho);
+            Fax = gr * mk(axa, axb);
+            Fay = gr * mk(aya, ayb);
+        }
+    }
+    const V2 Fx = (Fmx + Fax) + bc(ph.fx), Fy = (Fmy + Fay) + bc(ph.fy);
     const V2 jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const V2 jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const V2 rho = bc(ph.rho_ref) + drho;

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
         // B. wall nodes of plane zl - 1
         const int zw = zl - 1;
         const int nwb = sm.nw[ring(zw, 2)];
-        if (zw >= zb - 1 && zw <= ze && nwb > 0) {
+        // (the solid-fluid interaction scheme keeps psi = 0 on solids)
+        if (zw >= zb - 1 && zw <= ze && nwb > 0 && ph.wall_kind != 2) {
             const short* q = sm.wq[ring(zw, 2)];
             for (int k = tid; k < nwb; k += NT) {
                 const int i = q[k];
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
                 const int rc = (py + 1) * RX + px + 1, tc = (py + 2) * YX + px + 2;
                 C rw;
                 if (ph.wall_kind == 1) {
-                    rw = ph.rho_w_const;
+                    rw = ph.wall_param;
                 } else {
                     C num = C(0), den = C(0);
 #pragma unroll
@@ -229,7 +230,6 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
                     if (ez) sz += C(ez) * wd;
                 }
                 const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy, Fmz = -ph.G * psi_c * sz;
-                const C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
                 C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
@@ -239,6 +239,26 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
                     if (L::ez(a)) jz += C(L::ez(a)) * f[a];
                 }
                 const C rho = ph.rho_ref + drho;
+                // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+                C Fax = C(0), Fay = C(0), Faz = C(0);
+                if (solid && ph.wall_kind == 2 && !(t & T_BULK)) {
+                    const int tc = (ly + 3) * YX + lx + 3;
+                    C ax = C(0), ay = C(0), az = C(0);
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                        if (sm.type[ring(zc + ez, 5)][tc + ex + ey * YX] & T_SOLID) {
+                            if (ex) ax += C(L::wf(a) * ex);
+                            if (ey) ay += C(L::wf(a) * ey);
+                            if (ez) az += C(L::wf(a) * ez);
+                        }
+                    }
+                    const C gr = -ph.wall_param * rho;
+                    Fax = gr * ax;
+                    Fay = gr * ay;
+                    Faz = gr * az;
+                }
+                const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy, Fz = (Fmz + Faz) + ph.fz;
                 if (!(rho > C(0))) atomicOr(err, ERR_RHO);
                 const C inv = cdiv(C(1), rho);
                 const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv, uz = (jz + C(0.5) * Fz) * inv;

@@ -185,7 +185,9 @@ struct ZPSmem {
     int nw[4];
 };
 
-template <bool SOLID>
+// SF: the solid-fluid interaction scheme (Eq. 8) in a chunk holding solids, compiled as its own
+// body so that the adhesion force adds no registers to the other schemes' bodies
+template <bool SOLID, bool SF = false>
 __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float* __restrict__ fout, const Geo& g,
                                             const Phys<float>& ph, const Rates3P& kr, int x0, int y0, int zb,
                                             unsigned* err, ZPSmem<ZTX, ZTY>& sm) {
@@ -319,7 +321,8 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
             bool any = false;
             for (int zw = zl - 1; zw <= zl; ++zw) {
                 const int nwb = sm.nw[zw & 3];
-                if (zw < zb - 1 || zw > ze || nwb == 0) continue;
+                // (the solid-fluid interaction scheme keeps psi = 0 on solids)
+                if (zw < zb - 1 || zw > ze || nwb == 0 || ph.wall_kind == 2) continue;
                 any = true;
                 const short* q = sm.wq[zw & 3];
                 for (int k = tid; k < nwb; k += NT) {
@@ -328,7 +331,7 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
                     const int rc = (py + 1) * RX + px + 1, tc = (py + 2) * YX + px + 2;
                     float rw;
                     if (ph.wall_kind == 1) {
-                        rw = ph.rho_w_const;
+                        rw = ph.wall_param;
                     } else {
                         // Eq. 17: weighted mean of the fluid neighbours' densities
                         float num = 0.0f, den = 0.0f;
@@ -397,7 +400,7 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
                 // Eq. 5
                 const V2 gpsi = (-ph.G) * psi_c;
                 const V2 Fmx = gpsi * sx, Fmy = gpsi * sy, Fmz = gpsi * sz;
-                const V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy), Fz = Fmz + bc(ph.fz);
+                V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy), Fz = Fmz + bc(ph.fz);
                 V2 drho = f[0];
 #pragma unroll
                 for (int a = 1; a < Q; ++a) drho = drho + f[a];
@@ -405,6 +408,31 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
                 const V2 jy = ((f[3] - f[4]) + (f[7] - f[8])) + ((f[10] - f[9]) + (f[15] - f[16])) + (f[17] - f[18]);
                 const V2 jz = ((f[5] - f[6]) + (f[11] - f[12])) + ((f[14] - f[13]) + (f[15] - f[16])) + (f[18] - f[17]);
                 const V2 rho = bc(ph.rho_ref) + drho;
+                // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+                if constexpr (SOLID && SF) {
+                    {
+                        float ax0 = 0.0f, ay0 = 0.0f, az0 = 0.0f, ax1 = 0.0f, ay1 = 0.0f, az1 = 0.0f;
+#pragma unroll
+                        for (int a = 1; a < Q; ++a) {
+                            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a), off = ex + ey * YX;
+                            const float w = float(L::wf(a));
+                            if (sm.type[(zc + ez) & 7][ti + off] & T_SOLID) {
+                                if (ex) ax0 += w * float(ex);
+                                if (ey) ay0 += w * float(ey);
+                                if (ez) az0 += w * float(ez);
+                            }
+                            if (sm.type[(zc + 1 + ez) & 7][ti + off] & T_SOLID) {
+                                if (ex) ax1 += w * float(ex);
+                                if (ey) ay1 += w * float(ey);
+                                if (ez) az1 += w * float(ez);
+                            }
+                        }
+                        const V2 gr = (-ph.wall_param) * rho;
+                        Fx = (Fmx + gr * mk(ax0, ax1)) + bc(ph.fx);
+                        Fy = (Fmy + gr * mk(ay0, ay1)) + bc(ph.fy);
+                        Fz = (Fmz + gr * mk(az0, az1)) + bc(ph.fz);
+                    }
+                }
                 if ((fl0 && !(rho.v.x > 0.0f)) || (fl1 && !(rho.v.y > 0.0f))) atomicOr(err, ERR_RHO);
                 // Eq. 4: rho u = sum e f + F/2
                 const V2 inv = div2(bc(1.0f), rho);
@@ -434,8 +462,12 @@ __global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
     ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
     const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
-    if (solid) zpair_chunk<true>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
-    else zpair_chunk<false>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+    if (solid && ph.wall_kind == 2)
+        zpair_chunk<true, true>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+    else if (solid)
+        zpair_chunk<true>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+    else
+        zpair_chunk<false>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
 }
 
 }  // namespace

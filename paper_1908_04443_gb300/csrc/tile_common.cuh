@@ -13,7 +13,8 @@ template <class C>
 struct Phys {
     int eos_kind, wall_kind;
     C RT, a, b, b4, aphi, two_over_G, G;
-    C rho_l, rho_g, rho_ref, fx, fy, fz, rho_w_const;
+    C rho_l, rho_g, rho_ref, fx, fy, fz;
+    C wall_param;   // VD: the constant virtual density; SF: the adhesion parameter G_w of Eq. 8
     Rates<C> r;
 };
 
@@ -35,7 +36,7 @@ Phys<C> make_phys(const DevParams& p) {
     h.fx = C(p.fx);
     h.fy = C(p.fy);
     h.fz = C(p.fz);
-    h.rho_w_const = C(p.rho_w_const);
+    h.wall_param = C(p.wall_kind == 2 ? p.Gw : p.rho_w_const);
     h.r.s_e = C(p.s_e);
     h.r.s_eps = C(p.s_eps);
     h.r.s_q = C(p.s_q);

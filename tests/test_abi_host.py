@@ -102,3 +102,16 @@ def test_batch_rejects_mixed_physics_before_device_work():
         L.lbm_batch_init([a, b], [m, m])
     assert ei.value.status == L.LBM_ERR_ARG
     assert "differs" in str(ei.value)
+
+
+def test_sf_scheme_rejects_non_finite_gw_and_mixed_gw_batches():
+    """The solid-fluid interaction scheme needs a finite G_w, and a batch shares one G_w: both are
+    rejected with LBM_ERR_ARG before any device work."""
+    cfg = _cfg(wall="SF", Gw=float("nan"))
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_init(cfg, np.zeros((8, 8), np.uint8))
+    assert ei.value.status == L.LBM_ERR_ARG
+    m = np.zeros((8, 8), np.uint8)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_batch_init([_cfg(wall="SF", Gw=-0.1), _cfg(wall="SF", Gw=0.2)], [m, m])
+    assert ei.value.status == L.LBM_ERR_ARG

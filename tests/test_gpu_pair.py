@@ -45,6 +45,8 @@ def test_pair_one_step(shape, center, R, dc, r):
 @pytest.mark.parametrize("kw", [
     dict(kappa=-0.02),
     dict(wall="VD", rho_w_const=0.1),
+    dict(wall="SF", Gw=-0.2),
+    dict(wall="SF", Gw=0.3),
     dict(body_force=(1e-5, -3e-6, 0.0)),
     dict(eos_kind="PR", t_over_tc=0.86, sigma=0.11),
     dict(rates=dict(s_e=0.6, s_eps=1.5, s_q=1.2, s_nu=1.7)),

@@ -44,6 +44,8 @@ def test_one_step_fp64(shape, center, R, dc, r, kernel):
 @pytest.mark.parametrize("kw", [
     dict(kappa=-0.02),                                        # hydrophobic branch
     dict(wall="VD", rho_w_const=0.1),                         # constant virtual density
+    dict(wall="SF", Gw=-0.2),                                 # solid-fluid interaction (Eq. 8), wetting
+    dict(wall="SF", Gw=0.3),                                  # the same, repelling
     dict(body_force=(1e-5, -3e-6, 0.0)),
     dict(eos_kind="PR", t_over_tc=0.86, sigma=0.11),          # the paper's equation of state
     dict(rates=dict(s_e=0.6, s_eps=1.5, s_q=1.2, s_nu=1.7)),

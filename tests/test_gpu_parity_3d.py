@@ -27,7 +27,7 @@ def _one_step(case, precision="fp64", before=2):
 
 
 @pytest.mark.parametrize("kw", [dict(kappa=0.2), dict(kappa=-0.03), dict(wall="VD", rho_w_const=0.1),
-                                dict(body_force=(2e-6, -1e-6, 3e-6))])
+                                dict(wall="SF", Gw=-0.2), dict(body_force=(2e-6, -1e-6, 3e-6))])
 def test_one_step_d3q19_fp64(kw):
     s1, ref = _one_step(sphere_case(**kw))
     assert np.max(np.abs(s1 - ref)) < 1e-13
@@ -77,6 +77,8 @@ def test_sphere_60_steps_fp64_and_fp32():
     ((70, 16, 40), (20.0, 8.0, 30.0), 5.0, (20.0, 8.0, 40.0), 6.0, dict(kappa=0.1)),      # 3 chunks, last of 6
     ((5, 6, 7), (3.0, 3.0, 2.0), 1.0, (3.0, 3.0, 3.5), 1.5, dict(kappa=0.2)),              # smaller than a column
     ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(wall="VD", rho_w_const=0.1)),
+    ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(wall="SF", Gw=-0.2)),
+    ((21, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(wall="SF", Gw=0.3)),    # odd plane count
     ((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, dict(body_force=(2e-6, -1e-6, 3e-6))),
 ])
 def test_one_step_d3q19_fp32(shape, c, R, dc, r, kw):

@@ -42,7 +42,7 @@ def test_ymarch_one_step_fp64(shape, center, R, dc, r):
     assert np.max(np.abs(f1 - ref)) < 1e-13
 
 
-@pytest.mark.parametrize("kw", [dict(kappa=-0.03), dict(wall="VD", rho_w_const=0.15),
+@pytest.mark.parametrize("kw", [dict(kappa=-0.03), dict(wall="VD", rho_w_const=0.15), dict(wall="SF", Gw=-0.2),
                                 dict(eos_kind="PR", t_over_tc=0.86, sigma=0.11)])
 def test_ymarch_one_step_variants(kw):
     case = drop_on_cylinder((140, 250), (125.0, 50.0), 20.0, (125.0, 85.0), 16.0, step_kernel="ymarch", **kw)
