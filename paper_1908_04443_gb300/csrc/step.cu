@@ -340,8 +340,8 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
     }
     // Eq. 5
     const C Fmx = -ph.G * psi_c * sx, Fmy = -ph.G * psi_c * sy, Fmz = -ph.G * psi_c * sz;
+    C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
     // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
-    C Fax = C(0), Fay = C(0), Faz = C(0);
     if constexpr (SOLID) {
         if (tile_solid && ph.wall_kind == 2 && !(my_type & T_BULK)) {
             C ax = C(0), ay = C(0), az = C(0);
@@ -355,12 +355,11 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                 }
             }
             const C gr = -ph.wall_param * (ph.rho_ref + my_drho);
-            Fax = gr * ax;
-            Fay = gr * ay;
-            Faz = gr * az;
+            Fx = (Fmx + gr * ax) + ph.fx;
+            Fy = (Fmy + gr * ay) + ph.fy;
+            Fz = (Fmz + gr * az) + ph.fz;
         }
     }
-    const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy, Fz = (Fmz + Faz) + ph.fz;
     const C drho = my_drho;   // sum of f in the order of the pull's density
     C jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll

@@ -194,8 +194,8 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
                 if (L::ey(a)) jy += C(L::ey(a)) * f[a];
             }
             const C rho = ph.rho_ref + drho;
+            C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy;
             // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
-            C Fax = C(0), Fay = C(0);
             if constexpr (SOLID) {
                 if (ph.wall_kind == 2 && !(sm.type[yc & 7][ti] & T_BULK)) {
                     C ax = C(0), ay = C(0);
@@ -208,11 +208,10 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
                         }
                     }
                     const C gr = -ph.wall_param * rho;
-                    Fax = gr * ax;
-                    Fay = gr * ay;
+                    Fx = (Fmx + gr * ax) + ph.fx;
+                    Fy = (Fmy + gr * ay) + ph.fy;
                 }
             }
-            const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy;
             if (!(rho > C(0))) atomicOr(err, ERR_RHO);
             // Eq. 4: rho u = sum e f + F/2
             const C inv = cdiv(C(1), rho);

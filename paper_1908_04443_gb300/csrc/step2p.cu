@@ -414,8 +414,8 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
     // Eq. 5
     const V2 gpsi = (-ph.G) * psi_c;
     const V2 Fmx = gpsi * sx, Fmy = gpsi * sy;
+    V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy);
     // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
-    V2 Fax = bc(0.0f), Fay = bc(0.0f);
     if constexpr (SOLID) {
         if (ph.wall_kind == 2 && !((ta & tb) & T_BULK)) {
             float axa = 0.0f, aya = 0.0f, axb = 0.0f, ayb = 0.0f;
@@ -433,11 +433,10 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
                 }
             }
             const V2 gr = (-ph.wall_param) * (bc(ph.rho_ref) + drho);
-            Fax = gr * mk(axa, axb);
-            Fay = gr * mk(aya, ayb);
+            Fx = (Fmx + gr * mk(axa, axb)) + bc(ph.fx);
+            Fy = (Fmy + gr * mk(aya, ayb)) + bc(ph.fy);
         }
     }
-    const V2 Fx = (Fmx + Fax) + bc(ph.fx), Fy = (Fmy + Fay) + bc(ph.fy);
     const V2 jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const V2 jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const V2 rho = bc(ph.rho_ref) + drho;

@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
                     if (L::ez(a)) jz += C(L::ez(a)) * f[a];
                 }
                 const C rho = ph.rho_ref + drho;
+                C Fx = Fmx + ph.fx, Fy = Fmy + ph.fy, Fz = Fmz + ph.fz;
                 // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
-                C Fax = C(0), Fay = C(0), Faz = C(0);
                 if (solid && ph.wall_kind == 2 && !(t & T_BULK)) {
                     const int tc = (ly + 3) * YX + lx + 3;
                     C ax = C(0), ay = C(0), az = C(0);
@@ -254,11 +254,10 @@ __global__ void __launch_bounds__(ZShape<S>::X* ZShape<S>::Y, ZShape<S>::MINB)
                         }
                     }
                     const C gr = -ph.wall_param * rho;
-                    Fax = gr * ax;
-                    Fay = gr * ay;
-                    Faz = gr * az;
+                    Fx = (Fmx + gr * ax) + ph.fx;
+                    Fy = (Fmy + gr * ay) + ph.fy;
+                    Fz = (Fmz + gr * az) + ph.fz;
                 }
-                const C Fx = (Fmx + Fax) + ph.fx, Fy = (Fmy + Fay) + ph.fy, Fz = (Fmz + Faz) + ph.fz;
                 if (!(rho > C(0))) atomicOr(err, ERR_RHO);
                 const C inv = cdiv(C(1), rho);
                 const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv, uz = (jz + C(0.5) * Fz) * inv;
