@@ -161,6 +161,15 @@ lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n);
 /* Synchronise the handle's stream and report the sticky device error flag (LBM_ERR_UNSTABLE). */
 lbm_status lbm_check(lbm_handle* h);
 
+/* Self-test of the device's bounded waits (no counterpart in the paper).  Every wait of the step
+ * kernels on a shared-memory copy (an mbarrier) gives up after a fixed number of polls, flags
+ * ERR_TIMEOUT and lets the kernel return, so a copy that never lands becomes an error status
+ * (LBM_ERR_CUDA from the stepping call) instead of a hung GPU.  This call launches, on `stream`
+ * (NULL: the legacy default stream), one CTA whose threads wait with `polls` polls (> 0) on an
+ * mbarrier that nothing completes and no copy targets, and sets *timed_out to 1 if the waits gave
+ * up and flagged the timeout (the expected outcome), 0 otherwise.  Synchronises the stream. */
+lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* timed_out);
+
 /* Observables of the current state: mass, fluid density extremes, maximum |u| (u from Eq. 4 with
  * the current force), and the contact angle (interface at (rho_l + rho_g)/2 fitted by a Kasa
  * circle/sphere, points within 3 nodes of a solid dropped).  Optionally copies the density

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbmwet.h"
 #include "adjoint.h"
 #include "eos_host.h"
@@ -17,6 +19,14 @@
 #include "plan.h"
 
 using namespace lbmwet;
+
+// NVTX range over one entry point (visible to profilers; no cost without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 namespace {
 
@@ -291,6 +301,7 @@ lbm_status lbm_coexistence(const lbm_eos* eos, double* rho_g, double* rho_l) {
 
 lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0, const double* u0,
                     const double* kappa_per_wall, void* stream, lbm_handle** out) {
+    NvtxRange nvtx_range("lbm_init");
     if (!cfg || !solid_mask || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
     *out = nullptr;
     const lbm_config& c = *cfg;
@@ -545,6 +556,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
 }
 
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
+    NvtxRange nvtx_range("lbm_step");
     if (!h) return LBM_ERR_ARG;
     if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_step");
     lbm_status st = enqueue_steps(h, n);
@@ -554,6 +566,7 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
 }
 
 lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n) {
+    NvtxRange nvtx_range("lbm_enqueue_steps");
     if (!h) return LBM_ERR_ARG;
     if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_enqueue_steps");
     return enqueue_steps(h, n);
@@ -562,6 +575,23 @@ lbm_status lbm_enqueue_steps(lbm_handle* h, int64_t n) {
 lbm_status lbm_check(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
     return check_device_error(h);
+}
+
+lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* timed_out) {
+    if (!timed_out || polls == 0) return fail(nullptr, LBM_ERR_ARG, "null argument or zero polls");
+    *timed_out = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned* d_flag = nullptr;
+    unsigned flag = 0;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_flag), sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_wait_timeout_probe(d_flag, polls, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (d_flag) cudaFreeAsync(d_flag, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait self-test");
+    *timed_out = (flag & ERR_TIMEOUT) ? 1 : 0;
+    return LBM_OK;
 }
 
 lbm_status lbm_fields_device(lbm_handle* h, double* rho_dev, double* u_dev) {
@@ -573,6 +603,7 @@ lbm_status lbm_fields_device(lbm_handle* h, double* rho_dev, double* u_dev) {
 }
 
 lbm_status lbm_observables(lbm_handle* h, lbm_obs* out, double* rho_host, double* u_host) {
+    NvtxRange nvtx_range("lbm_observables");
     if (!h || !out) return LBM_ERR_ARG;
     lbm_status st = ensure_obs_buffers(h);
     if (st != LBM_OK) return st;
@@ -1005,6 +1036,7 @@ extern "C" {
 
 lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* const* masks, const double* const* rho0s,
                           const double* const* kappas_per_wall, void* stream, lbm_batch** out) {
+    NvtxRange nvtx_range("lbm_batch_init");
     if (n < 1 || !cfgs || !masks || !out) return bfail(nullptr, LBM_ERR_ARG, "null argument or empty batch");
     *out = nullptr;
     for (int i = 1; i < n; ++i)
@@ -1161,11 +1193,13 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
 }
 
 lbm_status lbm_batch_enqueue_steps(lbm_batch* b, int64_t n) {
+    NvtxRange nvtx_range("lbm_batch_enqueue_steps");
     if (!b) return LBM_ERR_ARG;
     return batch_enqueue(b, n);
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+    NvtxRange nvtx_range("lbm_batch_step");
     if (!b) return LBM_ERR_ARG;
     lbm_status st = batch_enqueue(b, n);
     if (st != LBM_OK) return st;
@@ -1218,6 +1252,7 @@ void lbm_batch_destroy(lbm_batch* b) {
 // ---------------------------------------------------------------------------------------------
 
 extern "C" lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_every) {
+    NvtxRange nvtx_range("lbm_record");
     if (!h) return LBM_ERR_ARG;
     if (h->batch_member) return fail(h, LBM_ERR_STATE, "a batch member is stepped by lbm_batch_step");
     if (h->D != 2) return fail(h, LBM_ERR_ARG, "the adjoint is implemented for D2Q9");
@@ -1255,6 +1290,7 @@ extern "C" lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_ev
 }
 
 extern "C" lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, double* dkappa_host) {
+    NvtxRange nvtx_range("lbm_adjoint");
     if (!h || !drho_final_dev || !dkappa_host) return fail(h, LBM_ERR_ARG, "null argument");
     if (h->rec_steps < 1 || h->step != h->rec_end_step || h->cur != h->rec_end_cur)
         return fail(h, LBM_ERR_STATE, "lbm_adjoint needs an lbm_record whose final state is the current one");

@@ -99,6 +99,9 @@ cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cu
 cudaError_t launch_pair_batched(int parity, const DevParams& phys, const BatchItem* items, int n_items, int ctas,
                                 unsigned* sched, cudaStream_t s);
 void pair_tile_shape(int* tx, int* ty);
+// Launches a kernel whose mbarrier wait cannot complete (bounded by `limit` polls); sets ERR_TIMEOUT
+// in *err.
+cudaError_t launch_wait_timeout_probe(unsigned* err, unsigned limit, cudaStream_t s);
 // Box (x extent, y extent; all 9 directions) of the pair kernel's TMA load: a tile and the cells its
 // pulls read, with x starting 4 cells before the tile (a 16-byte boundary).
 void pair_box_dims(int* bx, int* by);

@@ -487,9 +487,11 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     else pair_tile<false>(g, 0, ph, kr, blockIdx.x * PTX, blockIdx.y * PNY, err, sm, hst);
 }
 
-// Polls of an mbarrier before a wait gives up (flags ERR_TIMEOUT and goes on); far above any copy's
+// Polls of an mbarrier before a wait gives up (flags ERR_TIMEOUT and goes on).  A poll
+// (mbarrier.try_wait) suspends for about 3.8 us when the phase is incomplete (measured on GB300 by
+// lbm_selftest_bounded_wait), so 2^18 polls bound a wait at about one second, far above any copy's
 // latency.
-constexpr unsigned MBAR_POLL_LIMIT = 1u << 24;
+constexpr unsigned MBAR_POLL_LIMIT = 1u << 18;
 
 // Persistent form with dynamic tile scheduling.  CTA b starts with items b and b + gridDim.x; every
 // further item is claimed from a global counter (sched[0]), so that a CTA slowed by costly tiles
@@ -620,7 +622,25 @@ __global__ void __launch_bounds__(PTX* PTY, LBMWET_PAIR_MINB)
     }
 }
 
+// Self-test of the bounded waits: an mbarrier that no thread arrives on and no copy completes, waited
+// on by every thread with `limit` polls.  Each wait must give up and flag ERR_TIMEOUT; nothing is in
+// flight when the kernel returns.
+__global__ void __launch_bounds__(128) wait_timeout_probe(unsigned* err, unsigned limit) {
+    __shared__ alignas(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0u, limit)) atomicOr(err, ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout_probe(unsigned* err, unsigned limit, cudaStream_t s) {
+    wait_timeout_probe<<<1, 128, 0, s>>>(err, limit);
+    return cudaGetLastError();
+}
 
 void pair_tile_shape(int* tx, int* ty) {
     *tx = PTX;

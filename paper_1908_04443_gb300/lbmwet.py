@@ -69,6 +69,7 @@ def _load():
         "lbm_step": (C.c_int, [H, C.c_int64]),
         "lbm_enqueue_steps": (C.c_int, [H, C.c_int64]),
         "lbm_check": (C.c_int, [H]),
+        "lbm_selftest_bounded_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
         "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
         "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
         "lbm_observables_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.POINTER(lbm_obs)]),
@@ -107,6 +108,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
+            "lbm_selftest_bounded_wait",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
             "lbm_step_kernel_used", "lbm_batch_step_kernel_used",
@@ -180,6 +182,14 @@ def lbm_enqueue_steps(h, n: int):
 
 def lbm_check(h):
     _check(_lib.lbm_check(h), h)
+
+
+def lbm_selftest_bounded_wait(polls: int = 1024, stream=None) -> bool:
+    """Run the device's bounded-wait self-test: True if a wait that cannot complete gave up after
+    `polls` polls and flagged the timeout (the expected outcome)."""
+    t = C.c_int32(0)
+    _check(_lib.lbm_selftest_bounded_wait(_stream_ptr(stream), int(polls), C.byref(t)))
+    return bool(t.value)
 
 
 def lbm_observables(h, rho_host: Optional[np.ndarray] = None, u_host: Optional[np.ndarray] = None) -> lbm_obs:

@@ -115,3 +115,9 @@ def test_sf_scheme_rejects_non_finite_gw_and_mixed_gw_batches():
     with pytest.raises(L.LbmError) as ei:
         L.lbm_batch_init([_cfg(wall="SF", Gw=-0.1), _cfg(wall="SF", Gw=0.2)], [m, m])
     assert ei.value.status == L.LBM_ERR_ARG
+
+
+def test_bounded_wait_selftest_rejects_zero_polls_before_device_work():
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_selftest_bounded_wait(0)
+    assert ei.value.status == L.LBM_ERR_ARG
