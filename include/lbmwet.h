@@ -170,6 +170,16 @@ lbm_status lbm_check(lbm_handle* h);
  * up and flagged the timeout (the expected outcome), 0 otherwise.  Synchronises the stream. */
 lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* timed_out);
 
+/* Memory-safety check, for tests (the paper has no counterpart).  Both distribution buffers and
+ * the density / velocity fields of lbm_observables sit between two 4096-byte guard zones filled
+ * with the byte 0xA5 when they are allocated; D2Q9 distribution rows also carry padding nodes
+ * x in [nx, pitch), pitch = nx rounded up to 32, that lbm_init zeroes and no kernel writes.  Sets
+ * *guard_bad to the number of guard bytes that no longer hold 0xA5 and *pad_bad to the number of
+ * padding bytes of the distributions that are no longer 0: both 0 unless a kernel wrote outside
+ * its buffers.  Copies the whole distribution buffers to the host (sized for test grids) and
+ * synchronises the handle's stream.  Works on a batch instance (lbm_batch_handle). */
+lbm_status lbm_check_guards(lbm_handle* h, int64_t* guard_bad, int64_t* pad_bad);
+
 /* Observables of the current state: mass, fluid density extremes, maximum |u| (u from Eq. 4 with
  * the current force), and the contact angle (interface at (rho_l + rho_g)/2 fitted by a Kasa
  * circle/sphere, points within 3 nodes of a solid dropped).  Optionally copies the density

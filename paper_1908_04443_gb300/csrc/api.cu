@@ -163,10 +163,35 @@ bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
 
 EosHost to_host(const lbm_eos& e) { return EosHost{e.kind, e.a, e.b, e.R, e.T, e.omega}; }
 
+// Guard zones: the distribution buffers and the observable fields sit between two GUARD-byte
+// zones filled with GUARD_BYTE, so that a kernel writing past either end of one of them leaves a
+// trace that lbm_check_guards finds (a check that needs no memory checker).  GUARD keeps the
+// inner pointer at the allocation's alignment (256 B) for TMA maps and vector loads.
+constexpr size_t GUARD = 4096;
+constexpr unsigned char GUARD_BYTE = 0xA5;
+
+cudaError_t guarded_malloc(void** p, size_t bytes, cudaStream_t s) {
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * GUARD);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(base, GUARD_BYTE, GUARD, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + GUARD + bytes, GUARD_BYTE, GUARD, s);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        return e;
+    }
+    *p = base + GUARD;
+    return cudaSuccess;
+}
+
+void guarded_free(void* p) {
+    if (p) cudaFree(static_cast<char*>(p) - GUARD);
+}
+
 void free_all(lbm_handle* h) {
     for (int i = 0; i < 2; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
-        if (h->f[i]) cudaFree(h->f[i]);
+        guarded_free(h->f[i]);
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_type);
@@ -177,8 +202,8 @@ void free_all(lbm_handle* h) {
     cudaFree(h->d_wall_id);
     cudaFree(h->d_kappa);
     cudaFree(h->d_err);
-    cudaFree(h->d_rho);
-    cudaFree(h->d_u);
+    guarded_free(h->d_rho);
+    guarded_free(h->d_u);
     cudaFree(h->d_partials);
     cudaFree(h->d_red);
     for (void* c : h->ckpt) cudaFree(c);
@@ -200,8 +225,8 @@ lbm_status check_device_error(lbm_handle* h) {
 }
 
 lbm_status ensure_obs_buffers(lbm_handle* h) {
-    if (!h->d_rho) CK(h, cudaMalloc(&h->d_rho, sizeof(double) * h->N));
-    if (!h->d_u) CK(h, cudaMalloc(&h->d_u, sizeof(double) * h->N * h->D));
+    if (!h->d_rho) CK(h, guarded_malloc(reinterpret_cast<void**>(&h->d_rho), sizeof(double) * h->N, h->stream));
+    if (!h->d_u) CK(h, guarded_malloc(reinterpret_cast<void**>(&h->d_u), sizeof(double) * h->N * h->D, h->stream));
     if (!h->d_partials) CK(h, cudaMalloc(&h->d_partials, sizeof(double) * reduce_partials_size(h->N)));
     if (!h->d_red) CK(h, cudaMalloc(&h->d_red, sizeof(double) * NRED));
     return LBM_OK;
@@ -413,8 +438,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     cudaError_t e;
 #define CKI(call, what) \
     if ((e = (call)) != cudaSuccess) return oom(e, what)
-    CKI(cudaMalloc(&h->f[0], h->fbytes), "cudaMalloc f");
-    CKI(cudaMalloc(&h->f[1], h->fbytes), "cudaMalloc f");
+    CKI(guarded_malloc(&h->f[0], h->fbytes, h->stream), "cudaMalloc f");
+    CKI(guarded_malloc(&h->f[1], h->fbytes, h->stream), "cudaMalloc f");
     CKI(cudaMalloc(&h->d_type, N), "cudaMalloc type");
     CKI(cudaMalloc(&h->d_tile_solid, h->tile_solid.size()), "cudaMalloc tile flags");
     CKI(cudaMemcpyAsync(h->d_tile_solid, h->tile_solid.data(), h->tile_solid.size(), cudaMemcpyHostToDevice, h->stream),
@@ -591,6 +616,43 @@ lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* time
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait self-test");
     *timed_out = (flag & ERR_TIMEOUT) ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_check_guards(lbm_handle* h, int64_t* guard_bad, int64_t* pad_bad) {
+    if (!h || !guard_bad || !pad_bad) return LBM_ERR_ARG;
+    *guard_bad = 0;
+    *pad_bad = 0;
+    struct Buf {
+        const void* p;
+        size_t bytes;
+    };
+    const Buf bufs[4] = {{h->f[0], h->fbytes},
+                         {h->f[1], h->fbytes},
+                         {h->d_rho, sizeof(double) * (size_t)h->N},
+                         {h->d_u, sizeof(double) * (size_t)h->N * h->D}};
+    std::vector<unsigned char> zone(2 * GUARD);
+    for (const Buf& b : bufs) {
+        if (!b.p) continue;
+        const char* base = static_cast<const char*>(b.p) - GUARD;
+        CK(h, cudaMemcpyAsync(zone.data(), base, GUARD, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(zone.data() + GUARD, base + GUARD + b.bytes, GUARD, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (unsigned char v : zone) *guard_bad += v != GUARD_BYTE;
+    }
+    // padding nodes x in [nx, fp) of every row of both distribution buffers
+    const int nx = h->dp.nx, fp = h->dp.fp;
+    if (fp > nx) {
+        const size_t es = h->prec == LBM_FP64 ? sizeof(double) : sizeof(float);
+        const size_t rows = h->fbytes / (es * (size_t)fp);
+        std::vector<unsigned char> all(h->fbytes);
+        for (int i = 0; i < 2; ++i) {
+            CK(h, cudaMemcpyAsync(all.data(), h->f[i], h->fbytes, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (size_t r = 0; r < rows; ++r)
+                for (size_t k = (size_t)nx * es; k < (size_t)fp * es; ++k) *pad_bad += all[r * fp * es + k] != 0;
+        }
+    }
     return LBM_OK;
 }
 

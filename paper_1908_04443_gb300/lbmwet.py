@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -70,6 +70,7 @@ def _load():
         "lbm_enqueue_steps": (C.c_int, [H, C.c_int64]),
         "lbm_check": (C.c_int, [H]),
         "lbm_selftest_bounded_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
+        "lbm_check_guards": (C.c_int, [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
         "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
         "lbm_observables_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.POINTER(lbm_obs)]),
@@ -108,7 +109,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
-            "lbm_selftest_bounded_wait",
+            "lbm_selftest_bounded_wait", "lbm_check_guards",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
             "lbm_step_kernel_used", "lbm_batch_step_kernel_used",
@@ -190,6 +191,14 @@ def lbm_selftest_bounded_wait(polls: int = 1024, stream=None) -> bool:
     t = C.c_int32(0)
     _check(_lib.lbm_selftest_bounded_wait(_stream_ptr(stream), int(polls), C.byref(t)))
     return bool(t.value)
+
+
+def lbm_check_guards(h) -> Tuple[int, int]:
+    """(guard bytes overwritten, padding bytes of the distributions no longer zero) of a handle:
+    both 0 unless a kernel wrote outside its buffers."""
+    g, p = C.c_int64(0), C.c_int64(0)
+    _check(_lib.lbm_check_guards(h, C.byref(g), C.byref(p)), h)
+    return int(g.value), int(p.value)
 
 
 def lbm_observables(h, rho_host: Optional[np.ndarray] = None, u_host: Optional[np.ndarray] = None) -> lbm_obs:
@@ -420,6 +429,9 @@ class Simulation:
 
     def check(self):
         lbm_check(self.h)
+
+    def check_guards(self) -> Tuple[int, int]:
+        return lbm_check_guards(self.h)
 
     def observables(self, fields: bool = False):
         if not fields:
