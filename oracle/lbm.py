@@ -12,6 +12,8 @@ A step, in the paper's order:
           rho_ave = sum_a w_a rho(x+e_a) s_w(x+e_a) / sum_a w_a s_w(x+e_a),   (Eqs. 16-17)
           limited to rho_g <= rho_w <= rho_l                             (Sec. III.B)
      VD   rho_w = constant (Sec. II.B)
+     GF   (2D) rho_w = max or min of the densities where the two characteristic lines of the
+          prescribed angle theta_a cross the mesh (Eqs. 10-15; `oracle.geometric`)
   3. psi from Eq. 6 at fluid nodes (rho) and at wall nodes (rho_w)
   4. F_m = -G psi(x) sum_a w_a psi(x + e_a) e_a at fluid nodes (Eq. 5);  F = F_m + F_body
      (SF scheme: F_ads = -G_w rho(x) sum_a w_a s(x + e_a) e_a is added, Eq. 8, with psi = 0 on solids)
@@ -31,6 +33,7 @@ from typing import Optional
 
 import numpy as np
 
+from . import geometric
 from .eos import EOS, CS2
 from .lattice import Lattice, lattice as get_lattice
 
@@ -53,10 +56,11 @@ class Params:
     rho_l: float = 1.0        # limiter bounds of Sec. III.B
     rho_g: float = 0.1
     body_force: tuple = (0.0, 0.0, 0.0)
-    wall: str = "IVD"          # "IVD", "VD" or "SF"
+    wall: str = "IVD"          # "IVD", "VD", "SF" or "GF"
     kappa: object = 0.0        # IVD: scalar or array (one per wall node, in wall-node order)
     rho_w_const: float = 1.0   # VD
     Gw: float = 0.0            # SF
+    theta_a: float = 90.0      # GF: prescribed contact angle (degrees)
 
     @property
     def lat(self) -> Lattice:
@@ -134,6 +138,11 @@ def wall_density(rho, geo: Geometry, p: Params):
         num += lat.WF[a] * neighbour(rho_f, lat.E[a]) * neighbour(sw, lat.E[a])
         den += lat.WF[a] * neighbour(sw, lat.E[a])
     rho_ave = num[geo.wall] / den[geo.wall]
+    if p.wall == "GF":
+        if lat.d != 2:
+            raise ValueError("the geometric-formulation scheme is two-dimensional (Sec. III.A)")
+        rw[geo.wall] = geometric.wall_density(rho_f, geo, p.theta_a, rho_ave)
+        return rw
     kappa = p.kappa
     if np.ndim(kappa) > 0:
         kappa = np.asarray(kappa, dtype=np.float64)
