@@ -24,7 +24,8 @@ Readings (the paper defers the intersection cases to a reference that is not ava
     is the other node's density; when both are solid, D is dropped from Eq. 11.  With both D
     dropped, rho_P is the mean of Eq. 17 over the fluid neighbours (phi = 1).
   * A wall node whose sum in Eq. 13 vanishes has no normal; the scheme is then undefined there and
-    `characteristics` raises.
+    `characteristics` raises.  Every Eq. 14 weight is a multiple of 1/5040, so a nonzero component
+    of the sum is at least 1/5040: a sum below 1e-9 (rounding of cancelling terms) counts as zero.
   * The densities are those of the same step (after streaming, before collision), as for Eq. 17.
 """
 from __future__ import annotations
@@ -37,6 +38,7 @@ import numpy as np
 EQ14_WEIGHTS = {1: 4.0 / 21.0, 2: 4.0 / 45.0, 4: 1.0 / 60.0, 5: 2.0 / 315.0, 8: 1.0 / 5040.0}
 
 SNAP = 1e-12
+NO_NORMAL = 1e-9
 
 
 def eq14_stencil():
@@ -61,7 +63,7 @@ def solid_normal(solid: np.ndarray, x: int, y: int):
         gx += w * s * ex
         gy += w * s * ey
     norm = math.hypot(gx, gy)
-    if norm == 0.0:
+    if norm < NO_NORMAL:
         return None
     return -gx / norm, -gy / norm
 

@@ -154,6 +154,20 @@ def test_gf_mirror_symmetry_and_mass():
     assert o.u_max > 1e-5
 
 
+def test_no_normal_for_a_one_node_thick_plate():
+    """Next to a solid line one node thick the Eq. 13 sum cancels (up to rounding): no normal, and
+    the scheme refuses the geometry; a two-node plate has the outward normals."""
+    solid = np.zeros((8, 10), bool)
+    solid[4, :] = True
+    assert GF.solid_normal(solid, 3, 4) is None
+    geo = lbm.Geometry(solid.astype(np.uint8), "D2Q9")
+    with pytest.raises(ValueError):
+        GF.characteristics(geo, 60.0)
+    solid[5, :] = True
+    assert GF.solid_normal(solid, 3, 4) == pytest.approx((0.0, -1.0), abs=1e-15)
+    assert GF.solid_normal(solid, 3, 5) == pytest.approx((0.0, 1.0), abs=1e-15)
+
+
 def test_gf_rejects_three_dimensions():
     mask = np.zeros((5, 6, 7), np.uint8)
     mask[:, :2, :] = 1
