@@ -63,8 +63,16 @@ typedef enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 } lbm_eos_kind;
  * VD: the constant virtual density rho_w_const of Benzi et al. (Sec. II.B).
  * SF: the solid-fluid interaction of Martys and Chen (Eq. 8): psi = 0 on solid nodes and the
  * adhesion force F_ads = -Gw rho(x) sum_a w_a s(x + e_a) e_a added to the force of every fluid
- * node (Gw < 0 wets, Gw > 0 repels); the consistency term of Eq. 7 keeps F_m of Eq. 5 alone. */
-typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1, LBM_WALL_SF = 2 } lbm_wall_kind;
+ * node (Gw < 0 wets, Gw > 0 repels); the consistency term of Eq. 7 keeps F_m of Eq. 5 alone.
+ * GF (D2Q9 only): the curved geometric formulation (Sec. III.A, Eqs. 10-15) for a prescribed
+ * angle theta_a: at each wall node P, the surface normal of Eq. 13 (eighth-order weights of
+ * Eq. 14) rotated by +-(90 - theta_a) degrees (Eq. 15) gives two characteristic lines; each is
+ * followed to the first mesh line it crosses (x or y one node from P), where the density is
+ * interpolated linearly between the two fluid nodes of that mesh segment (a solid end is dropped;
+ * a crossing with no fluid end is unused); rho_w = max of the two (theta_a <= 90) or min (Eq. 11),
+ * or the mean of Eq. 17 when neither crossing is usable.  A wall node whose Eq. 13 sum vanishes
+ * (a one-node-thin solid, for example) has no normal: lbm_init rejects such a mask. */
+typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1, LBM_WALL_SF = 2, LBM_WALL_GF = 3 } lbm_wall_kind;
 
 /* Solid body used for the contact-angle observable.  BALL: a circle (2D) / sphere (3D) of
  * radius body_radius about body_center, wall at body_radius + 1/2 (halfway bounce-back).
@@ -111,6 +119,7 @@ typedef struct {
                                    periodic image nearest to it                                  */
     int32_t step_kernel;        /* lbm_step_kernel (D2Q9; D3Q19 always uses its z-march)         */
     double Gw;                  /* SF adhesion parameter (Eq. 8)                                 */
+    double theta_a;             /* GF prescribed contact angle, degrees in (0, 180)              */
 } lbm_config;
 
 typedef struct {
@@ -143,10 +152,11 @@ lbm_status lbm_critical_temperature(const lbm_eos* eos, double* tc);
  *   rho0           host, N doubles or NULL (uniform rho_g); values at solid nodes are ignored.
  *   u0             host, d*N doubles (component-major: u_x for all nodes, then u_y[, u_z]) or NULL.
  *   kappa_per_wall host, one IVD parameter per wall node in lbm_wall_nodes() order, or NULL to use
- *                  cfg->kappa everywhere.
+ *                  cfg->kappa everywhere (IVD only: LBM_ERR_ARG with the GF scheme).
  *   stream         cudaStream_t for all device work of this handle, or NULL.
  * The initial state is f = f^eq(rho0, u0) at fluid nodes (post-streaming, step 0).
- * Errors: LBM_ERR_ARG (bad sizes, rates, EOS, an all-solid grid), LBM_ERR_OOM, LBM_ERR_CUDA. */
+ * Errors: LBM_ERR_ARG (bad sizes, rates, EOS, an all-solid grid; GF with D3Q19, theta_a outside
+ * (0, 180) or a wall node without a normal), LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0,
                     const double* u0, const double* kappa_per_wall, void* stream, lbm_handle** out);
 
@@ -229,7 +239,8 @@ lbm_status lbm_set_state(lbm_handle* h, const double* f_host, int64_t step);
 lbm_status lbm_save_state(lbm_handle* h, void* host_buf, size_t* bytes);
 lbm_status lbm_load_state(lbm_handle* h, const void* host_buf, size_t bytes);
 
-/* Set the per-wall-node IVD parameter (one per wall node, lbm_wall_nodes() order). */
+/* Set the per-wall-node IVD parameter (one per wall node, lbm_wall_nodes() order).  LBM_ERR_ARG
+ * for a handle of another wall scheme. */
 lbm_status lbm_set_kappa(lbm_handle* h, const double* kappa_per_wall);
 
 /* Resolved coexistence densities used by the limiter (after a Maxwell construction if asked). */

@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "lattice.cuh"
 #include "plan.h"
+#include "wall_gf.h"
 
 using namespace lbmwet;
 
@@ -340,9 +341,17 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         (c.lattice == LBM_D3Q19 && (!rate_ok(c.s_pi) || !rate_ok(c.s_m))))
         return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
     if (!(c.G != 0.0) || !std::isfinite(c.G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
-    if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD && c.wall_kind != LBM_WALL_SF)
+    if (c.wall_kind != LBM_WALL_IVD && c.wall_kind != LBM_WALL_VD && c.wall_kind != LBM_WALL_SF &&
+        c.wall_kind != LBM_WALL_GF)
         return fail(nullptr, LBM_ERR_ARG, "unknown wall scheme");
     if (c.wall_kind == LBM_WALL_SF && !std::isfinite(c.Gw)) return fail(nullptr, LBM_ERR_ARG, "Gw must be finite");
+    if (c.wall_kind == LBM_WALL_GF) {
+        if (c.lattice != LBM_D2Q9)
+            return fail(nullptr, LBM_ERR_ARG, "the geometric-formulation scheme is two-dimensional (D2Q9)");
+        if (!(c.theta_a > 0.0 && c.theta_a < 180.0))
+            return fail(nullptr, LBM_ERR_ARG, "theta_a must lie in (0, 180) degrees");
+        if (kappa_per_wall) return fail(nullptr, LBM_ERR_ARG, "kappa_per_wall applies to the IVD scheme");
+    }
     if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH &&
         c.step_kernel != LBM_KERNEL_PAIR)
         return fail(nullptr, LBM_ERR_ARG, "unknown step kernel");
@@ -405,6 +414,18 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "the grid has no fluid node");
     }
+    // geometric-formulation scheme: per wall node the crossings of its characteristic lines
+    const bool gf = c.wall_kind == LBM_WALL_GF;
+    std::vector<double> gf_table;
+    if (gf) {
+        const size_t nw = h->wall_nodes.size();
+        gf_table.assign(GF_STRIDE * (nw ? nw : 1), 0.0);
+        std::string msg;
+        if (!gf_tables(solid_mask, nx, ny, h->wall_nodes.data(), nw, c.theta_a, gf_table.data(), &msg)) {
+            delete h;
+            return fail(nullptr, LBM_ERR_ARG, msg);
+        }
+    }
     // solid flags per tile of the step kernels (see tile_solid_flags)
     {
         int t[3];
@@ -447,7 +468,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     CKI(cudaMalloc(&h->d_wall_id, sizeof(int) * N), "cudaMalloc wall_id");
     CKI(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc err");
     const size_t nw = h->wall_nodes.size();
-    CKI(cudaMalloc(&h->d_kappa, sizeof(double) * (nw ? nw : 1)), "cudaMalloc kappa");
+    CKI(cudaMalloc(&h->d_kappa, sizeof(double) * (gf ? gf_table.size() : (nw ? nw : 1))), "cudaMalloc kappa");
     CKI(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "memset err");
     CKI(cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream), "memset f");   // padding included
     CKI(cudaMemsetAsync(h->f[1], 0, h->fbytes, h->stream), "memset f");
@@ -456,6 +477,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         std::vector<double> kap(nw ? nw : 1, c.kappa);
         if (kappa_per_wall)
             for (size_t i = 0; i < nw; ++i) kap[i] = kappa_per_wall[i];
+        if (gf) kap.swap(gf_table);
         // (a copy from pageable memory has left the host buffer when the call returns)
         CKI(cudaMemcpyAsync(h->d_kappa, kap.data(), sizeof(double) * kap.size(), cudaMemcpyHostToDevice, h->stream),
             "copy kappa");
@@ -507,7 +529,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.kappa = c.kappa;
     p.rho_w_const = c.rho_w_const;
     p.Gw = c.wall_kind == LBM_WALL_SF ? c.Gw : 0.0;
-    p.kappa_w = kappa_per_wall ? h->d_kappa : nullptr;
+    p.kappa_w = (kappa_per_wall || gf) ? h->d_kappa : nullptr;   // GF: the crossing tables
     p.wall_id = h->d_wall_id;
     p.type = h->d_type;
     p.tile_solid = h->d_tile_solid;
@@ -826,6 +848,7 @@ lbm_status lbm_load_state(lbm_handle* h, const void* host_buf, size_t bytes) {
 
 lbm_status lbm_set_kappa(lbm_handle* h, const double* kappa_per_wall) {
     if (!h || !kappa_per_wall) return LBM_ERR_ARG;
+    if (h->cfg.wall_kind != LBM_WALL_IVD) return fail(h, LBM_ERR_ARG, "kappa applies to the IVD scheme");
     const size_t nw = h->wall_nodes.size();
     if (nw) CK(h, cudaMemcpyAsync(h->d_kappa, kappa_per_wall, sizeof(double) * nw, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));

@@ -276,25 +276,32 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ fin, S* __restri
                     }
                 }
                 const C rho_ave = cdiv(num, den);
-                C kap;
-                if (g.kappa_w) {
-                    const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
-                    kap = C(g.kappa_w[g.wall_id[(cgz * ny + cgy) * nx + cgx]]);
+                if (D == 2 && ph.wall_kind == 3) {
+                    // geometric formulation (Eqs. 10-15): crossings of the characteristic lines
+                    const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1);
+                    const double* t = g.kappa_w + GF_STRIDE * g.wall_id[cgy * nx + cgx];
+                    rw = gf_wall_density(t, rho_ave, [&](int dx, int dy) { return sm.rho[rix(rx + dx, ry + dy, rz)]; });
                 } else {
-                    kap = C(g.kappa);
-                }
-                // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
-                const C raw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
-                rw = raw > ph.rho_l ? ph.rho_l : raw;
-                rw = rw < ph.rho_g ? ph.rho_g : rw;
-                if constexpr (MODE == 2) {
-                    const bool free = raw < ph.rho_l && raw > ph.rho_g;   // limiter inactive
-                    sm.wdk[i] = free ? (kap >= C(0) ? rho_ave : C(1)) : C(0);
-                    sm.wda[i] = free ? (kap >= C(0) ? C(1) + kap : C(1)) / den : C(0);
+                    C kap;
+                    if (g.kappa_w) {
+                        const int cgx = wx(x0 + px - 1), cgy = wy(y0 + py - 1), cgz = wz(z0 + pz - PZH);
+                        kap = C(g.kappa_w[g.wall_id[(cgz * ny + cgy) * nx + cgx]]);
+                    } else {
+                        kap = C(g.kappa);
+                    }
+                    // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                    const C raw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
+                    rw = raw > ph.rho_l ? ph.rho_l : raw;
+                    rw = rw < ph.rho_g ? ph.rho_g : rw;
+                    if constexpr (MODE == 2) {
+                        const bool free = raw < ph.rho_l && raw > ph.rho_g;   // limiter inactive
+                        sm.wdk[i] = free ? (kap >= C(0) ? rho_ave : C(1)) : C(0);
+                        sm.wda[i] = free ? (kap >= C(0) ? C(1) + kap : C(1)) / den : C(0);
+                    }
                 }
             }
             if constexpr (MODE == 2) {
-                if (ph.wall_kind == 1) sm.wdk[i] = sm.wda[i] = C(0);
+                if (ph.wall_kind != 0) sm.wdk[i] = sm.wda[i] = C(0);   // the adjoint covers IVD only
             }
             sm.psi[i] = psi_checked(rw, ph, err);
             if constexpr (MODE == 2) sm.wdpsi[i] = psi_slope(rw, sm.psi[i], ph);

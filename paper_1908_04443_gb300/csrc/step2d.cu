@@ -151,11 +151,18 @@ __device__ __forceinline__ void ymarch_run(const S* __restrict__ fin, S* __restr
                             }
                         }
                         const C rho_ave = cdiv(num, den);
-                        const C kap = g.kappa_w ? C(g.kappa_w[g.wall_id[wy(yw) * nx + gx]]) : C(g.kappa);
-                        // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
-                        const C raw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
-                        rw = raw > ph.rho_l ? ph.rho_l : raw;
-                        rw = rw < ph.rho_g ? ph.rho_g : rw;
+                        if (ph.wall_kind == 3) {
+                            // geometric formulation (Eqs. 10-15): crossings of the characteristic lines
+                            const double* t = g.kappa_w + GF_STRIDE * g.wall_id[wy(yw) * nx + gx];
+                            rw = gf_wall_density(t, rho_ave,
+                                                 [&](int dx, int dy) { return sm.rho[(yw + dy) & 3][hx + dx]; });
+                        } else {
+                            const C kap = g.kappa_w ? C(g.kappa_w[g.wall_id[wy(yw) * nx + gx]]) : C(g.kappa);
+                            // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                            const C raw = (kap >= C(0)) ? (C(1) + kap) * rho_ave : rho_ave + kap;
+                            rw = raw > ph.rho_l ? ph.rho_l : raw;
+                            rw = rw < ph.rho_g ? ph.rho_g : rw;
+                        }
                     }
                     sm.psi[yw & 7][hx] = psi_checked(rw, ph, err);
                 }

@@ -385,12 +385,19 @@ __device__ __forceinline__ void pair_body(const G& g, int parity, const Phys<flo
                         }
                     }
                     const float rho_ave = cdiv(num, den);
-                    const float kap = g.kappa_w ? float(g.kappa_w[g.wall_id[wr(y0 + py - 1, ny) * nx + wr(x0 + px - 1, nx)]])
-                                                : float(g.kappa);
-                    // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
-                    const float raw = (kap >= 0.0f) ? (1.0f + kap) * rho_ave : rho_ave + kap;
-                    rw = raw > ph.rho_l ? ph.rho_l : raw;
-                    rw = rw < ph.rho_g ? ph.rho_g : rw;
+                    const int gw = wr(y0 + py - 1, ny) * nx + wr(x0 + px - 1, nx);
+                    if (ph.wall_kind == 3) {
+                        // geometric formulation (Eqs. 10-15): crossings of the characteristic lines
+                        rw = gf_wall_density(g.kappa_w + GF_STRIDE * g.wall_id[gw], rho_ave, [&](int dx, int dy) {
+                            return sm.rho[rix(px + 1 + dx, py + 1 + dy)];
+                        });
+                    } else {
+                        const float kap = g.kappa_w ? float(g.kappa_w[g.wall_id[gw]]) : float(g.kappa);
+                        // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                        const float raw = (kap >= 0.0f) ? (1.0f + kap) * rho_ave : rho_ave + kap;
+                        rw = raw > ph.rho_l ? ph.rho_l : raw;
+                        rw = rw < ph.rho_g ? ph.rho_g : rw;
+                    }
                 }
                 sm.psi[i] = psi2(bc(rw), ph, true, false, err).v.x;
             }

@@ -5,6 +5,7 @@
 
 #include "kernels.h"
 #include "lattice.cuh"
+#include "wall_gf.h"
 
 namespace lbmwet {
 
@@ -64,6 +65,24 @@ struct Geo {
 // FP32 state).
 __device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+
+// Virtual density of the geometric-formulation scheme at a wall node (Eq. 11) from its table entry
+// t = {lambda_1, lambda_2, code} (see wall_gf.h) and rho_at(dx, dy), the same-step density of the
+// neighbour at offset (dx, dy); rho_ave (Eq. 17) where neither crossing is usable.
+template <typename C, typename F>
+__device__ __forceinline__ C gf_wall_density(const double* t, C rho_ave, F rho_at) {
+    const unsigned code = unsigned(t[2]);
+    if (!(code & (GF_USE1 | GF_USE2))) return rho_ave;
+    auto crossing = [&](int d) {
+        const unsigned a = (code >> (8 * d)) & 15u, b = (code >> (8 * d + 4)) & 15u;
+        const C ra = rho_at(int(a & 3u) - 1, int(a >> 2) - 1);
+        const C rb = rho_at(int(b & 3u) - 1, int(b >> 2) - 1);
+        return ra + C(t[d]) * (rb - ra);
+    };
+    const C r1 = (code & GF_USE1) ? crossing(0) : crossing(1);
+    const C r2 = (code & GF_USE2) ? crossing(1) : r1;
+    return (code & GF_MAX) ? (r1 > r2 ? r1 : r2) : (r1 < r2 ? r1 : r2);
+}
 
 template <class C>
 __device__ __forceinline__ C psi_arg(C rho, const Phys<C>& e) {

@@ -20,7 +20,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE, LBM_ERR_STATE 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32_DEV = 0, 1
 LBM_EOS_PR, LBM_EOS_CS = 0, 1
-LBM_WALL_IVD, LBM_WALL_VD, LBM_WALL_SF = 0, 1, 2
+LBM_WALL_IVD, LBM_WALL_VD, LBM_WALL_SF, LBM_WALL_GF = 0, 1, 2, 3
 LBM_BODY_NONE, LBM_BODY_BALL, LBM_BODY_PLANE = 0, 1, 2
 
 
@@ -39,7 +39,7 @@ class lbm_config(C.Structure):
                 ("body_force", C.c_double * 3), ("wall_kind", C.c_int32), ("kappa", C.c_double),
                 ("rho_w_const", C.c_double), ("body_kind", C.c_int32), ("body_center", C.c_double * 3),
                 ("body_radius", C.c_double), ("drop_hint", C.c_double * 3),
-                ("step_kernel", C.c_int32), ("Gw", C.c_double)]
+                ("step_kernel", C.c_int32), ("Gw", C.c_double), ("theta_a", C.c_double)]
 
 
 class lbm_obs(C.Structure):
@@ -372,11 +372,12 @@ def make_eos(kind: str, a: float, b: float, R: float = 1.0, T: float = 0.0, omeg
 def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos, *, G=-1.0, sigma=0.12,
                 s_rho=1.0, s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1, s_nu=1.0 / 0.95, s_pi=1.1, s_m=1.1,
                 rho_l=0.0, rho_g=0.0, rho_ref=0.0, body_force=(0.0, 0.0, 0.0), wall="IVD", kappa=0.0,
-                rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0), step_kernel="auto", Gw=0.0) -> lbm_config:
+                rho_w_const=1.0, body=None, drop_hint=(0.0, 0.0, 0.0), step_kernel="auto", Gw=0.0,
+                theta_a=90.0) -> lbm_config:
     """Build an lbm_config.  `shape` is the numpy shape (ny, nx) or (nz, ny, nx).  `body` is
     ("ball", center, radius) or ("plane", wall_y) or None.  `step_kernel` is "auto", "tile",
     "ymarch" or "pair" (D2Q9 work decomposition, see lbm_step_kernel in the header).  `wall` is
-    "IVD" (parameter kappa), "VD" (rho_w_const) or "SF" (Gw)."""
+    "IVD" (parameter kappa), "VD" (rho_w_const), "SF" (Gw) or "GF" (theta_a, degrees; D2Q9)."""
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
     else:
@@ -392,8 +393,9 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
     for i in range(3):
         cfg.body_force[i] = body_force[i] if i < len(body_force) else 0.0
         cfg.drop_hint[i] = drop_hint[i] if i < len(drop_hint) else 0.0
-    cfg.wall_kind = {"IVD": LBM_WALL_IVD, "VD": LBM_WALL_VD, "SF": LBM_WALL_SF}[wall]
+    cfg.wall_kind = {"IVD": LBM_WALL_IVD, "VD": LBM_WALL_VD, "SF": LBM_WALL_SF, "GF": LBM_WALL_GF}[wall]
     cfg.Gw = Gw
+    cfg.theta_a = theta_a
     cfg.kappa = kappa
     cfg.rho_w_const = rho_w_const
     cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2, "pair": 3}[step_kernel]

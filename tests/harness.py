@@ -29,6 +29,7 @@ class Case:
     wall: str = "IVD"
     rho_w_const: float = 0.2
     Gw: float = 0.0
+    theta_a: float = 90.0
     body_force: tuple = (0.0, 0.0, 0.0)
     u0: Optional[np.ndarray] = None
     rates: dict = dataclasses.field(default_factory=dict)
@@ -47,8 +48,8 @@ class Case:
     def oracle(self):
         g, l = self.bounds()
         p = lbm.Params(self.lattice, self.oracle_eos(), sigma=self.sigma, rho_l=l, rho_g=g, kappa=self.kappa,
-                       wall=self.wall, rho_w_const=self.rho_w_const, Gw=self.Gw, body_force=self.body_force,
-                       **self.rates)
+                       wall=self.wall, rho_w_const=self.rho_w_const, Gw=self.Gw, theta_a=self.theta_a,
+                       body_force=self.body_force, **self.rates)
         geo = lbm.Geometry(self.mask, self.lattice)
         f0 = lbm.init_state(self.rho0, geo, self.u0)
         return geo, p, f0
@@ -61,6 +62,7 @@ class Case:
         kappa_scalar = float(self.kappa) if np.ndim(self.kappa) == 0 else 0.0
         cfg = L.make_config(self.lattice, precision, self.shape, e, sigma=self.sigma, rho_l=l, rho_g=g,
                             kappa=kappa_scalar, wall=self.wall, rho_w_const=self.rho_w_const, Gw=self.Gw,
+                            theta_a=self.theta_a,
                             body_force=self.body_force, body=self.body, drop_hint=self.drop_hint,
                             rho_ref=self.rho_ref, step_kernel=self.step_kernel, **self.rates)
         kpw = None if np.ndim(self.kappa) == 0 else np.asarray(self.kappa, dtype=np.float64)

@@ -121,3 +121,30 @@ def test_bounded_wait_selftest_rejects_zero_polls_before_device_work():
     with pytest.raises(L.LbmError) as ei:
         L.lbm_selftest_bounded_wait(0)
     assert ei.value.status == L.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("case", ["3d", "theta0", "theta180", "thetanan", "kappa", "thin"])
+def test_gf_scheme_rejections(case):
+    """The geometric-formulation scheme is two-dimensional, needs 0 < theta_a < 180, takes no
+    per-wall-node kappa, and cannot give a normal to a wall node whose Eq. 13 sum vanishes (a solid
+    line one node thick): each is rejected with LBM_ERR_ARG before any device work."""
+    e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
+    e.T = 0.7 * L.lbm_critical_temperature(e)
+    shape, kw, mask, kpw = (8, 10), dict(wall="GF", theta_a=60.0), None, None
+    if case == "3d":
+        shape = (6, 8, 10)
+    elif case.startswith("theta"):
+        kw["theta_a"] = {"theta0": 0.0, "theta180": 180.0, "thetanan": float("nan")}[case]
+    mask = np.zeros(shape, np.uint8)
+    if case == "thin":
+        mask[4, :] = 1                                  # a one-node-thick plate, periodic in x
+    else:
+        mask[..., :2, :] = 1
+    if case == "kappa":
+        kpw = np.full(int(mask.sum()), 0.1)
+    cfg = L.make_config("D3Q19" if case == "3d" else "D2Q9", "fp64", shape, e, **kw)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_init(cfg, mask, kappa_per_wall=kpw)
+    assert ei.value.status == L.LBM_ERR_ARG
+    if case == "thin":
+        assert "normal" in str(ei.value)
