@@ -44,8 +44,8 @@ UNIT = "MLUPS"
 # of the kernel sources: when the sources change the figure is stale and reported as null.
 NCU_TRAFFIC = {
     # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
-    # one launch (214,311,680 + 157,672,448 bytes)
-    ("c2", "fp32", "3ab4a01ec56daf3b"): 371984128,
+    # one launch (214,332,672 + 157,231,872 bytes)
+    ("c2", "fp32", "ed013185aff0a47f"): 371564544,
 }
 
 
@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
 # instructions of one launch) / nodes = (2 x 478,996,920 + 503,049,168 + 231,630,840) / 5,760,000;
 # keyed by a hash of the tile kernel's sources.
 FP64_FLOPS_PER_NODE = {
-    ("c2", "96299da93062cf8a"): 293.87,
+    ("c2", "6614596315506827"): 293.87,
 }
 # FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
 # SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
