@@ -1,0 +1,71 @@
+"""The paper's comparison of the four contact-angle schemes on the Sec. IV.A cylinder (300 x 350,
+PR at 0.86 Tc, R = 70 at (150, 130), drop r = 50 at (150, 230)), FP32, 30,000 steps.
+
+  * With the parameters the paper tunes to about 60 degrees (Sec. IV.B: rho_w = 3.45, theta_a =
+    63.5, phi = 1.135) the virtual-density, geometric and improved schemes all give about 60
+    degrees (measured 61.2, 63.2 and 62.3).
+  * Mass-transfer layer (Figs. 4 and 7): next to the lower half of the cylinder, far from the
+    drop, the constant virtual density leaves a dense layer (mean 1.73 against rho_g = 0.39); the
+    geometric and improved schemes leave the gas there (0.39 and 0.44).
+  * Spurious currents (Fig. 10): below 0.006 for the three virtual-density-type schemes, smaller
+    for the geometric and improved schemes than for the constant virtual density, largest for the
+    solid-fluid interaction.
+  * Extreme densities (Fig. 11): at the coexistence values for the three, the gas density clearly
+    off for the solid-fluid interaction (0.28).
+The solid-fluid interaction's angle is not compared: the paper does not say how the cohesive
+force treats solid nodes under that scheme, and the reading taken here (psi = 0 on solids) gives
+other angles for its G_w values."""
+import numpy as np
+import pytest
+
+from tests.harness import drop_on_cylinder
+
+pytestmark = pytest.mark.gpu
+
+SHAPE, C, R = (350, 300), (150.0, 130.0), 70.0
+SCHEMES = {"VD": dict(wall="VD", rho_w_const=3.45), "GF": dict(wall="GF", theta_a=63.5),
+           "IVD": dict(kappa=0.135), "SF": dict(wall="SF", Gw=-0.6)}
+
+
+def _run(kw):
+    case = drop_on_cylinder(SHAPE, C, R, (150.0, 230.0), 50.0, eos_kind="PR", t_over_tc=0.86, sigma=0.11, **kw)
+    case.rho_ref = case.bounds()[0]
+    with case.gpu("fp32") as sim:
+        sim.step(30000)
+        o, rho, _ = sim.observables(fields=True)
+    yy, xx = np.mgrid[0:SHAPE[0], 0:SHAPE[1]]
+    d = np.hypot(xx - C[0], yy - C[1]) - R
+    layer = float(rho[(d > 0) & (d <= 2.0) & (yy < 110)].mean())
+    return o, layer, case.bounds()
+
+
+@pytest.fixture(scope="module")
+def results():
+    return {k: _run(kw) for k, kw in SCHEMES.items()}
+
+
+def test_three_schemes_reach_about_sixty_degrees(results):
+    for k in ("VD", "GF", "IVD"):
+        assert abs(results[k][0].theta_deg - 60.0) < 5.0, k
+
+
+def test_mass_transfer_layer_only_with_the_constant_virtual_density(results):
+    g = results["VD"][2][0]
+    assert results["VD"][1] > 3.0 * g
+    assert results["GF"][1] < 1.05 * g
+    assert results["IVD"][1] < 1.25 * g
+
+
+def test_spurious_currents_ordering(results):
+    u = {k: v[0].u_max for k, v in results.items()}
+    assert max(u["VD"], u["GF"], u["IVD"]) < 0.006
+    assert u["GF"] < u["VD"] and u["IVD"] < u["VD"]
+    assert u["SF"] > u["VD"]
+
+
+def test_extreme_densities(results):
+    g, l = results["VD"][2]
+    for k in ("VD", "GF", "IVD"):
+        o = results[k][0]
+        assert abs(o.rho_max / l - 1) < 0.01 and abs(o.rho_min / g - 1) < 0.05, k
+    assert results["SF"][0].rho_min < 0.85 * g
