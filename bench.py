@@ -193,26 +193,43 @@ print(json.dumps({{"times": times, "nodes": wl.nodes}}))
 """
 
 
-def run_oracle(wl_name: str, steps: int, warmup: int):
+def run_oracle(wl_name: str, steps: int, warmup: int, procs: int = 1):
+    """Step times of `procs` concurrent single-thread oracle processes (one list per process) and
+    the grid's node count."""
     ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()", "c4": "c4_batch(96)[0]"}.get(
         wl_name, "c2_cylinder_600x400(kappa=0.15)")
     code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["times"], d["nodes"]
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    outs = []
+    for pr in ps:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    return [d["times"] for d in outs], outs[0]["nodes"]
 
 
-def cpu_baseline(wl_name: str, target_s: float = 15.0):
+def cpu_baseline(wl_name: str, target_s: float = 15.0, all_cores: bool = True):
     # estimate the step time from one step, then take a sample of about target_s seconds
-    t1, nodes = run_oracle(wl_name, 1, 0)
+    (t1,), nodes = run_oracle(wl_name, 1, 0)
     n = max(1, min(2000, int(target_s / max(t1[0], 1e-4))))
-    times, nodes = run_oracle(wl_name, n, 0)
+    (times,), nodes = run_oracle(wl_name, n, 0)
     total = sum(times)
-    return {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 oracle steps of one {nodes}-node grid of the workload, one thread"}
+    res = {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} FP64 oracle steps of one {nodes}-node grid of the workload, one thread"}
+    procs = os.cpu_count() or 1
+    if all_cores and procs > 1:
+        # every host core: the workload's grids are independent, so one single-thread oracle
+        # process per core, each on a grid of the workload, all at once
+        m = max(1, n // 2)
+        runs, _ = run_oracle(wl_name, m, 0, procs)
+        slowest = max(sum(t) for t in runs)
+        res["all_cores"] = {"value": round(procs * nodes * m / slowest / 1e6, 4), "unit": UNIT, "cores": procs,
+                            "sample": f"{procs} concurrent single-thread oracle processes, {m} steps each of one "
+                                      f"{nodes}-node grid of the workload (rate over the slowest process)"}
+    return res
 
 
 # ---------------------------------------------------------------------------------------------
@@ -606,7 +623,7 @@ def run_reference(args):
     if rank != 0:
         return
     wls, precision, label = workload(args.workload)
-    times, nodes = run_oracle(args.workload, args.steps, args.warmup)
+    (times,), nodes = run_oracle(args.workload, args.steps, args.warmup)
     total = sum(times)
     value = nodes * args.steps / total / 1e6
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,

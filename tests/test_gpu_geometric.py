@@ -54,6 +54,32 @@ def test_gf_one_step_fp32(kernel, theta_a, grid):
     assert np.max(np.abs(f1 - ref)) <= 2e-6 * np.max(np.abs(ref))
 
 
+def _notch_case(theta_a, kernel):
+    """A solid block with a notch and a post under it (concave corners: crossings with solid ends,
+    unusable crossings and the Eq. 17 fallback all occur), a drop over the notch."""
+    import workloads as W
+    from tests.harness import Case
+    base = drop_on_cylinder((40, 48), (24.0, 30.0), 5.0, (22.0, 24.0), 8.0)   # for the EOS and densities
+    g, l = base.bounds()
+    mask = np.zeros((40, 48), np.uint8)
+    mask[5:20, 8:40] = 1
+    mask[12:20, 18:26] = 0
+    mask[20:30, 30:34] = 1
+    rho = W.tanh_drop_density((40, 48), (22.0, 24.0), 8.0, l, g) + W.density_noise((40, 48), 1e-6, 99)
+    rho = np.where(mask != 0, g, rho)
+    return Case("D2Q9", (40, 48), mask, rho, wall="GF", theta_a=theta_a, step_kernel=kernel)
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp64", "tile"), ("fp64", "ymarch"), ("fp32", "pair")])
+@pytest.mark.parametrize("theta_a", [20.0, 60.0, 170.0])
+def test_gf_concave_corners(precision, kernel, theta_a):
+    f1, ref = _one_step(_notch_case(theta_a, kernel), precision)
+    if precision == "fp64":
+        assert np.max(np.abs(f1 - ref)) < 1e-13
+    else:
+        assert np.max(np.abs(f1 - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("kernel", ["tile", "ymarch"])
 def test_gf_run_fp64(kernel):
     """40 steps from the initial state: the wall densities feed back through the whole run."""
