@@ -148,3 +148,14 @@ def test_gf_scheme_rejections(case):
     assert ei.value.status == L.LBM_ERR_ARG
     if case == "thin":
         assert "normal" in str(ei.value)
+
+
+def test_batch_rejects_mixed_wall_schemes():
+    """A batch shares one wall scheme (instances may differ in its per-grid parameter, such as the
+    geometric formulation's theta_a): a geometric-formulation grid with an IVD grid is rejected with
+    LBM_ERR_ARG before any device work."""
+    m = np.zeros((8, 8), np.uint8)
+    m[:2, :] = 1
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_batch_init([_cfg(wall="GF", theta_a=60.0), _cfg(kappa=0.1)], [m, m])
+    assert ei.value.status == L.LBM_ERR_ARG
