@@ -3,7 +3,7 @@
 FP64 storage: within 1e-10 max-abs in density after the 1000 steps of the 100x100 cylinder
 workload, within 1e-13 after one step on assorted small grids (ragged tiles, tiny grids, all-fluid,
 per-wall-node kappa, VD walls, body force, PR and C-S).  FP32 deviation storage: within 1e-4
-relative in density.  Observables (mass, density extremes, max |u|, contact angle) are compared with
+relative in density at bulk nodes and 1e-4 of the liquid density in the interface band.  Observables (mass, density extremes, max |u|, contact angle) are compared with
 the oracle's on the same state.
 """
 import numpy as np
@@ -11,6 +11,7 @@ import pytest
 
 import workloads as W
 from oracle import lbm, contact_angle as CA
+from tests.fp32_bounds import split_errors
 from tests.harness import Case, c1_case, drop_on_cylinder
 
 pytestmark = pytest.mark.gpu
@@ -107,12 +108,12 @@ def test_c1_fp64_1000_steps():
 
 @pytest.mark.parametrize("kernel", ["pair", "tile"])
 def test_c1_fp32_deviation_storage(kernel):
-    """FP32 deviation storage vs the FP64 oracle after 1000 steps: density within 1e-4 relative to
-    the liquid density (the system's density scale) at every fluid node, within 1e-4 in the relative
-    L2 norm, and the contact angle within 0.5 degrees.  (The drop is still spreading at step 1000:
-    the FP64 path itself differs from the oracle by ~5e-12 there although each step agrees to 1e-16,
-    so rounding is amplified ~1e4-fold by the dynamics; a per-node relative bound at gas-side
-    interface nodes would measure that amplification, not the storage precision.)"""
+    """FP32 deviation storage vs the FP64 oracle after 1000 steps: 1e-4 relative in density at every
+    bulk fluid node (more than 3 nodes from the rho_mid contour and from a solid), 1e-4 of the
+    liquid density inside that interface band, and the contact angle within 0.5 degrees.  (The drop
+    is still spreading at step 1000: rounding that moves the interface by a tiny fraction of a node
+    changes the density in the band by a large fraction of itself, so the band is held to the
+    liquid density scale; see tests/fp32_bounds.py.)"""
     case = c1_case()
     case.step_kernel = kernel
     g, l = case.bounds()
@@ -123,10 +124,11 @@ def test_c1_fp32_deviation_storage(kernel):
     with case.gpu("fp32") as sim:
         sim.step(1000)
         o, rho, _ = sim.observables(fields=True)
-    fl = geo.fluid
-    d = np.abs(rho[fl] - rho_ref[fl])
-    assert d.max() < 1e-4 * l
-    assert np.linalg.norm(d) < 1e-4 * np.linalg.norm(rho_ref[fl])
+    bulk, band, nb, ni = split_errors(rho, rho_ref, case.mask, l, g)
+    print(f"C1 FP32 ({kernel}) after 1000 steps: bulk max |drho|/rho = {bulk:.3e} over {nb} nodes, "
+          f"interface band max |drho|/rho_l = {band:.3e} over {ni} nodes")
+    assert bulk <= 1e-4
+    assert band <= 1e-4
     th, *_ = CA.contact_angle(rho_ref, case.mask, l, g, case.drop_hint, case.body[1], case.body[2])
     assert abs(o.theta_deg - th) < 0.5
 

@@ -1,11 +1,13 @@
 """D3Q19 parity of the CUDA path with the FP64 oracle: one step on ragged 3D grids (tiles of
 32 x 4 x 4 do not divide them), 60 steps of a drop on a sphere in FP64 (1e-11) and FP32 deviation
-storage (1e-4 of the liquid density), per-wall-node kappa, the constant virtual density, and the
-3D observables (mass, extremes, max |u|, sphere-fit contact angle)."""
+storage (1e-4 relative at bulk nodes, 1e-4 of the liquid density in the interface band),
+per-wall-node kappa, the constant virtual density, and the 3D observables (mass, extremes,
+max |u|, sphere-fit contact angle)."""
 import numpy as np
 import pytest
 
 from oracle import lbm, contact_angle as CA
+from tests.fp32_bounds import split_errors
 from tests.harness import drop_on_cylinder
 
 pytestmark = pytest.mark.gpu
@@ -67,7 +69,11 @@ def test_sphere_60_steps_fp64_and_fp32():
     with case.gpu("fp32") as sim:
         sim.step(60)
         o32, rho32, _ = sim.observables(fields=True)
-    assert np.max(np.abs(rho32[fl] - rho_ref[fl])) < 1e-4 * l
+    bulk, band, nb, ni = split_errors(rho32, rho_ref, case.mask, l, g)
+    print(f"D3Q19 FP32 after 60 steps: bulk max |drho|/rho = {bulk:.3e} over {nb} nodes, "
+          f"interface band max |drho|/rho_l = {band:.3e} over {ni} nodes")
+    assert bulk <= 1e-4
+    assert band <= 1e-4
     assert abs(o32.theta_deg - th) < 0.5
 
 
