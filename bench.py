@@ -275,6 +275,7 @@ class Runner:
     def __init__(self, L, cfgs, masks, rho0s, stream):
         self.L = L
         self.batch = len(cfgs) > 1
+        self.lattice3 = cfgs[0].lattice == 1
         if self.batch:
             self.b = L.lbm_batch_init(cfgs, masks, rho0s, None, stream)
             self.handles = [L.lbm_batch_handle(self.b, i) for i in range(len(cfgs))]
@@ -301,6 +302,10 @@ class Runner:
     def kernel_name(self):
         """Name of the step kernel this run launches."""
         k = self.L.lbm_batch_step_kernel_used(self.b) if self.batch else self.L.lbm_step_kernel_used(self.h)
+        if k == "ztma":
+            return "ztma_step"
+        if self.lattice3:
+            return "zpair_step" if k == "pair" else "zmarch_step"
         if k == "ymarch":
             return "ymarch_step"
         if k == "pair":
@@ -650,8 +655,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint side measurements")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "tile", "ymarch", "pair"],
-                    help="D2Q9 step kernel (auto: pair in FP32, tile in FP64)")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "tile", "ymarch", "pair", "ztma"],
+                    help="step kernel (auto: pair in D2Q9 FP32, ztma in D3Q19 FP32, tile in FP64)")
     args = ap.parse_args()
     STEP_KERNEL = args.step_kernel
     if args.impl == "reference":

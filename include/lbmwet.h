@@ -79,15 +79,24 @@ typedef enum { LBM_WALL_IVD = 0, LBM_WALL_VD = 1, LBM_WALL_SF = 2, LBM_WALL_GF =
  * PLANE: a flat wall at y = body_center[1] (the halfway position), liquid at larger y. */
 typedef enum { LBM_BODY_NONE = 0, LBM_BODY_BALL = 1, LBM_BODY_PLANE = 2 } lbm_body_kind;
 
-/* Step kernel of a D2Q9 grid (no counterpart in the paper: a choice of work decomposition).
- * TILE: one CTA per 32 x 8 tile with its halo ring, one node per thread.  YMARCH: persistent CTAs
- * walking runs of rows of column blocks (124 own columns plus a 2-cell halo on each side),
- * planned on the host so that every CTA pulls about the same number of rows; bit-identical to
- * TILE.  PAIR (FP32 only): 32 x 16 tiles, two nodes per thread computed together with packed
- * FP32x2 instructions; equal to TILE up to FP32 rounding (the operations are regrouped).  AUTO:
- * PAIR in FP32, TILE in FP64.  A batch uses instance 0's choice.  A y-march handle that records a
- * trajectory for the adjoint steps with TILE from lbm_record on. */
-typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_TILE = 1, LBM_KERNEL_YMARCH = 2, LBM_KERNEL_PAIR = 3 } lbm_step_kernel;
+/* Step kernel (no counterpart in the paper: a choice of work decomposition).
+ * D2Q9:
+ *   TILE: one CTA per 32 x 8 tile with its halo ring, one node per thread.  YMARCH: persistent
+ *   CTAs walking runs of rows of column blocks (124 own columns plus a 2-cell halo on each side),
+ *   planned on the host so that every CTA pulls about the same number of rows; bit-identical to
+ *   TILE.  PAIR (FP32 only): 32 x 16 tiles, two nodes per thread computed together with packed
+ *   FP32x2 instructions; equal to TILE up to FP32 rounding (the operations are regrouped).  AUTO:
+ *   PAIR in FP32, TILE in FP64.  A batch uses instance 0's choice.  A y-march handle that records
+ *   a trajectory for the adjoint steps with TILE from lbm_record on.
+ * D3Q19 (every kernel marches z-planes through 32-plane chunks of x-y columns):
+ *   ZTMA (FP32 only): 32 x 8 columns whose lead plane's 19 pull boxes are staged in shared memory
+ *   by TMA, two planes in flight, two cells per thread in packed FP32x2 arithmetic; chunks holding
+ *   solids run the z-pair march.  PAIR (FP32 only): the z-pair march, 32 x 4 columns, two planes
+ *   per thread.  TILE: the scalar z-march (the only D3Q19 kernel in FP64).  AUTO: ZTMA in FP32
+ *   (PAIR where the rows are not a multiple of 16 bytes), TILE in FP64.  The FP32 kernels agree up
+ *   to FP32 rounding. */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_TILE = 1, LBM_KERNEL_YMARCH = 2, LBM_KERNEL_PAIR = 3,
+               LBM_KERNEL_ZTMA = 4 } lbm_step_kernel;
 
 typedef struct {
     int32_t kind;      /* lbm_eos_kind                                       */
@@ -117,7 +126,7 @@ typedef struct {
     double body_radius;
     double drop_hint[3];        /* a point inside the drop: interface points are unwrapped to the
                                    periodic image nearest to it                                  */
-    int32_t step_kernel;        /* lbm_step_kernel (D2Q9; D3Q19 always uses its z-march)         */
+    int32_t step_kernel;        /* lbm_step_kernel                                               */
     double Gw;                  /* SF adhesion parameter (Eq. 8)                                 */
     double theta_a;             /* GF prescribed contact angle, degrees in (0, 180)              */
 } lbm_config;
@@ -249,8 +258,9 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
-/* Step kernel the handle's lbm_step uses now: LBM_KERNEL_TILE, LBM_KERNEL_YMARCH or
- * LBM_KERNEL_PAIR (D2Q9, see lbm_step_kernel), LBM_KERNEL_AUTO for D3Q19 (z-march) or a NULL handle. */
+/* Step kernel the handle's lbm_step uses now (see lbm_step_kernel): LBM_KERNEL_TILE,
+ * LBM_KERNEL_YMARCH or LBM_KERNEL_PAIR for D2Q9; LBM_KERNEL_ZTMA, LBM_KERNEL_PAIR or
+ * LBM_KERNEL_TILE for D3Q19; LBM_KERNEL_AUTO for a NULL handle. */
 int32_t lbm_step_kernel_used(const lbm_handle* h);
 
 /* ---- Adjoint (D2Q9, IVD walls) -------------------------------------------------------------

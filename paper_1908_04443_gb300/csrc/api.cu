@@ -50,6 +50,7 @@ struct lbm_handle {
     std::vector<uint8_t> tile_solid;   // per step-kernel tile: a solid node within the tile + 3-node halo
     std::vector<uint8_t> pair_solid;   // the same per tile of the FP32 pair kernel (D2Q9)
     uint8_t* d_pair_solid = nullptr;   // set when this handle steps with the pair kernel
+    void* d_zmaps = nullptr;           // D3Q19 FP32: TMA tensor maps of f[0] and f[1]
     int tiles[3] = {1, 1, 1};
     int int_tile[3] = {1, 1, 1};
     int* d_wall_id = nullptr;
@@ -143,6 +144,23 @@ bool encode_pair_map(CUtensorMap* m, void* f, int nx, int ny, int fp, long long 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// TMA tensor map of one FP32 D3Q19 distribution buffer f[a][z][y][x] seen as a 3D tensor
+// (x, y, a * nz + z): a box of the TMA-staged z-march (one direction on one plane, `by` rows).
+// False where TMA cannot address the buffer (rows not a multiple of 16 bytes).
+bool encode_z_map(CUtensorMap* m, void* f, int nx, int ny, int nz, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || nx % 4 != 0) return false;
+    int bx, by_bulk, by_solid;
+    ztma_box_dims(&bx, &by_bulk, &by_solid);
+    const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(19) * cuuint64_t(nz)};
+    const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * cuuint64_t(ny) * 4};
+    const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 lbm_status fail(lbm_handle* h, lbm_status s, const std::string& msg) {
     if (h) h->err = msg;
     else g_init_error = msg;
@@ -198,6 +216,7 @@ void free_all(lbm_handle* h) {
     cudaFree(h->d_type);
     cudaFree(h->d_tile_solid);
     cudaFree(h->d_pair_solid);
+    cudaFree(h->d_zmaps);
     cudaFree(h->d_yitems);
     cudaFree(h->d_ybegin);
     cudaFree(h->d_wall_id);
@@ -289,6 +308,78 @@ lbm_status enqueue_steps(lbm_handle* h, int64_t n) {
     return LBM_OK;
 }
 
+// lbm_obs from the NRED sums of the observables reduction (mass, density extremes, max |u|^2,
+// interface-point moments): the Kasa circle/sphere fit and the contact angle on the handle's body.
+// Shared by lbm_observables and lbm_observables_noalloc.
+void obs_from_reduction(const lbm_handle* h, const double* red, lbm_obs* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->mass = red[0];
+    out->rho_max = red[1];
+    out->rho_min = red[2];
+    out->u_max = std::sqrt(red[3]);
+    out->step = h->step;
+    out->theta_deg = NAN;
+    out->drop_radius = NAN;
+    for (int k = 0; k < 3; ++k) out->drop_center[k] = NAN;
+    const double n = red[4];
+    out->n_interface = (int64_t)n;
+    const int D = h->D;
+    if (!(n >= D + 1)) return;
+    // Kasa normal equations for (D_1..D_d, F): sum (|p|^2 + D.p + F)^2 minimal, p relative to the hint
+    const double m1[3] = {red[5], red[6], red[7]};
+    const double mxx[3][3] = {{red[8], red[11], red[12]}, {red[11], red[9], red[13]}, {red[12], red[13], red[10]}};
+    const double mr[3] = {red[14], red[15], red[16]};
+    const int m = D + 1;
+    double A[4][5];
+    for (int i = 0; i < D; ++i) {
+        for (int j = 0; j < D; ++j) A[i][j] = mxx[i][j];
+        A[i][D] = m1[i];
+        A[i][m] = -mr[i];
+    }
+    for (int j = 0; j < D; ++j) A[D][j] = m1[j];
+    A[D][D] = n;
+    A[D][m] = -red[17];
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        if (std::fabs(A[piv][col]) < 1e-300) return;
+        for (int j = 0; j <= m; ++j) std::swap(A[col][j], A[piv][j]);
+        for (int r = 0; r < m; ++r) {
+            if (r == col) continue;
+            const double fct = A[r][col] / A[col][col];
+            for (int j = col; j <= m; ++j) A[r][j] -= fct * A[col][j];
+        }
+    }
+    double c[3] = {0, 0, 0}, cc = 0;
+    for (int k = 0; k < D; ++k) {
+        c[k] = -0.5 * A[k][m] / A[k][k];
+        cc += c[k] * c[k];
+    }
+    const double r2 = cc - A[D][m] / A[D][D];
+    if (!(r2 > 0)) return;
+    const double r = std::sqrt(r2);
+    for (int k = 0; k < D; ++k) out->drop_center[k] = h->cfg.drop_hint[k] + c[k];
+    out->drop_radius = r;
+    double cth = NAN;
+    if (h->cfg.body_kind == LBM_BODY_BALL) {
+        const double Rw = h->cfg.body_radius + 0.5;
+        double d2 = 0;
+        for (int k = 0; k < D; ++k) {
+            const double dd = out->drop_center[k] - h->cfg.body_center[k];
+            d2 += dd * dd;
+        }
+        cth = (Rw * Rw + r * r - d2) / (2.0 * Rw * r);
+    } else if (h->cfg.body_kind == LBM_BODY_PLANE) {
+        cth = -(out->drop_center[1] - h->cfg.body_center[1]) / r;
+    }
+    if (!std::isnan(cth)) {
+        cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
+        out->theta_deg = std::acos(cth) * 180.0 / M_PI;
+    }
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -353,10 +444,14 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         if (kappa_per_wall) return fail(nullptr, LBM_ERR_ARG, "kappa_per_wall applies to the IVD scheme");
     }
     if (c.step_kernel != LBM_KERNEL_AUTO && c.step_kernel != LBM_KERNEL_TILE && c.step_kernel != LBM_KERNEL_YMARCH &&
-        c.step_kernel != LBM_KERNEL_PAIR)
+        c.step_kernel != LBM_KERNEL_PAIR && c.step_kernel != LBM_KERNEL_ZTMA)
         return fail(nullptr, LBM_ERR_ARG, "unknown step kernel");
-    if (c.step_kernel == LBM_KERNEL_PAIR && (c.lattice != LBM_D2Q9 || c.precision != LBM_FP32_DEV))
-        return fail(nullptr, LBM_ERR_ARG, "the pair kernel is for D2Q9 in FP32");
+    if (c.step_kernel == LBM_KERNEL_PAIR && c.precision != LBM_FP32_DEV)
+        return fail(nullptr, LBM_ERR_ARG, "the pair kernels (D2Q9 pair, D3Q19 z-pair march) are FP32");
+    if (c.step_kernel == LBM_KERNEL_YMARCH && c.lattice != LBM_D2Q9)
+        return fail(nullptr, LBM_ERR_ARG, "the y-march is a D2Q9 kernel");
+    if (c.step_kernel == LBM_KERNEL_ZTMA && (c.lattice != LBM_D3Q19 || c.precision != LBM_FP32_DEV))
+        return fail(nullptr, LBM_ERR_ARG, "the TMA-staged z-march is for D3Q19 in FP32");
     double tc;
     lbm_status st = lbm_critical_temperature(&c.eos, &tc);
     if (st != LBM_OK) return st;
@@ -534,6 +629,24 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.type = h->d_type;
     p.tile_solid = h->d_tile_solid;
     p.err = h->d_err;
+    // D3Q19 FP32 step kernel and the tensor maps of the TMA-staged z-march
+    p.step3 = c.step_kernel == LBM_KERNEL_PAIR ? 1 : (c.step_kernel == LBM_KERNEL_TILE ? 2 : 0);
+    p.ztmap = nullptr;
+    p.zf0 = h->f[0];
+    if (h->D == 3 && c.precision == LBM_FP32_DEV && p.step3 == 0) {
+        // per buffer: the box of chunks without solids (rows y0 - 2 .. y0 + 9), then the one of chunks
+        // holding solids (rows y0 - 3 .. y0 + 10)
+        int bx, by_bulk, by_solid;
+        ztma_box_dims(&bx, &by_bulk, &by_solid);
+        CUtensorMap maps[4];
+        if (encode_z_map(&maps[0], h->f[0], nx, ny, nz, by_bulk) && encode_z_map(&maps[1], h->f[0], nx, ny, nz, by_solid) &&
+            encode_z_map(&maps[2], h->f[1], nx, ny, nz, by_bulk) && encode_z_map(&maps[3], h->f[1], nx, ny, nz, by_solid)) {
+            CKI(cudaMalloc(&h->d_zmaps, sizeof(maps)), "cudaMalloc tensor maps");
+            CKI(cudaMemcpyAsync(h->d_zmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, h->stream), "copy tensor maps");
+            CKI(cudaStreamSynchronize(h->stream), "sync");
+            p.ztmap = h->d_zmaps;
+        }
+    }
 
     // initial state f = f^eq(rho0, u0), stored so that the first pull yields it
     {
@@ -705,84 +818,7 @@ lbm_status lbm_observables(lbm_handle* h, lbm_obs* out, double* rho_host, double
         CK(h, cudaMemcpyAsync(u_host, h->d_u, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost, h->stream));
     st = check_device_error(h);
     if (st != LBM_OK) return st;
-    std::memset(out, 0, sizeof(*out));
-    out->mass = red[0];
-    out->rho_max = red[1];
-    out->rho_min = red[2];
-    out->u_max = std::sqrt(red[3]);
-    out->step = h->step;
-    out->theta_deg = NAN;
-    out->drop_radius = NAN;
-    for (int k = 0; k < 3; ++k) out->drop_center[k] = NAN;
-    const double n = red[4];
-    out->n_interface = (int64_t)n;
-    // Kasa fit: minimise sum (|p|^2 + D.p + F)^2 -> normal equations, p relative to the hint
-    const int D = h->D;
-    if (n >= D + 1) {
-        const double Sx = red[5], Sy = red[6], Sz = red[7], Sxx = red[8], Syy = red[9], Szz = red[10];
-        const double Sxy = red[11], Sxz = red[12], Syz = red[13], Sxr = red[14], Syr = red[15], Szr = red[16],
-                     Sr = red[17];
-        double A[4][5];
-        int m = D + 1;
-        if (D == 2) {
-            double B[3][4] = {{Sxx, Sxy, Sx, -Sxr}, {Sxy, Syy, Sy, -Syr}, {Sx, Sy, n, -Sr}};
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 4; ++j) A[i][j] = B[i][j];
-        } else {
-            double B[4][5] = {{Sxx, Sxy, Sxz, Sx, -Sxr}, {Sxy, Syy, Syz, Sy, -Syr}, {Sxz, Syz, Szz, Sz, -Szr},
-                              {Sx, Sy, Sz, n, -Sr}};
-            for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 5; ++j) A[i][j] = B[i][j];
-        }
-        // Gaussian elimination with partial pivoting
-        bool ok = true;
-        for (int col = 0; col < m && ok; ++col) {
-            int piv = col;
-            for (int r = col + 1; r < m; ++r)
-                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
-            if (std::fabs(A[piv][col]) < 1e-300) {
-                ok = false;
-                break;
-            }
-            for (int j = 0; j <= m; ++j) std::swap(A[col][j], A[piv][j]);
-            for (int r = 0; r < m; ++r) {
-                if (r == col) continue;
-                const double fct = A[r][col] / A[col][col];
-                for (int j = col; j <= m; ++j) A[r][j] -= fct * A[col][j];
-            }
-        }
-        if (ok) {
-            double sol[4];
-            for (int i = 0; i < m; ++i) sol[i] = A[i][m] / A[i][i];
-            double c[3] = {0, 0, 0};
-            double cc = 0;
-            for (int k = 0; k < D; ++k) {
-                c[k] = -0.5 * sol[k];
-                cc += c[k] * c[k];
-            }
-            const double r2 = cc - sol[D];
-            if (r2 > 0) {
-                const double r = std::sqrt(r2);
-                for (int k = 0; k < D; ++k) out->drop_center[k] = h->cfg.drop_hint[k] + c[k];
-                out->drop_radius = r;
-                if (h->cfg.body_kind == LBM_BODY_BALL) {
-                    const double Rw = h->cfg.body_radius + 0.5;
-                    double d2 = 0;
-                    for (int k = 0; k < D; ++k) {
-                        const double dd = out->drop_center[k] - h->cfg.body_center[k];
-                        d2 += dd * dd;
-                    }
-                    double cth = (Rw * Rw + r * r - d2) / (2.0 * Rw * r);
-                    cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
-                    out->theta_deg = std::acos(cth) * 180.0 / M_PI;
-                } else if (h->cfg.body_kind == LBM_BODY_PLANE) {
-                    double cth = -(out->drop_center[1] - h->cfg.body_center[1]) / r;
-                    cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
-                    out->theta_deg = std::acos(cth) * 180.0 / M_PI;
-                }
-            }
-        }
-    }
+    obs_from_reduction(h, red, out);
     return LBM_OK;
 }
 
@@ -874,7 +910,11 @@ lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l)
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
 
 int32_t lbm_step_kernel_used(const lbm_handle* h) {
-    if (!h || h->D != 2) return LBM_KERNEL_AUTO;
+    if (!h) return LBM_KERNEL_AUTO;
+    if (h->D == 3) {
+        if (h->prec == LBM_FP64 || h->dp.step3 == 2) return LBM_KERNEL_TILE;
+        return h->dp.step3 == 0 && h->dp.ztmap ? LBM_KERNEL_ZTMA : LBM_KERNEL_PAIR;
+    }
     if (h->ymarch) return LBM_KERNEL_YMARCH;
     return h->dp.pair_solid ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE;
 }
@@ -895,77 +935,6 @@ void lbm_destroy(lbm_handle* h) {
 // library's static device scratch; allocates nothing.
 // ---------------------------------------------------------------------------------------------
 
-namespace {
-
-void obs_from_reduction(const lbm_handle* h, const double* red, lbm_obs* out) {
-    std::memset(out, 0, sizeof(*out));
-    out->mass = red[0];
-    out->rho_max = red[1];
-    out->rho_min = red[2];
-    out->u_max = std::sqrt(red[3]);
-    out->step = h->step;
-    out->theta_deg = NAN;
-    out->drop_radius = NAN;
-    for (int k = 0; k < 3; ++k) out->drop_center[k] = NAN;
-    const double n = red[4];
-    out->n_interface = (int64_t)n;
-    const int D = h->D;
-    if (!(n >= D + 1)) return;
-    // Kasa normal equations for (D_1..D_d, F): sum (|p|^2 + D.p + F)^2 minimal, p relative to the hint
-    const double m1[3] = {red[5], red[6], red[7]};
-    const double mxx[3][3] = {{red[8], red[11], red[12]}, {red[11], red[9], red[13]}, {red[12], red[13], red[10]}};
-    const double mr[3] = {red[14], red[15], red[16]};
-    const int m = D + 1;
-    double A[4][5];
-    for (int i = 0; i < D; ++i) {
-        for (int j = 0; j < D; ++j) A[i][j] = mxx[i][j];
-        A[i][D] = m1[i];
-        A[i][m] = -mr[i];
-    }
-    for (int j = 0; j < D; ++j) A[D][j] = m1[j];
-    A[D][D] = n;
-    A[D][m] = -red[17];
-    for (int col = 0; col < m; ++col) {
-        int piv = col;
-        for (int r = col + 1; r < m; ++r)
-            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
-        if (std::fabs(A[piv][col]) < 1e-300) return;
-        for (int j = 0; j <= m; ++j) std::swap(A[col][j], A[piv][j]);
-        for (int r = 0; r < m; ++r) {
-            if (r == col) continue;
-            const double fct = A[r][col] / A[col][col];
-            for (int j = col; j <= m; ++j) A[r][j] -= fct * A[col][j];
-        }
-    }
-    double c[3] = {0, 0, 0}, cc = 0;
-    for (int k = 0; k < D; ++k) {
-        c[k] = -0.5 * A[k][m] / A[k][k];
-        cc += c[k] * c[k];
-    }
-    const double r2 = cc - A[D][m] / A[D][D];
-    if (!(r2 > 0)) return;
-    const double r = std::sqrt(r2);
-    for (int k = 0; k < D; ++k) out->drop_center[k] = h->cfg.drop_hint[k] + c[k];
-    out->drop_radius = r;
-    double cth = NAN;
-    if (h->cfg.body_kind == LBM_BODY_BALL) {
-        const double Rw = h->cfg.body_radius + 0.5;
-        double d2 = 0;
-        for (int k = 0; k < D; ++k) {
-            const double dd = out->drop_center[k] - h->cfg.body_center[k];
-            d2 += dd * dd;
-        }
-        cth = (Rw * Rw + r * r - d2) / (2.0 * Rw * r);
-    } else if (h->cfg.body_kind == LBM_BODY_PLANE) {
-        cth = -(out->drop_center[1] - h->cfg.body_center[1]) / r;
-    }
-    if (!std::isnan(cth)) {
-        cth = cth > 1 ? 1 : (cth < -1 ? -1 : cth);
-        out->theta_deg = std::acos(cth) * 180.0 / M_PI;
-    }
-}
-
-}  // namespace
 
 extern "C" lbm_status lbm_observables_noalloc(lbm_handle* h, const double* rho_dev, const double* u_dev,
                                                lbm_obs* out) {

@@ -31,6 +31,10 @@ struct DevParams {
     const uint8_t* type;         // per node: T_SOLID | T_WALL | T_NEARWALL | T_BULK
     const uint8_t* tile_solid;   // per tile of the step kernel's grid: a solid node within the tile + 3-node halo
     const uint8_t* pair_solid;   // the same per tile of the FP32 pair kernel; null: FP32 steps use the tile kernel
+    // D3Q19 FP32 step kernel: 0 the TMA-staged z-march, 1 the z-pair march, 2 the scalar z-march
+    int step3;
+    const void* ztmap;           // TMA tensor maps of the two 3D FP32 distribution buffers (device, 2 x 2 x 128 B)
+    const void* zf0;             // the buffer the first map describes
     unsigned* err;               // sticky device error flags
 };
 
@@ -120,6 +124,12 @@ void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz);
 // D3Q19 FP32 step as a z-pair march (two planes per thread, packed FP32x2 arithmetic); chunk flags
 // g.tile_solid per FP32 z-march chunk.
 cudaError_t launch_zpair_step(const void* fin, void* fout, const Geo& g, const DevParams& p, cudaStream_t s);
+// D3Q19 FP32 step, TMA-staged z-march over 32 x 8 columns of 32-plane chunks (ragged columns and
+// small grids take the z-pair march); tmap: the two tensor maps of fin (dimensions x, y, 19 nz;
+// boxes bx x by_bulk x 1 and bx x by_solid x 1, see ztma_box_dims), 128 bytes each.
+cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, const Geo& g, const DevParams& p,
+                             cudaStream_t s);
+void ztma_box_dims(int* bx, int* by_bulk, int* by_solid);
 // Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);
 int batched_ctas_per_sm(int lat, int prec);

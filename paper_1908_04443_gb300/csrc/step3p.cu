@@ -458,7 +458,7 @@ __device__ __forceinline__ void zpair_chunk(const float* __restrict__ fin, float
 __global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
     zpair_step(const float* __restrict__ fin, float* __restrict__ fout, Geo g, Phys<float> ph, Rates3P kr,
                unsigned* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
     const int tile = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const bool solid = g.tile_solid ? g.tile_solid[tile] != 0 : true;
@@ -468,6 +468,583 @@ __global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
         zpair_chunk<true>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
     else
         zpair_chunk<false>(fin, fout, g, ph, kr, blockIdx.x * ZTX, blockIdx.y * ZTY, blockIdx.z * ZCH, err, sm);
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// TMA-staged z-march (the default FP32 D3Q19 step).  A CTA of 32 x 4 threads owns a 32 x 8 column
+// of a 32-plane chunk; thread (lx, ly) carries the cells (x0 + lx, y0 + ly) and (x0 + lx, y0 + ly + 4)
+// as the two lanes of its FP32x2 values.  The chunk marches plane by plane through shared memory:
+//   * every lead plane zl is staged by TMA: for each direction a, the box of f*_a on plane zl - ez(a)
+//     over x0 - 4 .. x0 + 35 (x starts on a 16-byte boundary) and y0 - 2 .. y0 + 9 (y0 - 3 .. y0 + 10
+//     in chunks holding solids, whose walls need densities two nodes out), so that the pull (Eq. 3)
+//     of any cell of the column and of its halo reads its 19 values at constant offsets from one
+//     shared-memory address; two stages on two mbarriers keep the next plane's 19 boxes in flight
+//     while the current one is used;
+//   * where the box crosses a periodic edge of the grid (TMA cannot wrap), the out-of-range columns
+//     and rows it needs are loaded by the threads and written over the box's zero fill after its
+//     wait (one plane ahead, from registers, in chunks without solids);
+//   * phase A of lead plane zl: rho (Eq. 4) and psi (Eq. 6) of the column and its halo into rings of
+//     planes; the column's own pulled values stay in registers;
+//   * chunks holding solids: bounce-back (Fig. 3) replaces a pulled value whose source is solid by
+//     the cell's own post-collision value in the opposite direction (plain loads, rare), and phase B
+//     gives the wall cells of plane zl - 1 their virtual density (Eqs. 16-17 with the limiter, or the
+//     constant one) from the densities of planes zl - 2 .. zl;
+//   * phase C collides plane zl - 1 (zl - 2 in chunks holding solids) once its psi neighbours are
+//     final: F_m (Eq. 5; plus Eq. 8 with the solid-fluid interaction scheme), u (Eq. 4), the MRT
+//     collision with the consistency source (Eqs. 2, 7), coalesced stores.
+// Ragged edge columns and small grids take the z-pair march on the column's two 32 x 4 halves.
+// ---------------------------------------------------------------------------------------------
+constexpr int TTX = 32, TTY = 8, TCH = ZCH;
+static_assert(TTX == ZTX && TTY == 2 * ZTY, "a TMA column is two z-pair columns");
+constexpr int TBX = TTX + 8;                  // box columns: x0 - 4 .. x0 + 35
+constexpr int TBY = TTY + 4, TSY = TTY + 6;   // box rows: y0 - 2 .. y0 + 9 (bulk), y0 - 3 .. y0 + 10 (solids)
+constexpr int TSLOT = 576;                    // floats per direction and stage (>= 14 x 40, 128-byte multiple)
+static_assert(TSLOT >= TSY * TBX && (TSLOT * 4) % 128 == 0, "every direction's box starts on a 128-byte boundary");
+constexpr int TPX = TTX + 2, TPY = TTY + 2;   // psi window: the column + 1-node ring (box cols 3..36)
+constexpr int TRX = TTX + 4, TRY = TTY + 4;   // density window (solid chunks): + 2-node ring
+constexpr int TYX = TTX + 6, TYY = TTY + 6;   // node-type window (solid chunks): + 3-node ring
+constexpr int TRING = 2 * TPX + 2 * (TPY - 2);                 // 84 cells of the 1-node ring
+constexpr int TRING2 = 2 * TRX + 2 * (TRY - 2);                // 92 cells of the 2-node ring
+constexpr int TTYPES = TYX * TYY;                              // 532 type cells per plane
+constexpr unsigned TBYTES_BULK = 19u * TBY * TBX * 4u, TBYTES_SOLID = 19u * TSY * TBX * 4u;
+
+struct ZTSmem {
+    float stage[2][19][TSLOT];
+    float psi[8][TPY * TPX];
+    float rho[4][TRY * TRX];
+    uint8_t type[8][TTYPES];
+    uint64_t bar[2];
+};
+constexpr size_t ZT_SMEM = sizeof(ZTSmem) > sizeof(ZPSmem<ZTX, ZTY>) ? sizeof(ZTSmem) : sizeof(ZPSmem<ZTX, ZTY>);
+
+// Polls of an mbarrier before a wait gives up (about one second at ~3.8 us per unsuccessful poll).
+constexpr unsigned ZT_POLL_LIMIT = 1u << 18;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_box3(void* dst, const void* tmap, int cx, int cy, int cz, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(cx), "r"(cy), "r"(cz), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// z component of D3Q19 velocity a for a run-time index (bit tables instead of an indexed array)
+__device__ __forceinline__ int ez_rt(int a) {
+    constexpr unsigned PLUS = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);
+    constexpr unsigned MINUS = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);
+    return int((PLUS >> a) & 1u) - int((MINUS >> a) & 1u);
+}
+
+// Out-of-range part of a box's used window (rows [rw0, rw1), columns [cw0, cw1) of a box whose
+// cell (0, 0) is the grid node (bx0, by0)): rows [r_lo, r_lo + nr) and columns [c_lo, c_lo + nc),
+// each on one side at most (the grid is wider than the window).
+struct OutBand {
+    int r_lo, nr, c_lo, nc, rin_lo, rin, cells, wc;
+    __device__ OutBand(int bx0, int by0, int nx, int ny, int rw0, int rw1, int cw0, int cw1) {
+        r_lo = rw0;
+        nr = 0;
+        if (by0 + rw0 < 0) {
+            nr = -(by0 + rw0);
+        } else if (by0 + rw1 > ny) {
+            nr = by0 + rw1 - ny;
+            r_lo = rw1 - nr;
+        }
+        c_lo = cw0;
+        nc = 0;
+        if (bx0 + cw0 < 0) {
+            nc = -(bx0 + cw0);
+        } else if (bx0 + cw1 > nx) {
+            nc = bx0 + cw1 - nx;
+            c_lo = cw1 - nc;
+        }
+        wc = cw1 - cw0;
+        rin = (rw1 - rw0) - nr;
+        rin_lo = r_lo == rw0 ? rw0 + nr : rw0;
+        cells = nr * wc + nc * rin;
+    }
+    // the k-th out-of-range cell (k < cells): whole rows first, then the columns of the other rows
+    __device__ void cell(int k, int cw0, int& r, int& c) const {
+        if (k < nr * wc) {
+            r = r_lo + k / wc;
+            c = cw0 + k % wc;
+        } else {
+            k -= nr * wc;
+            c = c_lo + k / rin;
+            r = rin_lo + k % rin;
+        }
+    }
+};
+
+// A chunk without solids within 3 nodes: no walls, no bounce-back; lag 1 between the lead plane
+// and the collided plane.
+__device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, float* __restrict__ fout,
+                                                const void* tmap, const Geo& g, const Phys<float>& ph,
+                                                const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
+                                                ZTSmem& S) {
+    using L = D3Q19;
+    constexpr int Q = 19;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const long long fs = g.fs;
+    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TTX + lx;
+    const int zlo = zb - 1, zhi = min(zb + TCH, nz);   // lead planes zlo .. zhi, collided planes zb .. zhi - 1
+    const int nlead = zhi - zlo + 1;
+
+    // out-of-range cells of the used window (rows 0 .. 11, columns 2 .. 37): at most
+    // 2 * 36 + 2 * 10 = 92 < 128, one per thread, prefetched one plane ahead
+    const OutBand ob_(x0 - 4, y0 - 2, nx, ny, 0, TBY, 2, TBX - 2);
+    const bool edge = ob_.cells > 0;
+    int fr = 0, fcl = 0, fsrc = 0;
+    const bool fixer = tid < ob_.cells;
+    if (fixer) {
+        ob_.cell(tid, 2, fr, fcl);
+        fsrc = wrap_full(y0 - 2 + fr, ny) * nx + wrap_full(x0 - 4 + fcl, nx);
+    }
+    float fix[Q];
+    auto issue = [&](int zl, int s) {   // thread 0: the 19 boxes of lead plane zl into stage s
+        fence_proxy_async();
+        mbar_expect_tx(&S.bar[s], TBYTES_BULK);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, y0 - 2, a * nz + wrap1(zl - L::ez(a), nz), &S.bar[s]);
+    };
+
+    if (tid == 0) {
+        issue(zlo, 0);
+        issue(zlo + 1, 1);
+    }
+    if (edge && fixer) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fix[a] = fin[a * fs + (long long)wrap1(zlo - L::ez(a), nz) * nxy + fsrc];
+    }
+
+    // own cells in box and psi-window coordinates
+    const int ob = (ly + 2) * TBX + lx + 4;
+    const int pc = (ly + 1) * TPX + lx + 1;
+    // this thread's halo-ring cell (threads 0 .. 83)
+    int rb = 0, rp = 0;
+    const bool ringer = tid < TRING;
+    if (ringer) {
+        int px, py, pz;
+        Shell<TPX, TPY, 1, 2>::cell(tid, px, py, pz);
+        rb = (py + 1) * TBX + px + 3;
+        rp = py * TPX + px;
+    }
+
+    V2 fprev[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fprev[a] = bc(0.0f);
+
+#pragma unroll 1
+    for (int i = 0; i < nlead; ++i) {
+        const int zl = zlo + i, s = i & 1;
+        if (!mbar_wait(&S.bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+        float* st = S.stage[s][0];
+        if (edge) {
+            if (fixer) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) st[a * TSLOT + fr * TBX + fcl] = fix[a];
+                fence_proxy_async();
+            }
+            if (fixer && zl + 1 <= zhi) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a)
+                    fix[a] = fin[a * fs + (long long)wrap1(zl + 1 - L::ez(a), nz) * nxy + fsrc];
+            }
+            __syncthreads();
+        }
+        // A. rho and psi of lead plane zl: the column (own values kept) and its halo ring
+        V2 fcur[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int off = a * TSLOT - L::ey(a) * TBX - L::ex(a);
+            fcur[a] = mk(st[ob + off], st[ob + 4 * TBX + off]);
+        }
+        {
+            V2 d = fcur[0];
+#pragma unroll
+            for (int a = 1; a < Q; ++a) d = d + fcur[a];
+            const V2 ps = psi2(bc(ph.rho_ref) + d, ph, true, true, err);
+            float* pp = S.psi[zl & 3];
+            pp[pc] = ps.v.x;
+            pp[pc + 4 * TPX] = ps.v.y;
+        }
+        if (ringer) {
+            float d = 0.0f;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) d += st[rb + a * TSLOT - L::ey(a) * TBX - L::ex(a)];
+            S.psi[zl & 3][rp] = psi_checked(ph.rho_ref + d, ph, err);
+        }
+        __syncthreads();
+        if (tid == 0 && zl + 2 <= zhi) issue(zl + 2, s);
+
+        // C. collide plane zc = zl - 1
+        const int zc = zl - 1;
+        if (zc >= zb) {
+            V2(&f)[Q] = fprev;
+            auto psi_at = [&](int dz, int off) {
+                const float* pp = S.psi[(zc + dz) & 3];
+                return mk(pp[pc + off], pp[pc + 4 * TPX + off]);
+            };
+            const V2 psi_c = psi_at(0, 0);
+            V2 sx = bc(0.0f), sy = bc(0.0f), sz = bc(0.0f);
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                if (L::opp(a) < a) continue;
+                const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                const int off = ex + ey * TPX;
+                const V2 wd = float(L::wf(a)) * (psi_at(ez, off) - psi_at(-ez, -off));
+                if (ex) sx = ex > 0 ? sx + wd : sx - wd;
+                if (ey) sy = ey > 0 ? sy + wd : sy - wd;
+                if (ez) sz = ez > 0 ? sz + wd : sz - wd;
+            }
+            // Eq. 5
+            const V2 gpsi = (-ph.G) * psi_c;
+            const V2 Fmx = gpsi * sx, Fmy = gpsi * sy, Fmz = gpsi * sz;
+            const V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy), Fz = Fmz + bc(ph.fz);
+            V2 drho = f[0];
+#pragma unroll
+            for (int a = 1; a < Q; ++a) drho = drho + f[a];
+            const V2 jx = ((f[1] - f[2]) + (f[7] - f[8])) + ((f[9] - f[10]) + (f[11] - f[12])) + (f[13] - f[14]);
+            const V2 jy = ((f[3] - f[4]) + (f[7] - f[8])) + ((f[10] - f[9]) + (f[15] - f[16])) + (f[17] - f[18]);
+            const V2 jz = ((f[5] - f[6]) + (f[11] - f[12])) + ((f[14] - f[13]) + (f[15] - f[16])) + (f[18] - f[17]);
+            const V2 rho = bc(ph.rho_ref) + drho;
+            if (!(rho.v.x > 0.0f) || !(rho.v.y > 0.0f)) atomicOr(err, ERR_RHO);
+            // Eq. 4: rho u = sum e f + F/2
+            const V2 inv = div2(bc(1.0f), rho);
+            const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv, uz = fma2(0.5f, Fz, jz) * inv;
+            const V2 X = div2(fma2(Fmx, Fmx, fma2(Fmy, Fmy, Fmz * Fmz)), psi_c * psi_c);
+            collide3p(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, kr);
+            float* o = fout + (long long)zc * nxy + (y0 + ly) * nx + x0 + lx;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                o[a * fs] = f[a].v.x;
+                o[a * fs + 4 * nx] = f[a].v.y;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fprev[a] = fcur[a];
+    }
+}
+
+// A chunk holding solids within 3 nodes: node types of planes zl - 3 .. zl + 2 in a ring, bounce-back
+// links, a 2-node density ring for the wall cells' Eq. 17, lag 2 between lead and collided plane.
+template <bool SF>
+__device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, float* __restrict__ fout,
+                                                 const void* tmap, const Geo& g, const Phys<float>& ph,
+                                                 const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
+                                                 ZTSmem& S) {
+    using L = D3Q19;
+    constexpr int Q = 19;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const long long fs = g.fs;
+    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TTX + lx;
+    const int ze = min(zb + TCH, nz);
+    const int zlo = zb - 2, zhi = ze + 1;   // lead planes; collided planes zb .. ze - 1
+    const int nlead = zhi - zlo + 1;
+    const int by0 = y0 - 3;                 // box row 0 is grid row y0 - 3; box column 0 is x0 - 4
+    auto wz = [&](int z) { return wrap1(wrap1(z, nz), nz); };
+    // node types of plane z (window columns 1 .. 38, rows 0 .. 13 of the box) into ring slot z & 7
+    auto type_src = [&](int z, int k) {
+        const int r = k / TYX, c = k % TYX;
+        return g.type[(long long)wz(z) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 3 + c, nx)];
+    };
+    // out-of-range cells of the used window (rows 0 .. 13, columns 1 .. 38), written after each
+    // wait from plain loads (chunks holding solids rarely touch the grid's edges)
+    const OutBand band(x0 - 4, by0, nx, ny, 0, TSY, 1, TBX - 1);
+    const bool edge = band.cells > 0;
+    auto issue = [&](int zl, int s) {
+        fence_proxy_async();
+        mbar_expect_tx(&S.bar[s], TBYTES_SOLID);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, by0, a * nz + wz(zl - L::ez(a)), &S.bar[s]);
+    };
+    if (tid == 0) {
+        issue(zlo, 0);
+        issue(zlo + 1, 1);
+    }
+    for (int z = zlo - 3; z <= zlo + 1; ++z)
+        for (int k = tid; k < TTYPES; k += TTX * ZTY) S.type[z & 7][k] = type_src(z, k);
+    __syncthreads();
+
+    // post-collision value f*_{opp(a)} of box cell (c, r) on plane z (bounce-back source)
+    auto bb_src = [&](int a, int z, int r, int c) {
+        return fin[L::opp(a) * fs + (long long)wz(z) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 4 + c, nx)];
+    };
+    // pull of a fluid cell (c, r) of plane zl with its type t: the 19 values, summed; own: keep them
+    auto pull = [&](const float* st, int zl, int r, int c, uint8_t t, float (&v)[Q]) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) v[a] = st[a * TSLOT + (r - L::ey(a)) * TBX + c - L::ex(a)];
+        if (!(t & T_BULK)) {
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                const uint8_t tu = S.type[(zl - L::ez(a)) & 7][(r - L::ey(a)) * TYX + c - L::ex(a) - 1];
+                if (tu & T_SOLID) v[a] = bb_src(a, zl, r, c);
+            }
+        }
+    };
+    const int pc = (ly + 1) * TPX + lx + 1;   // own cell in the psi window
+    const int rc = (ly + 2) * TRX + lx + 2;   // own cell in the density window
+    const int tcl = (ly + 3) * TYX + lx + 3;  // own cell in the type window
+    V2 f1[Q], f2[Q];                          // own values of planes zl - 1 and zl - 2
+#pragma unroll
+    for (int a = 0; a < Q; ++a) f1[a] = f2[a] = bc(0.0f);
+    uint8_t tnext[5];                         // types of plane zl + 2 (this thread's cells)
+
+#pragma unroll 1
+    for (int i = 0; i < nlead; ++i) {
+        const int zl = zlo + i, s = i & 1;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int k = tid + j * TTX * ZTY;
+            tnext[j] = k < TTYPES ? type_src(zl + 2, k) : uint8_t(0);
+        }
+        if (!mbar_wait(&S.bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+        float* st = S.stage[s][0];
+        if (edge) {
+            for (int k = tid; k < band.cells * Q; k += TTX * ZTY) {
+                const int a = k / band.cells;
+                int r, c;
+                band.cell(k - a * band.cells, 1, r, c);
+                st[a * TSLOT + r * TBX + c] =
+                    fin[a * fs + (long long)wz(zl - ez_rt(a)) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 4 + c, nx)];
+            }
+            fence_proxy_async();
+            __syncthreads();
+        }
+        // A. densities of the density window, psi of the psi window (fluid cells), own values kept
+        const uint8_t* ty = S.type[zl & 7];
+        float* rr = S.rho[zl & 3];
+        float* pp = S.psi[zl & 7];
+        V2 fcur[Q];
+        {
+            float v[Q];
+            const uint8_t t0 = ty[tcl], t1 = ty[tcl + 4 * TYX];
+            const bool fl0 = !(t0 & T_SOLID), fl1 = !(t1 & T_SOLID);
+            float d0 = 0.0f, d1 = 0.0f;
+            if (fl0) {
+                pull(st, zl, ly + 3, lx + 4, t0, v);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) d0 += v[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) v[a] = 0.0f;
+            }
+#pragma unroll
+            for (int a = 0; a < Q; ++a) fcur[a].v.x = v[a];
+            if (fl1) {
+                pull(st, zl, ly + 7, lx + 4, t1, v);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) d1 += v[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) v[a] = 0.0f;
+            }
+#pragma unroll
+            for (int a = 0; a < Q; ++a) fcur[a].v.y = v[a];
+            const V2 rho = mk(ph.rho_ref + d0, ph.rho_ref + d1);
+            const V2 ps = psi2(rho, ph, fl0, fl1, err);
+            rr[rc] = fl0 ? rho.v.x : 0.0f;
+            rr[rc + 4 * TRX] = fl1 ? rho.v.y : 0.0f;
+            pp[pc] = fl0 ? ps.v.x : 0.0f;
+            pp[pc + 4 * TPX] = fl1 ? ps.v.y : 0.0f;
+        }
+        // halo cells: the 1-node ring (density and psi) and the 2-node ring (density)
+        for (int k = tid; k < TRING + TRING2; k += TTX * ZTY) {
+            int px, py, pz, r, c;
+            if (k < TRING) {
+                Shell<TPX, TPY, 1, 2>::cell(k, px, py, pz);
+                r = py + 2;
+                c = px + 3;
+            } else {
+                Shell<TRX, TRY, 1, 2>::cell(k - TRING, px, py, pz);
+                r = py + 1;
+                c = px + 2;
+            }
+            const uint8_t t = ty[r * TYX + c - 1];
+            const bool fl = !(t & T_SOLID);
+            float rho = 0.0f;
+            if (fl) {
+                float v[Q];
+                pull(st, zl, r, c, t, v);
+                float d = 0.0f;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) d += v[a];
+                rho = ph.rho_ref + d;
+            }
+            rr[(r - 1) * TRX + c - 2] = rho;
+            if (k < TRING) pp[(r - 2) * TPX + c - 3] = fl ? psi_checked(rho, ph, err) : 0.0f;
+        }
+        __syncthreads();
+        if (tid == 0 && zl + 2 <= zhi) issue(zl + 2, s);
+
+        // B. wall cells of plane zw = zl - 1: virtual density and its psi (the solid-fluid interaction
+        // scheme keeps psi = 0 on solids); node types of plane zl + 2 into the ring
+        const int zw = zl - 1;
+        if (!SF && zw >= zb - 1) {
+            const uint8_t* tw = S.type[zw & 7];
+            for (int k = tid; k < TPX * TPY; k += TTX * ZTY) {
+                const int c = k % TPX + 3, r = k / TPX + 2;
+                if (!(tw[r * TYX + c - 1] & T_WALL)) continue;
+                float rw;
+                if (ph.wall_kind == 1) {
+                    rw = ph.wall_param;
+                } else {
+                    // Eq. 17: weighted mean of the fluid neighbours' densities
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                        if (!(S.type[(zw + ez) & 7][(r + ey) * TYX + c + ex - 1] & T_SOLID)) {
+                            num += float(L::wf(a)) * S.rho[(zw + ez) & 3][(r + ey - 1) * TRX + c + ex - 2];
+                            den += float(L::wf(a));
+                        }
+                    }
+                    const float rho_ave = cdiv(num, den);
+                    const float kap =
+                        g.kappa_w ? float(g.kappa_w[g.wall_id[(long long)wz(zw) * nxy + wrap1(by0 + r, ny) * nx +
+                                                              wrap1(x0 - 4 + c, nx)]])
+                                  : float(g.kappa);
+                    // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
+                    const float raw = (kap >= 0.0f) ? (1.0f + kap) * rho_ave : rho_ave + kap;
+                    rw = raw > ph.rho_l ? ph.rho_l : raw;
+                    rw = rw < ph.rho_g ? ph.rho_g : rw;
+                }
+                S.psi[zw & 7][k] = psi_checked(rw, ph, err);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int k = tid + j * TTX * ZTY;
+            if (k < TTYPES) S.type[(zl + 2) & 7][k] = tnext[j];
+        }
+        __syncthreads();
+
+        // C. collide plane zc = zl - 2
+        const int zc = zl - 2;
+        if (zc >= zb) {
+            const uint8_t* tc = S.type[zc & 7];
+            const bool fl0 = !(tc[tcl] & T_SOLID), fl1 = !(tc[tcl + 4 * TYX] & T_SOLID);
+            if (fl0 || fl1) {
+                V2(&f)[Q] = f2;
+                auto psi_at = [&](int dz, int off) {
+                    const float* q = S.psi[(zc + dz) & 7];
+                    return mk(q[pc + off], q[pc + 4 * TPX + off]);
+                };
+                const V2 psi_c = psi_at(0, 0);
+                V2 sx = bc(0.0f), sy = bc(0.0f), sz = bc(0.0f);
+#pragma unroll
+                for (int a = 1; a < Q; ++a) {
+                    if (L::opp(a) < a) continue;
+                    const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+                    const int off = ex + ey * TPX;
+                    const V2 wd = float(L::wf(a)) * (psi_at(ez, off) - psi_at(-ez, -off));
+                    if (ex) sx = ex > 0 ? sx + wd : sx - wd;
+                    if (ey) sy = ey > 0 ? sy + wd : sy - wd;
+                    if (ez) sz = ez > 0 ? sz + wd : sz - wd;
+                }
+                // Eq. 5
+                const V2 gpsi = (-ph.G) * psi_c;
+                const V2 Fmx = gpsi * sx, Fmy = gpsi * sy, Fmz = gpsi * sz;
+                V2 Fx = Fmx + bc(ph.fx), Fy = Fmy + bc(ph.fy), Fz = Fmz + bc(ph.fz);
+                V2 drho = f[0];
+#pragma unroll
+                for (int a = 1; a < Q; ++a) drho = drho + f[a];
+                const V2 jx = ((f[1] - f[2]) + (f[7] - f[8])) + ((f[9] - f[10]) + (f[11] - f[12])) + (f[13] - f[14]);
+                const V2 jy = ((f[3] - f[4]) + (f[7] - f[8])) + ((f[10] - f[9]) + (f[15] - f[16])) + (f[17] - f[18]);
+                const V2 jz = ((f[5] - f[6]) + (f[11] - f[12])) + ((f[14] - f[13]) + (f[15] - f[16])) + (f[18] - f[17]);
+                const V2 rho = bc(ph.rho_ref) + drho;
+                // Eq. 8 (solid-fluid interaction scheme): F_ads = -G_w rho sum_a w_a s(x + e_a) e_a
+                if constexpr (SF) {
+                    float ax0 = 0.0f, ay0 = 0.0f, az0 = 0.0f, ax1 = 0.0f, ay1 = 0.0f, az1 = 0.0f;
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a), off = ex + ey * TYX;
+                        const float w = float(L::wf(a));
+                        const uint8_t* tz = S.type[(zc + ez) & 7];
+                        if (tz[tcl + off] & T_SOLID) {
+                            if (ex) ax0 += w * float(ex);
+                            if (ey) ay0 += w * float(ey);
+                            if (ez) az0 += w * float(ez);
+                        }
+                        if (tz[tcl + 4 * TYX + off] & T_SOLID) {
+                            if (ex) ax1 += w * float(ex);
+                            if (ey) ay1 += w * float(ey);
+                            if (ez) az1 += w * float(ez);
+                        }
+                    }
+                    const V2 gr = (-ph.wall_param) * rho;
+                    Fx = (Fmx + gr * mk(ax0, ax1)) + bc(ph.fx);
+                    Fy = (Fmy + gr * mk(ay0, ay1)) + bc(ph.fy);
+                    Fz = (Fmz + gr * mk(az0, az1)) + bc(ph.fz);
+                }
+                if ((fl0 && !(rho.v.x > 0.0f)) || (fl1 && !(rho.v.y > 0.0f))) atomicOr(err, ERR_RHO);
+                // Eq. 4: rho u = sum e f + F/2
+                const V2 inv = div2(bc(1.0f), rho);
+                const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv, uz = fma2(0.5f, Fz, jz) * inv;
+                const V2 X = div2(fma2(Fmx, Fmx, fma2(Fmy, Fmy, Fmz * Fmz)), psi_c * psi_c);
+                collide3p(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, kr);
+                float* o = fout + (long long)zc * nxy + (y0 + ly) * nx + x0 + lx;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    if (fl0) o[a * fs] = f[a].v.x;
+                    if (fl1) o[a * fs + 4 * nx] = f[a].v.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            f2[a] = f1[a];
+            f1[a] = fcur[a];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TTX* ZTY, 2)
+    ztma_step(const float* __restrict__ fin, float* __restrict__ fout, const void* tmap, Geo g, Phys<float> ph,
+              Rates3P kr, unsigned* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int x0 = blockIdx.x * TTX, y0 = blockIdx.y * TTY, zb = blockIdx.z * TCH;
+    // chunk flags of the two 32 x 4 halves (the z-pair tiling)
+    const int ty4 = (g.ny + ZTY - 1) / ZTY, tx = gridDim.x;
+    const int h0 = (blockIdx.z * ty4 + 2 * blockIdx.y) * tx + blockIdx.x;
+    const bool has1 = y0 + ZTY < g.ny;
+    const bool s0 = g.tile_solid ? g.tile_solid[h0] != 0 : true;
+    const bool s1 = has1 && (g.tile_solid ? g.tile_solid[h0 + tx] != 0 : true);
+    const bool boxed = tmap != nullptr && x0 + TTX <= g.nx && y0 + TTY <= g.ny && g.nx >= 64 && g.ny >= 16 &&
+                       g.nz >= 4;
+    const bool sf = ph.wall_kind == 2;
+    if (boxed) {
+        ZTSmem& S = *reinterpret_cast<ZTSmem*>(smem_raw);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            mbar_init(&S.bar[0]);
+            mbar_init(&S.bar[1]);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        // tmap: the buffer's two maps (box heights TBY and TSY)
+        if (!s0 && !s1)
+            ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S);
+        else if (sf)
+            ztma_chunk_solid<true>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S);
+        else
+            ztma_chunk_solid<false>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S);
+        return;
+    }
+    ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
+    for (int h = 0; h < (has1 ? 2 : 1); ++h) {
+        const bool solid = h ? s1 : s0;
+        if (h) __syncthreads();   // the first half is done with shared memory
+        if (solid && sf)
+            zpair_chunk<true, true>(fin, fout, g, ph, kr, x0, y0 + h * ZTY, zb, err, sm);
+        else if (solid)
+            zpair_chunk<true>(fin, fout, g, ph, kr, x0, y0 + h * ZTY, zb, err, sm);
+        else
+            zpair_chunk<false>(fin, fout, g, ph, kr, x0, y0 + h * ZTY, zb, err, sm);
+    }
 }
 
 }  // namespace
@@ -493,6 +1070,29 @@ cudaError_t launch_zpair_step(const void* fin, void* fout, const Geo& g, const D
     zpair_step<<<grid, dim3(ZTX, ZTY, 1), bytes, s>>>(static_cast<const float*>(fin), static_cast<float*>(fout), g,
                                                       make_phys<float>(p), make_rates3p(p), p.err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, const Geo& g, const DevParams& p,
+                             cudaStream_t s) {
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(ztma_step, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZT_SMEM));
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    dim3 grid((p.nx + TTX - 1) / TTX, (p.ny + TTY - 1) / TTY, (p.nz + TCH - 1) / TCH);
+    ztma_step<<<grid, dim3(TTX, ZTY, 1), ZT_SMEM, s>>>(static_cast<const float*>(fin), static_cast<float*>(fout), tmap,
+                                                      g, make_phys<float>(p), make_rates3p(p), p.err);
+    return cudaGetLastError();
+}
+
+void ztma_box_dims(int* bx, int* by_bulk, int* by_solid) {
+    *bx = TBX;
+    *by_bulk = TBY;
+    *by_solid = TSY;
 }
 
 }  // namespace lbmwet

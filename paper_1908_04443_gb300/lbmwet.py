@@ -270,7 +270,7 @@ def lbm_kernel_launches(h) -> int:
     return int(_lib.lbm_kernel_launches(h))
 
 
-KERNEL_NAMES = {0: "auto", 1: "tile", 2: "ymarch", 3: "pair"}
+KERNEL_NAMES = {0: "auto", 1: "tile", 2: "ymarch", 3: "pair", 4: "ztma"}
 
 
 def lbm_step_kernel_used(h) -> str:
@@ -376,7 +376,7 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
                 theta_a=90.0) -> lbm_config:
     """Build an lbm_config.  `shape` is the numpy shape (ny, nx) or (nz, ny, nx).  `body` is
     ("ball", center, radius) or ("plane", wall_y) or None.  `step_kernel` is "auto", "tile",
-    "ymarch" or "pair" (D2Q9 work decomposition, see lbm_step_kernel in the header).  `wall` is
+    "ymarch", "pair" or "ztma" (work decomposition, see lbm_step_kernel in the header).  `wall` is
     "IVD" (parameter kappa), "VD" (rho_w_const), "SF" (Gw) or "GF" (theta_a, degrees; D2Q9)."""
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
@@ -398,7 +398,7 @@ def make_config(lattice: str, precision: str, shape: Sequence[int], eos: lbm_eos
     cfg.theta_a = theta_a
     cfg.kappa = kappa
     cfg.rho_w_const = rho_w_const
-    cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2, "pair": 3}[step_kernel]
+    cfg.step_kernel = {"auto": 0, "tile": 1, "ymarch": 2, "pair": 3, "ztma": 4}[step_kernel]
     cfg.body_kind = LBM_BODY_NONE
     if body is not None:
         if body[0] == "ball":

@@ -40,12 +40,19 @@ def test_2d_step_kernels_stay_in_bounds(precision, kernel, grid, wall):
         _untouched(sim.h)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision,kernel", [("fp64", "auto"), ("fp32", "tile"), ("fp32", "pair"),
+                                               ("fp32", "ztma")])
 @pytest.mark.parametrize("wall", ["IVD", "SF"])
-def test_3d_step_kernels_stay_in_bounds(precision, wall):
-    # (nz, ny, nx) = (22, 20, 26): ragged in every direction of the z-march and z-pair tiles
-    case = drop_on_cylinder((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0, lattice="D3Q19",
-                            kappa=0.1, wall=wall, Gw=-0.2 if wall == "SF" else 0.0)
+@pytest.mark.parametrize("grid", [0, 1])
+def test_3d_step_kernels_stay_in_bounds(precision, kernel, wall, grid):
+    # (nz, ny, nx) = (22, 20, 26): ragged in every direction of the z-march and z-pair tiles;
+    # (37, 21, 100): TMA-staged columns on the x and y edges next to ragged ones, a partial chunk
+    g3 = [((22, 20, 26), (13.0, 10.0, 8.0), 4.5, (13.0, 10.0, 16.0), 6.0),
+          ((37, 21, 100), (70.0, 10.0, 30.0), 3.5, (70.0, 10.0, 20.0), 5.0)][grid]
+    case = drop_on_cylinder(*g3, lattice="D3Q19", kappa=0.1, wall=wall, Gw=-0.2 if wall == "SF" else 0.0,
+                            step_kernel=kernel)
+    if precision == "fp32":
+        case.rho_ref = case.bounds()[0]
     with case.gpu(precision) as sim:
         sim.step(19)
         sim.observables(fields=True)
