@@ -499,8 +499,10 @@ constexpr int TTX = 32, TTY = 8, TCH = ZCH;
 static_assert(TTX == ZTX && TTY == 2 * ZTY, "a TMA column is two z-pair columns");
 constexpr int TBX = TTX + 8;                  // box columns: x0 - 4 .. x0 + 35
 constexpr int TBY = TTY + 4, TSY = TTY + 6;   // box rows: y0 - 2 .. y0 + 9 (bulk), y0 - 3 .. y0 + 10 (solids)
-constexpr int TSLOT = 576;                    // floats per direction and stage (>= 14 x 40, 128-byte multiple)
-static_assert(TSLOT >= TSY * TBX && (TSLOT * 4) % 128 == 0, "every direction's box starts on a 128-byte boundary");
+constexpr int TBSLOT = TBY * TBX;             // floats per direction and stage, chunks without solids (480)
+constexpr int TSSLOT = 576;                   // floats per direction, chunks holding solids (>= 14 x 40)
+static_assert((TBSLOT * 4) % 128 == 0 && TSSLOT >= TSY * TBX && (TSSLOT * 4) % 128 == 0,
+              "every direction's box starts on a 128-byte boundary");
 constexpr int TPX = TTX + 2, TPY = TTY + 2;   // psi window: the column + 1-node ring (box cols 3..36)
 constexpr int TRX = TTX + 4, TRY = TTY + 4;   // density window (solid chunks): + 2-node ring
 constexpr int TYX = TTX + 6, TYY = TTY + 6;   // node-type window (solid chunks): + 3-node ring
@@ -509,11 +511,26 @@ constexpr int TRING2 = 2 * TRX + 2 * (TRY - 2);                // 92 cells of th
 constexpr int TTYPES = TYX * TYY;                              // 532 type cells per plane
 constexpr unsigned TBYTES_BULK = 19u * TBY * TBX * 4u, TBYTES_SOLID = 19u * TSY * TBX * 4u;
 
-struct ZTSmem {
-    float stage[2][19][TSLOT];
+// Shared memory of the two kinds of chunk, overlaid.  Chunks without solids keep two planes of
+// boxes in flight; chunks holding solids (one or two tenths of a domain) stage one plane at a time
+// (its load overlaps their wall and collision phases) so that the CTA stays near 77 KB: two CTAs
+// per SM then leave the L1 about 90 KB, which the loads of the periodic-edge patches need (with
+// 107 KB CTAs the 256^3 step ran at 0.65 of the HBM roofline instead of 0.79).
+struct ZTBulk {
+    float stage[2][19][TBSLOT];
+    float psi[4][TPY * TPX];
+};
+struct ZTSolid {
+    float stage[19][TSSLOT];
     float psi[8][TPY * TPX];
     float rho[4][TRY * TRX];
     uint8_t type[8][TTYPES];
+};
+struct ZTSmem {
+    union {
+        ZTBulk b;
+        ZTSolid s;
+    };
     uint64_t bar[2];
 };
 constexpr size_t ZT_SMEM = sizeof(ZTSmem) > sizeof(ZPSmem<ZTX, ZTY>) ? sizeof(ZTSmem) : sizeof(ZPSmem<ZTX, ZTY>);
@@ -585,7 +602,7 @@ struct OutBand {
 __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, float* __restrict__ fout,
                                                 const void* tmap, const Geo& g, const Phys<float>& ph,
                                                 const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
-                                                ZTSmem& S) {
+                                                ZTBulk& S, uint64_t* bar) {
     using L = D3Q19;
     constexpr int Q = 19;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
@@ -607,9 +624,9 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
     float fix[Q];
     auto issue = [&](int zl, int s) {   // thread 0: the 19 boxes of lead plane zl into stage s
         fence_proxy_async();
-        mbar_expect_tx(&S.bar[s], TBYTES_BULK);
+        mbar_expect_tx(&bar[s], TBYTES_BULK);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, y0 - 2, a * nz + wrap1(zl - L::ez(a), nz), &S.bar[s]);
+        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, y0 - 2, a * nz + wrap1(zl - L::ez(a), nz), &bar[s]);
     };
 
     if (tid == 0) {
@@ -641,12 +658,12 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
 #pragma unroll 1
     for (int i = 0; i < nlead; ++i) {
         const int zl = zlo + i, s = i & 1;
-        if (!mbar_wait(&S.bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+        if (!mbar_wait(&bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
         float* st = S.stage[s][0];
         if (edge) {
             if (fixer) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) st[a * TSLOT + fr * TBX + fcl] = fix[a];
+                for (int a = 0; a < Q; ++a) st[a * TBSLOT + fr * TBX + fcl] = fix[a];
                 fence_proxy_async();
             }
             if (fixer && zl + 1 <= zhi) {
@@ -660,7 +677,7 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
         V2 fcur[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const int off = a * TSLOT - L::ey(a) * TBX - L::ex(a);
+            const int off = a * TBSLOT - L::ey(a) * TBX - L::ex(a);
             fcur[a] = mk(st[ob + off], st[ob + 4 * TBX + off]);
         }
         {
@@ -675,7 +692,7 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
         if (ringer) {
             float d = 0.0f;
 #pragma unroll
-            for (int a = 0; a < Q; ++a) d += st[rb + a * TSLOT - L::ey(a) * TBX - L::ex(a)];
+            for (int a = 0; a < Q; ++a) d += st[rb + a * TBSLOT - L::ey(a) * TBX - L::ex(a)];
             S.psi[zl & 3][rp] = psi_checked(ph.rho_ref + d, ph, err);
         }
         __syncthreads();
@@ -736,7 +753,7 @@ template <bool SF>
 __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, float* __restrict__ fout,
                                                  const void* tmap, const Geo& g, const Phys<float>& ph,
                                                  const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
-                                                 ZTSmem& S) {
+                                                 ZTSolid& S, uint64_t* bar) {
     using L = D3Q19;
     constexpr int Q = 19;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
@@ -756,16 +773,13 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
     // wait from plain loads (chunks holding solids rarely touch the grid's edges)
     const OutBand band(x0 - 4, by0, nx, ny, 0, TSY, 1, TBX - 1);
     const bool edge = band.cells > 0;
-    auto issue = [&](int zl, int s) {
+    auto issue = [&](int zl) {   // thread 0: the 19 boxes of lead plane zl into the (single) stage
         fence_proxy_async();
-        mbar_expect_tx(&S.bar[s], TBYTES_SOLID);
+        mbar_expect_tx(&bar[0], TBYTES_SOLID);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, by0, a * nz + wz(zl - L::ez(a)), &S.bar[s]);
+        for (int a = 0; a < Q; ++a) tma_box3(S.stage[a], tmap, x0 - 4, by0, a * nz + wz(zl - L::ez(a)), &bar[0]);
     };
-    if (tid == 0) {
-        issue(zlo, 0);
-        issue(zlo + 1, 1);
-    }
+    if (tid == 0) issue(zlo);
     for (int z = zlo - 3; z <= zlo + 1; ++z)
         for (int k = tid; k < TTYPES; k += TTX * ZTY) S.type[z & 7][k] = type_src(z, k);
     __syncthreads();
@@ -777,7 +791,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
     // pull of a fluid cell (c, r) of plane zl with its type t: the 19 values, summed; own: keep them
     auto pull = [&](const float* st, int zl, int r, int c, uint8_t t, float (&v)[Q]) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) v[a] = st[a * TSLOT + (r - L::ey(a)) * TBX + c - L::ex(a)];
+        for (int a = 0; a < Q; ++a) v[a] = st[a * TSSLOT + (r - L::ey(a)) * TBX + c - L::ex(a)];
         if (!(t & T_BULK)) {
 #pragma unroll
             for (int a = 1; a < Q; ++a) {
@@ -796,20 +810,20 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 
 #pragma unroll 1
     for (int i = 0; i < nlead; ++i) {
-        const int zl = zlo + i, s = i & 1;
+        const int zl = zlo + i;
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             const int k = tid + j * TTX * ZTY;
             tnext[j] = k < TTYPES ? type_src(zl + 2, k) : uint8_t(0);
         }
-        if (!mbar_wait(&S.bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
-        float* st = S.stage[s][0];
+        if (!mbar_wait(&bar[0], unsigned(i) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+        float* st = S.stage[0];
         if (edge) {
             for (int k = tid; k < band.cells * Q; k += TTX * ZTY) {
                 const int a = k / band.cells;
                 int r, c;
                 band.cell(k - a * band.cells, 1, r, c);
-                st[a * TSLOT + r * TBX + c] =
+                st[a * TSSLOT + r * TBX + c] =
                     fin[a * fs + (long long)wz(zl - ez_rt(a)) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 4 + c, nx)];
             }
             fence_proxy_async();
@@ -879,7 +893,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             if (k < TRING) pp[(r - 2) * TPX + c - 3] = fl ? psi_checked(rho, ph, err) : 0.0f;
         }
         __syncthreads();
-        if (tid == 0 && zl + 2 <= zhi) issue(zl + 2, s);
+        if (tid == 0 && zl + 1 <= zhi) issue(zl + 1);   // loads while phases B and C run
 
         // B. wall cells of plane zw = zl - 1: virtual density and its psi (the solid-fluid interaction
         // scheme keeps psi = 0 on solids); node types of plane zl + 2 into the ring
@@ -1027,11 +1041,11 @@ __global__ void __launch_bounds__(TTX* ZTY, 2)
         __syncthreads();
         // tmap: the buffer's two maps (box heights TBY and TSY)
         if (!s0 && !s1)
-            ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S);
+            ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.b, S.bar);
         else if (sf)
-            ztma_chunk_solid<true>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S);
+            ztma_chunk_solid<true>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
         else
-            ztma_chunk_solid<false>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S);
+            ztma_chunk_solid<false>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
         return;
     }
     ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
