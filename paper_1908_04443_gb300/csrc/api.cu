@@ -145,13 +145,11 @@ bool encode_pair_map(CUtensorMap* m, void* f, int nx, int ny, int fp, long long 
 }
 
 // TMA tensor map of one FP32 D3Q19 distribution buffer f[a][z][y][x] seen as a 3D tensor
-// (x, y, a * nz + z): a box of the TMA-staged z-march (one direction on one plane, `by` rows).
+// (x, y, a * nz + z): the box of the TMA-staged z-march (one direction on one plane, bx x by).
 // False where TMA cannot address the buffer (rows not a multiple of 16 bytes).
-bool encode_z_map(CUtensorMap* m, void* f, int nx, int ny, int nz, int by) {
+bool encode_z_map(CUtensorMap* m, void* f, int nx, int ny, int nz, int bx, int by) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc || nx % 4 != 0) return false;
-    int bx, by_bulk, by_solid;
-    ztma_box_dims(&bx, &by_bulk, &by_solid);
     const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(19) * cuuint64_t(nz)};
     const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * cuuint64_t(ny) * 4};
     const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
@@ -634,13 +632,10 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     p.ztmap = nullptr;
     p.zf0 = h->f[0];
     if (h->D == 3 && c.precision == LBM_FP32_DEV && p.step3 == 0) {
-        // per buffer: the box of chunks without solids (rows y0 - 2 .. y0 + 9), then the one of chunks
-        // holding solids (rows y0 - 3 .. y0 + 10)
-        int bx, by_bulk, by_solid;
-        ztma_box_dims(&bx, &by_bulk, &by_solid);
-        CUtensorMap maps[4];
-        if (encode_z_map(&maps[0], h->f[0], nx, ny, nz, by_bulk) && encode_z_map(&maps[1], h->f[0], nx, ny, nz, by_solid) &&
-            encode_z_map(&maps[2], h->f[1], nx, ny, nz, by_bulk) && encode_z_map(&maps[3], h->f[1], nx, ny, nz, by_solid)) {
+        int bx, by;
+        ztma_box_dims(&bx, &by);
+        CUtensorMap maps[2];
+        if (encode_z_map(&maps[0], h->f[0], nx, ny, nz, bx, by) && encode_z_map(&maps[1], h->f[1], nx, ny, nz, bx, by)) {
             CKI(cudaMalloc(&h->d_zmaps, sizeof(maps)), "cudaMalloc tensor maps");
             CKI(cudaMemcpyAsync(h->d_zmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, h->stream), "copy tensor maps");
             CKI(cudaStreamSynchronize(h->stream), "sync");

@@ -33,7 +33,7 @@ struct DevParams {
     const uint8_t* pair_solid;   // the same per tile of the FP32 pair kernel; null: FP32 steps use the tile kernel
     // D3Q19 FP32 step kernel: 0 the TMA-staged z-march, 1 the z-pair march, 2 the scalar z-march
     int step3;
-    const void* ztmap;           // TMA tensor maps of the two 3D FP32 distribution buffers (device, 2 x 2 x 128 B)
+    const void* ztmap;           // TMA tensor maps of the two 3D FP32 distribution buffers (device, 2 x 128 B)
     const void* zf0;             // the buffer the first map describes
     unsigned* err;               // sticky device error flags
 };
@@ -125,11 +125,11 @@ void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz);
 // g.tile_solid per FP32 z-march chunk.
 cudaError_t launch_zpair_step(const void* fin, void* fout, const Geo& g, const DevParams& p, cudaStream_t s);
 // D3Q19 FP32 step, TMA-staged z-march over 32 x 8 columns of 32-plane chunks (ragged columns and
-// small grids take the z-pair march); tmap: the two tensor maps of fin (dimensions x, y, 19 nz;
-// boxes bx x by_bulk x 1 and bx x by_solid x 1, see ztma_box_dims), 128 bytes each.
+// small grids take the z-pair march); tmap: the tensor map of fin (dimensions x, y, 19 nz; box
+// bx x by x 1, see ztma_box_dims), 128 bytes.
 cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, const Geo& g, const DevParams& p,
                              cudaStream_t s);
-void ztma_box_dims(int* bx, int* by_bulk, int* by_solid);
+void ztma_box_dims(int* bx, int* by);
 // Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);
 int batched_ctas_per_sm(int lat, int prec);

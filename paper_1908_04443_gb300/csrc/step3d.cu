@@ -322,7 +322,7 @@ void zmarch_tile_shape(int prec, int* tx, int* ty, int* tz) {
 cudaError_t launch_step3d(int prec, int mode, const void* fin, void* fout, const Geo& g, const DevParams& p,
                           double* rho, double* u, cudaStream_t s) {
     if (prec == PREC_FP32 && mode == 0 && p.step3 == 0 && p.ztmap)
-        return launch_ztma_step(fin, fout, static_cast<const char*>(p.ztmap) + (fin == p.zf0 ? 0 : 256), g, p, s);
+        return launch_ztma_step(fin, fout, static_cast<const char*>(p.ztmap) + (fin == p.zf0 ? 0 : 128), g, p, s);
     if (prec == PREC_FP32 && mode == 0 && p.step3 != 2) return launch_zpair_step(fin, fout, g, p, s);
     if (prec == PREC_FP64)
         return mode == 0 ? launch_z<double, 0>(fin, fout, g, p, rho, u, s) : launch_z<double, 1>(fin, fout, g, p, rho, u, s);

@@ -14,6 +14,7 @@
 // Rings indexed by the absolute plane: densities 4 planes, psi 8, node types 8, wall queues 4 (and,
 // with LBMWET_ZP_REPULL = 0, the own distributions, 4 planes).  Results equal the scalar z-march's up to FP32 rounding (operations regrouped).
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.h"
 #include "lattice.cuh"
@@ -498,31 +499,36 @@ __global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
 constexpr int TTX = 32, TTY = 8, TCH = ZCH;
 static_assert(TTX == ZTX && TTY == 2 * ZTY, "a TMA column is two z-pair columns");
 constexpr int TBX = TTX + 8;                  // box columns: x0 - 4 .. x0 + 35
-constexpr int TBY = TTY + 4, TSY = TTY + 6;   // box rows: y0 - 2 .. y0 + 9 (bulk), y0 - 3 .. y0 + 10 (solids)
+constexpr int TBY = TTY + 4;                  // box rows: y0 - 2 .. y0 + 9
 constexpr int TBSLOT = TBY * TBX;             // floats per direction and stage, chunks without solids (480)
-constexpr int TSSLOT = 576;                   // floats per direction, chunks holding solids (>= 14 x 40)
-static_assert((TBSLOT * 4) % 128 == 0 && TSSLOT >= TSY * TBX && (TSSLOT * 4) % 128 == 0,
-              "every direction's box starts on a 128-byte boundary");
+static_assert((TBSLOT * 4) % 128 == 0, "every direction's box starts on a 128-byte boundary");
 constexpr int TPX = TTX + 2, TPY = TTY + 2;   // psi window: the column + 1-node ring (box cols 3..36)
 constexpr int TRX = TTX + 4, TRY = TTY + 4;   // density window (solid chunks): + 2-node ring
 constexpr int TYX = TTX + 6, TYY = TTY + 6;   // node-type window (solid chunks): + 3-node ring
 constexpr int TRING = 2 * TPX + 2 * (TPY - 2);                 // 84 cells of the 1-node ring
 constexpr int TRING2 = 2 * TRX + 2 * (TRY - 2);                // 92 cells of the 2-node ring
 constexpr int TTYPES = TYX * TYY;                              // 532 type cells per plane
-constexpr unsigned TBYTES_BULK = 19u * TBY * TBX * 4u, TBYTES_SOLID = 19u * TSY * TBX * 4u;
+constexpr unsigned TBYTES_BULK = 19u * TBY * TBX * 4u;
+// the directions with ey = +1 (3, 7, 10, 15, 17) and ey = -1 (4, 8, 9, 16, 18), five bits each
+constexpr unsigned XROW_UP = 3u | 7u << 5 | 10u << 10 | 15u << 15 | 17u << 20;
+constexpr unsigned XROW_DN = 4u | 8u << 5 | 9u << 10 | 16u << 15 | 18u << 20;
+__host__ __device__ constexpr int xrow_slot(int a) {   // position of a among its five directions
+    return a == 3 || a == 4 ? 0 : a == 7 || a == 8 ? 1 : a == 10 || a == 9 ? 2 : a == 15 || a == 16 ? 3 : 4;
+}
 
-// Shared memory of the two kinds of chunk, overlaid.  Chunks without solids keep two planes of
-// boxes in flight; chunks holding solids (one or two tenths of a domain) stage one plane at a time
-// (its load overlaps their wall and collision phases) so that the CTA stays near 77 KB: two CTAs
-// per SM then leave the L1 about 90 KB, which the loads of the periodic-edge patches need (with
-// 107 KB CTAs the 256^3 step ran at 0.65 of the HBM roofline instead of 0.79).
+// Shared memory of the two kinds of chunk, overlaid: both keep two planes of boxes in flight (the
+// same 12-row boxes); chunks holding solids add node types, a density ring and the two rows beyond
+// the box that their 2-node density ring pulls from.  The CTA stays under 97 KB, so that two CTAs
+// per SM leave the L1 at least 60 KB, which the loads of the periodic-edge patches need (with 107 KB
+// CTAs the 256^3 step ran at 0.65 of the HBM roofline instead of 0.78).
 struct ZTBulk {
     float stage[2][19][TBSLOT];
     float psi[4][TPY * TPX];
 };
 struct ZTSolid {
-    float stage[19][TSSLOT];
-    float psi[8][TPY * TPX];
+    float stage[2][19][TBSLOT];
+    float xrow[2][2][5][TBX];   // by plane parity: row y0 - 3 (directions with ey = 1), row y0 + 10 (ey = -1)
+    float psi[5][TPY * TPX];
     float rho[4][TRY * TRX];
     uint8_t type[8][TTYPES];
 };
@@ -749,57 +755,83 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
 
 // A chunk holding solids within 3 nodes: node types of planes zl - 3 .. zl + 2 in a ring, bounce-back
 // links, a 2-node density ring for the wall cells' Eq. 17, lag 2 between lead and collided plane.
+// Coordinates (rb, c) are those of the box: row rb is grid row y0 - 2 + rb, column c is x0 - 4 + c.
 template <bool SF>
 __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, float* __restrict__ fout,
                                                  const void* tmap, const Geo& g, const Phys<float>& ph,
                                                  const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
                                                  ZTSolid& S, uint64_t* bar) {
     using L = D3Q19;
-    constexpr int Q = 19;
+    constexpr int Q = 19, NT = TTX * ZTY;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const long long fs = g.fs;
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TTX + lx;
     const int ze = min(zb + TCH, nz);
     const int zlo = zb - 2, zhi = ze + 1;   // lead planes; collided planes zb .. ze - 1
     const int nlead = zhi - zlo + 1;
-    const int by0 = y0 - 3;                 // box row 0 is grid row y0 - 3; box column 0 is x0 - 4
     auto wz = [&](int z) { return wrap1(wrap1(z, nz), nz); };
-    // node types of plane z (window columns 1 .. 38, rows 0 .. 13 of the box) into ring slot z & 7
+    auto ps5 = [](int z) { return (z + 10) % 5; };   // psi ring slot (z >= -10)
+    // node types of plane z (rows -1 .. 12, columns 1 .. 38 of the box) into ring slot z & 7
     auto type_src = [&](int z, int k) {
-        const int r = k / TYX, c = k % TYX;
-        return g.type[(long long)wz(z) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 3 + c, nx)];
+        const int tr = k / TYX, tc = k % TYX;
+        return g.type[(long long)wz(z) * nxy + wrap1(y0 - 3 + tr, ny) * nx + wrap1(x0 - 3 + tc, nx)];
     };
-    // out-of-range cells of the used window (rows 0 .. 13, columns 1 .. 38), written after each
+    // the rows beyond the box that the 2-node ring pulls from (box row -1 for ey = 1, row 12 for
+    // ey = -1), columns 1 .. 38: item k < 380 of plane z
+    auto xrow_src = [&](int z, int k) {
+        const int row = k / 190, rem = k - row * 190, d = rem / 38, col = 1 + rem % 38;
+        const int a = int(((row ? XROW_DN : XROW_UP) >> (5 * d)) & 31u);
+        return fin[a * fs + (long long)wz(z - ez_rt(a)) * nxy + wrap1(row ? y0 + 10 : y0 - 3, ny) * nx +
+                   wrap1(x0 - 4 + col, nx)];
+    };
+    auto xrow_dst = [&](int z, int k) -> float& {
+        const int row = k / 190, rem = k - row * 190, d = rem / 38, col = 1 + rem % 38;
+        return S.xrow[z & 1][row][d][col];
+    };
+    // out-of-range cells of the used window (rows 0 .. 11, columns 1 .. 38), written after each
     // wait from plain loads (chunks holding solids rarely touch the grid's edges)
-    const OutBand band(x0 - 4, by0, nx, ny, 0, TSY, 1, TBX - 1);
+    const OutBand band(x0 - 4, y0 - 2, nx, ny, 0, TBY, 1, TBX - 1);
     const bool edge = band.cells > 0;
-    auto issue = [&](int zl) {   // thread 0: the 19 boxes of lead plane zl into the (single) stage
+    auto issue = [&](int zl, int s) {   // thread 0: the 19 boxes of lead plane zl into stage s
         fence_proxy_async();
-        mbar_expect_tx(&bar[0], TBYTES_SOLID);
+        mbar_expect_tx(&bar[s], TBYTES_BULK);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) tma_box3(S.stage[a], tmap, x0 - 4, by0, a * nz + wz(zl - L::ez(a)), &bar[0]);
+        for (int a = 0; a < Q; ++a) tma_box3(S.stage[s][a], tmap, x0 - 4, y0 - 2, a * nz + wz(zl - L::ez(a)), &bar[s]);
     };
-    if (tid == 0) issue(zlo);
+    if (tid == 0) {
+        issue(zlo, 0);
+        issue(zlo + 1, 1);
+    }
     for (int z = zlo - 3; z <= zlo + 1; ++z)
-        for (int k = tid; k < TTYPES; k += TTX * ZTY) S.type[z & 7][k] = type_src(z, k);
+        for (int k = tid; k < TTYPES; k += NT) S.type[z & 7][k] = type_src(z, k);
+    for (int k = tid; k < 380; k += NT) xrow_dst(zlo, k) = xrow_src(zlo, k);
     __syncthreads();
 
-    // post-collision value f*_{opp(a)} of box cell (c, r) on plane z (bounce-back source)
-    auto bb_src = [&](int a, int z, int r, int c) {
-        return fin[L::opp(a) * fs + (long long)wz(z) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 4 + c, nx)];
+    // post-collision value f*_{opp(a)} of box cell (rb, c) on plane z (bounce-back source)
+    auto bb_src = [&](int a, int z, int rb, int c) {
+        return fin[L::opp(a) * fs + (long long)wz(z) * nxy + wrap1(y0 - 2 + rb, ny) * nx + wrap1(x0 - 4 + c, nx)];
     };
-    // pull of a fluid cell (c, r) of plane zl with its type t: the 19 values, summed; own: keep them
-    auto pull = [&](const float* st, int zl, int r, int c, uint8_t t, float (&v)[Q]) {
+    // pull of a fluid cell (rb, c) of plane zl with its type t; RING2: the cell may lie on box row 0
+    // or 11, whose pulls reach the rows beyond the box
+    auto pull = [&](auto ring2, const float* st, int zl, int rb, int c, uint8_t t, float (&v)[Q]) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) v[a] = st[a * TSSLOT + (r - L::ey(a)) * TBX + c - L::ex(a)];
+        for (int a = 0; a < Q; ++a) {
+            const int ey = L::ey(a), sr = rb - ey;
+            if (decltype(ring2)::value && ey != 0 && (sr < 0 || sr >= TBY))
+                v[a] = S.xrow[zl & 1][sr < 0 ? 0 : 1][xrow_slot(a)][c - L::ex(a)];
+            else
+                v[a] = st[a * TBSLOT + sr * TBX + c - L::ex(a)];
+        }
         if (!(t & T_BULK)) {
 #pragma unroll
             for (int a = 1; a < Q; ++a) {
-                const uint8_t tu = S.type[(zl - L::ez(a)) & 7][(r - L::ey(a)) * TYX + c - L::ex(a) - 1];
-                if (tu & T_SOLID) v[a] = bb_src(a, zl, r, c);
+                const uint8_t tu = S.type[(zl - L::ez(a)) & 7][(rb - L::ey(a) + 1) * TYX + c - L::ex(a) - 1];
+                if (tu & T_SOLID) v[a] = bb_src(a, zl, rb, c);
             }
         }
     };
+    using NoRing2 = std::integral_constant<bool, false>;
+    using Ring2 = std::integral_constant<bool, true>;
     const int pc = (ly + 1) * TPX + lx + 1;   // own cell in the psi window
     const int rc = (ly + 2) * TRX + lx + 2;   // own cell in the density window
     const int tcl = (ly + 3) * TYX + lx + 3;  // own cell in the type window
@@ -807,24 +839,30 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 #pragma unroll
     for (int a = 0; a < Q; ++a) f1[a] = f2[a] = bc(0.0f);
     uint8_t tnext[5];                         // types of plane zl + 2 (this thread's cells)
+    float xnext[3];                           // the rows beyond the box of plane zl + 1
 
 #pragma unroll 1
     for (int i = 0; i < nlead; ++i) {
-        const int zl = zlo + i;
+        const int zl = zlo + i, s = i & 1;
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            const int k = tid + j * TTX * ZTY;
+            const int k = tid + j * NT;
             tnext[j] = k < TTYPES ? type_src(zl + 2, k) : uint8_t(0);
         }
-        if (!mbar_wait(&bar[0], unsigned(i) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
-        float* st = S.stage[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = tid + j * NT;
+            xnext[j] = (k < 380 && zl + 1 <= zhi) ? xrow_src(zl + 1, k) : 0.0f;
+        }
+        if (!mbar_wait(&bar[s], unsigned(i >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+        float* st = S.stage[s][0];
         if (edge) {
-            for (int k = tid; k < band.cells * Q; k += TTX * ZTY) {
+            for (int k = tid; k < band.cells * Q; k += NT) {
                 const int a = k / band.cells;
-                int r, c;
-                band.cell(k - a * band.cells, 1, r, c);
-                st[a * TSSLOT + r * TBX + c] =
-                    fin[a * fs + (long long)wz(zl - ez_rt(a)) * nxy + wrap1(by0 + r, ny) * nx + wrap1(x0 - 4 + c, nx)];
+                int rb, c;
+                band.cell(k - a * band.cells, 1, rb, c);
+                st[a * TBSLOT + rb * TBX + c] =
+                    fin[a * fs + (long long)wz(zl - ez_rt(a)) * nxy + wrap1(y0 - 2 + rb, ny) * nx + wrap1(x0 - 4 + c, nx)];
             }
             fence_proxy_async();
             __syncthreads();
@@ -832,7 +870,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
         // A. densities of the density window, psi of the psi window (fluid cells), own values kept
         const uint8_t* ty = S.type[zl & 7];
         float* rr = S.rho[zl & 3];
-        float* pp = S.psi[zl & 7];
+        float* pp = S.psi[ps5(zl)];
         V2 fcur[Q];
         {
             float v[Q];
@@ -840,7 +878,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             const bool fl0 = !(t0 & T_SOLID), fl1 = !(t1 & T_SOLID);
             float d0 = 0.0f, d1 = 0.0f;
             if (fl0) {
-                pull(st, zl, ly + 3, lx + 4, t0, v);
+                pull(NoRing2{}, st, zl, ly + 2, lx + 4, t0, v);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d0 += v[a];
             } else {
@@ -850,7 +888,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 #pragma unroll
             for (int a = 0; a < Q; ++a) fcur[a].v.x = v[a];
             if (fl1) {
-                pull(st, zl, ly + 7, lx + 4, t1, v);
+                pull(NoRing2{}, st, zl, ly + 6, lx + 4, t1, v);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d1 += v[a];
             } else {
@@ -867,42 +905,43 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             pp[pc + 4 * TPX] = fl1 ? ps.v.y : 0.0f;
         }
         // halo cells: the 1-node ring (density and psi) and the 2-node ring (density)
-        for (int k = tid; k < TRING + TRING2; k += TTX * ZTY) {
-            int px, py, pz, r, c;
+        for (int k = tid; k < TRING + TRING2; k += NT) {
+            int px, py, pz, rb, c;
             if (k < TRING) {
                 Shell<TPX, TPY, 1, 2>::cell(k, px, py, pz);
-                r = py + 2;
+                rb = py + 1;
                 c = px + 3;
             } else {
                 Shell<TRX, TRY, 1, 2>::cell(k - TRING, px, py, pz);
-                r = py + 1;
+                rb = py;
                 c = px + 2;
             }
-            const uint8_t t = ty[r * TYX + c - 1];
+            const uint8_t t = ty[(rb + 1) * TYX + c - 1];
             const bool fl = !(t & T_SOLID);
             float rho = 0.0f;
             if (fl) {
                 float v[Q];
-                pull(st, zl, r, c, t, v);
+                pull(Ring2{}, st, zl, rb, c, t, v);
                 float d = 0.0f;
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d += v[a];
                 rho = ph.rho_ref + d;
             }
-            rr[(r - 1) * TRX + c - 2] = rho;
-            if (k < TRING) pp[(r - 2) * TPX + c - 3] = fl ? psi_checked(rho, ph, err) : 0.0f;
+            rr[rb * TRX + c - 2] = rho;
+            if (k < TRING) pp[(rb - 1) * TPX + c - 3] = fl ? psi_checked(rho, ph, err) : 0.0f;
         }
         __syncthreads();
-        if (tid == 0 && zl + 1 <= zhi) issue(zl + 1);   // loads while phases B and C run
+        if (tid == 0 && zl + 2 <= zhi) issue(zl + 2, s);
 
         // B. wall cells of plane zw = zl - 1: virtual density and its psi (the solid-fluid interaction
-        // scheme keeps psi = 0 on solids); node types of plane zl + 2 into the ring
+        // scheme keeps psi = 0 on solids); node types of plane zl + 2 and the rows beyond the box of
+        // plane zl + 1 into their rings
         const int zw = zl - 1;
         if (!SF && zw >= zb - 1) {
             const uint8_t* tw = S.type[zw & 7];
-            for (int k = tid; k < TPX * TPY; k += TTX * ZTY) {
-                const int c = k % TPX + 3, r = k / TPX + 2;
-                if (!(tw[r * TYX + c - 1] & T_WALL)) continue;
+            for (int k = tid; k < TPX * TPY; k += NT) {
+                const int c = k % TPX + 3, rb = k / TPX + 1;
+                if (!(tw[(rb + 1) * TYX + c - 1] & T_WALL)) continue;
                 float rw;
                 if (ph.wall_kind == 1) {
                     rw = ph.wall_param;
@@ -912,14 +951,14 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 #pragma unroll
                     for (int a = 1; a < Q; ++a) {
                         const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-                        if (!(S.type[(zw + ez) & 7][(r + ey) * TYX + c + ex - 1] & T_SOLID)) {
-                            num += float(L::wf(a)) * S.rho[(zw + ez) & 3][(r + ey - 1) * TRX + c + ex - 2];
+                        if (!(S.type[(zw + ez) & 7][(rb + ey + 1) * TYX + c + ex - 1] & T_SOLID)) {
+                            num += float(L::wf(a)) * S.rho[(zw + ez) & 3][(rb + ey) * TRX + c + ex - 2];
                             den += float(L::wf(a));
                         }
                     }
                     const float rho_ave = cdiv(num, den);
                     const float kap =
-                        g.kappa_w ? float(g.kappa_w[g.wall_id[(long long)wz(zw) * nxy + wrap1(by0 + r, ny) * nx +
+                        g.kappa_w ? float(g.kappa_w[g.wall_id[(long long)wz(zw) * nxy + wrap1(y0 - 2 + rb, ny) * nx +
                                                               wrap1(x0 - 4 + c, nx)]])
                                   : float(g.kappa);
                     // Eq. 16 (kappa >= 0: phi = 1 + kappa; kappa < 0: drho = -kappa) and the limiter
@@ -927,13 +966,18 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
                     rw = raw > ph.rho_l ? ph.rho_l : raw;
                     rw = rw < ph.rho_g ? ph.rho_g : rw;
                 }
-                S.psi[zw & 7][k] = psi_checked(rw, ph, err);
+                S.psi[ps5(zw)][k] = psi_checked(rw, ph, err);
             }
         }
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            const int k = tid + j * TTX * ZTY;
+            const int k = tid + j * NT;
             if (k < TTYPES) S.type[(zl + 2) & 7][k] = tnext[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = tid + j * NT;
+            if (k < 380) xrow_dst(zl + 1, k) = xnext[j];
         }
         __syncthreads();
 
@@ -945,7 +989,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             if (fl0 || fl1) {
                 V2(&f)[Q] = f2;
                 auto psi_at = [&](int dz, int off) {
-                    const float* q = S.psi[(zc + dz) & 7];
+                    const float* q = S.psi[ps5(zc + dz)];
                     return mk(q[pc + off], q[pc + 4 * TPX + off]);
                 };
                 const V2 psi_c = psi_at(0, 0);
@@ -1001,11 +1045,11 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
                 const V2 ux = fma2(0.5f, Fx, jx) * inv, uy = fma2(0.5f, Fy, jy) * inv, uz = fma2(0.5f, Fz, jz) * inv;
                 const V2 X = div2(fma2(Fmx, Fmx, fma2(Fmy, Fmy, Fmz * Fmz)), psi_c * psi_c);
                 collide3p(f, drho, rho, ux, uy, uz, Fx, Fy, Fz, X, kr);
-                float* o = fout + (long long)zc * nxy + (y0 + ly) * nx + x0 + lx;
+                const int gi = zc * nxy + (y0 + ly) * nx + x0 + lx;
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    if (fl0) o[a * fs] = f[a].v.x;
-                    if (fl1) o[a * fs + 4 * nx] = f[a].v.y;
+                    if (fl0) fout[a * fs + gi] = f[a].v.x;
+                    if (fl1) fout[a * fs + gi + 4 * nx] = f[a].v.y;
                 }
             }
         }
@@ -1039,13 +1083,13 @@ __global__ void __launch_bounds__(TTX* ZTY, 2)
             fence_mbar_init();
         }
         __syncthreads();
-        // tmap: the buffer's two maps (box heights TBY and TSY)
+        // tmap: the input buffer's map (box TBX x TBY x 1)
         if (!s0 && !s1)
             ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.b, S.bar);
         else if (sf)
-            ztma_chunk_solid<true>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
+            ztma_chunk_solid<true>(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
         else
-            ztma_chunk_solid<false>(fin, fout, static_cast<const char*>(tmap) + 128, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
+            ztma_chunk_solid<false>(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
         return;
     }
     ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
@@ -1103,10 +1147,9 @@ cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, cons
     return cudaGetLastError();
 }
 
-void ztma_box_dims(int* bx, int* by_bulk, int* by_solid) {
+void ztma_box_dims(int* bx, int* by) {
     *bx = TBX;
-    *by_bulk = TBY;
-    *by_solid = TSY;
+    *by = TBY;
 }
 
 }  // namespace lbmwet
