@@ -9,17 +9,21 @@
   steps a 15^3 window around each sampled node taken from the GPU state: one step's output at a node
   depends on the state within 3 nodes (pull, psi of neighbours, virtual densities of neighbouring
   wall nodes), so the window's centre is exact although its edges wrap.
-* The 600 x 400 workload run for its configured 20000 steps in FP32 deviation storage and in FP64:
-  the contact angle within 0.5 degrees and the density within 1e-4 of the liquid density.
+* The 600 x 400 workload run for its configured 20000 steps in FP32 deviation storage and in FP64,
+  against each other and against the FP64 oracle's stored result (tests/golden): the contact angle
+  within 0.5 degrees (FP32) and the split FP32 density bounds.
 
 FP32 single-step tolerances: the stored deviations carry float rounding (relative 6e-8 of the
 distributions) through one collision; 2e-6 of the largest distribution bounds it with margin.
 """
+import os
+
 import numpy as np
 import pytest
 
 import workloads as W
 from oracle import eos as E, lbm
+from tests.fp32_bounds import split_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -143,7 +147,48 @@ def test_c2_20000_steps_fp32_against_fp64():
             out[prec] = sim.observables(fields=True)
     o64, r64, _ = out["fp64"]
     o32, r32, _ = out["fp32"]
-    fl = wl.mask() == 0
-    assert np.max(np.abs(r32[fl] - r64[fl])) <= 1e-4 * l
+    bulk, band, nb, ni = split_errors(r32, r64, wl.mask(), l, g)
+    print(f"C2 FP32 vs FP64 after 20000 steps: bulk max |drho|/rho = {bulk:.3e} over {nb} nodes, "
+          f"interface band max |drho|/rho_l = {band:.3e} over {ni} nodes")
+    assert bulk <= 1e-4
+    assert band <= 1e-4
     assert abs(o32.theta_deg - o64.theta_deg) <= 0.5
     assert abs(o32.mass / o64.mass - 1) <= 1e-4
+
+
+GOLDEN_C2 = os.path.join(os.path.dirname(__file__), "golden", "c2_600x400_kappa0.15_20000.npz")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_c2_20000_steps_against_oracle_golden(prec):
+    """The 600 x 400 workload after its 20000 steps against the FP64 oracle's result (written by
+    tests/golden/make_c2_golden.py, which calls only the oracle).  FP32: the split density bounds
+    (1e-4 relative at bulk nodes, 1e-4 of rho_l in the interface band) and the contact angle within
+    0.5 degrees.  FP64: the contact angle within 1e-6 degrees, the density within 1e-8 and the mass
+    within 1e-11.  One step agrees with the oracle to 1e-16 (the same arithmetic in another order);
+    over 20000 steps of the still-spreading drop those differences grow to 2.3e-9 in density
+    (measured on GB300), so the 1e-10 of the 1000-step parity case is out of reach here and 1e-8 is
+    the bound.  The total mass drifts by rounding on both sides (at most a few ulps of the sum per
+    step, about 2e-12 relative after 20000 steps each)."""
+    from paper_1908_04443_gb300 import lbmwet as L
+    ref = np.load(GOLDEN_C2)
+    eos, g, l = _eos(0.6)
+    assert abs(float(ref["rho_l"]) - l) < 1e-14 and abs(float(ref["rho_g"]) - g) < 1e-14
+    wl = W.c2_cylinder_600x400(kappa=float(ref["kappa"]))
+    with L.Simulation(_cfg(L, wl, prec, g, l), wl.mask(), wl.rho0(l, g)) as sim:
+        sim.step(int(ref["steps"]))
+        o, rho, _ = sim.observables(fields=True)
+    rho_ref = ref["rho"]
+    fl = wl.mask() == 0
+    d = np.abs(rho - rho_ref)[fl]
+    bulk, band, nb, ni = split_errors(rho, rho_ref, wl.mask(), l, g)
+    print(f"C2 {prec} vs oracle after 20000 steps: max |drho| = {d.max():.3e}, bulk max |drho|/rho = {bulk:.3e}, "
+          f"band max |drho|/rho_l = {band:.3e}, theta {o.theta_deg:.6f} vs {float(ref['theta_deg']):.6f} deg")
+    if prec == "fp32":
+        assert bulk <= 1e-4
+        assert band <= 1e-4
+        assert abs(o.theta_deg - float(ref["theta_deg"])) <= 0.5
+    else:
+        assert d.max() <= 1e-8
+        assert abs(o.theta_deg - float(ref["theta_deg"])) <= 1e-6
+        assert abs(o.mass / float(ref["mass"]) - 1) <= 1e-11
