@@ -59,6 +59,9 @@ FP64_FLOPS_PER_NODE = {
 # FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
 # SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# GB300 HBM3e nominal bandwidth (the roofline fractions are against the measured copy rate; this is
+# reported beside it)
+NOMINAL_HBM_GBS = 7900.0
 
 
 def tile_kernel_hash() -> str:
@@ -72,6 +75,14 @@ def tile_kernel_hash() -> str:
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in ("step2p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the pair kernel's sources
+        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ztma_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step3p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the 3D kernel's sources
         with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -174,14 +185,23 @@ class ClockSampler:
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
+import numpy as np
 import workloads as W
 from oracle import eos as E, lbm
 wl = W.{ctor}
 e = (E.cs_config() if wl.eos == "CS" else E.pr_paper()).at_reduced_temperature(wl.t_over_tc)
 g, l = E.maxwell(e)
-geo = lbm.Geometry(wl.mask(), wl.lattice)
+mask, rho0 = wl.mask(), wl.rho0(l, g)
+crop = {crop}
+if crop:   # a window of the workload (mask and initial density) around the lower part of the body
+    # and the gas below it: no liquid-gas interface crosses the window's (periodic) faces
+    c = [int(round(v)) for v in wl.body_center[::-1]]
+    c[0] -= 24
+    win = tuple(slice(ci - crop // 2, ci + crop // 2) for ci in c)
+    mask, rho0 = np.ascontiguousarray(mask[win]), np.ascontiguousarray(rho0[win])
+geo = lbm.Geometry(mask, wl.lattice)
 p = lbm.Params(wl.lattice, e, sigma={sigma}, rho_l=l, rho_g=g, kappa=wl.kappa)
-f = lbm.init_state(wl.rho0(l, g), geo)
+f = lbm.init_state(rho0, geo)
 for _ in range({warmup}):
     f = lbm.step(f, geo, p)
 times = []
@@ -189,8 +209,12 @@ for _ in range({steps}):
     t = time.perf_counter()
     f = lbm.step(f, geo, p)
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times, "nodes": wl.nodes}}))
+print(json.dumps({{"times": times, "nodes": int(mask.size)}}))
 """
+
+
+# the 256^3 sphere's oracle sample: a 96^3 window of it around the sphere's lower half
+C3_ORACLE_WINDOW = 96
 
 
 def run_oracle(wl_name: str, steps: int, warmup: int, procs: int = 1):
@@ -198,7 +222,8 @@ def run_oracle(wl_name: str, steps: int, warmup: int, procs: int = 1):
     the grid's node count."""
     ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()", "c4": "c4_batch(96)[0]"}.get(
         wl_name, "c2_cylinder_600x400(kappa=0.15)")
-    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps)
+    crop = C3_ORACLE_WINDOW if wl_name == "c3" else 0
+    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps, crop=crop)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
                            env=env) for _ in range(procs)]
@@ -217,8 +242,11 @@ def cpu_baseline(wl_name: str, target_s: float = 15.0, all_cores: bool = True):
     n = max(1, min(2000, int(target_s / max(t1[0], 1e-4))))
     (times,), nodes = run_oracle(wl_name, n, 0)
     total = sum(times)
+    what = (f"a {C3_ORACLE_WINDOW}^3 window of the 256^3 sphere workload (mask and initial density of "
+            f"z 28..123 around the sphere's lower half, periodic)" if wl_name == "c3"
+            else f"one {nodes}-node grid of the workload")
     res = {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{n} FP64 oracle steps of one {nodes}-node grid of the workload, one thread"}
+           "sample": f"{n} FP64 oracle steps of {what}, one thread"}
     procs = os.cpu_count() or 1
     if all_cores and procs > 1:
         # every host core: the workload's grids are independent, so one single-thread oracle
@@ -230,6 +258,47 @@ def cpu_baseline(wl_name: str, target_s: float = 15.0, all_cores: bool = True):
                             "sample": f"{procs} concurrent single-thread oracle processes, {m} steps each of one "
                                       f"{nodes}-node grid of the workload (rate over the slowest process)"}
     return res
+
+
+# ---------------------------------------------------------------------------------------------
+# error against the FP64 oracle: one step from the GPU's own state (the GPU steps once more; the
+# oracle steps the same state), on a sampled instance or, for the 256^3 sphere, on windows around
+# sampled nodes (one step's output at a node depends on the state within 3 nodes)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_params(wl):
+    from oracle import eos as E, lbm
+    e = (E.cs_config() if wl.eos == "CS" else E.pr_paper()).at_reduced_temperature(wl.t_over_tc)
+    g, l = E.maxwell(e)
+    return lbm.Params(wl.lattice, e, sigma=sigma_for(wl), rho_l=l, rho_g=g, kappa=wl.kappa)
+
+
+def err_one_step(L, h, wl, step_once, windows=0, seed=3):
+    """max |f_gpu - f_oracle| / max |f_oracle| after one step from the GPU state of handle h (the
+    step is taken by step_once(), which may step a whole batch)."""
+    from oracle import lbm
+    q = 9 if wl.lattice == "D2Q9" else 19
+    before = L.lbm_get_state(h, q, wl.nodes).reshape((q,) + wl.shape)
+    step_once()
+    after = L.lbm_get_state(h, q, wl.nodes).reshape((q,) + wl.shape)
+    p = oracle_params(wl)
+    mask = wl.mask()
+    if not windows:
+        ref = lbm.step(before, lbm.Geometry(mask, wl.lattice), p)
+        return {"max_rel": float(np.max(np.abs(after - ref)) / np.max(np.abs(ref))), "nodes": "all",
+                "definition": "one step from a common state: max |f_gpu - f_oracle| / max |f_oracle|"}
+    rng = np.random.default_rng(seed)
+    fluid = np.argwhere(mask == 0)
+    r = 7
+    worst, ref_max, used = 0.0, 0.0, 0
+    for z, y, x in fluid[rng.choice(len(fluid), windows, replace=False)]:
+        win = np.ix_(*[np.arange(c - r, c + r + 1) % n for c, n in zip((z, y, x), wl.shape)])
+        ref = lbm.step(before[(slice(None),) + win], lbm.Geometry(mask[win], wl.lattice), p)[:, r, r, r]
+        worst = max(worst, float(np.max(np.abs(after[:, z, y, x] - ref))))
+        ref_max = max(ref_max, float(np.max(np.abs(ref))))
+        used += 1
+    return {"max_rel": worst / ref_max, "nodes": f"{used} sampled fluid nodes (15^3 oracle windows)",
+            "definition": "one step from a common state: max |f_gpu - f_oracle| / max |f_oracle|"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -321,52 +390,152 @@ class Runner:
             self.L.lbm_destroy(self.h)
 
 
-def adjoint_ratio(L, torch, stream, steps=2000, ckpt=100):
-    """The 256 x 256 adjoint workload: per-wall-node kappa on a cylinder of radius 40, FP32, loss
-    sum (rho_T - rho_target)^2.  Times the forward pass with checkpoints (lbm_record) and the
-    gradient (lbm_adjoint: segment recomputation + reverse sweep) with CUDA events."""
+def adjoint_c5(L, torch, stream, steps=2000, ckpt=100, n_fd=8, dk=1e-3):
+    """The 256 x 256 adjoint workload as configured: per-wall-node wettability kappa_j on a cylinder of
+    radius 40 (kappa = 0.1 everywhere), loss L = sum over fluid nodes of (rho_T - rho_target)^2 after
+    2000 steps, where rho_target comes from the same run with kappa_j = 0.1 + a seeded smooth random
+    function of the polar angle (4 modes, amplitude 0.2, seed 7).  The FP32 forward pass with
+    checkpoints every 100 steps (lbm_record) and the gradient (lbm_adjoint: segment recomputation +
+    reverse sweep) are timed with CUDA events; the gradient is checked against FP64 central finite
+    differences of L at n_fd wall nodes spread around the cylinder."""
     wl = W.c5_adjoint_256()
     e = L.make_eos("CS", 0.25, 4.0, 1.0, 0.0)
     e.T = wl.t_over_tc * L.lbm_critical_temperature(e)
     rho_g, rho_l = L.lbm_coexistence(e)
-    cfg = make_cfg(L, wl, "fp32", rho_g, rho_l)
     mask = wl.mask()
-    h = L.lbm_init(cfg, mask, wl.rho0(rho_l, rho_g), None, None, stream)
-    nw = len(L.lbm_wall_nodes(h))
+    fl = (mask.reshape(-1) == 0)
+    rho0 = wl.rho0(rho_l, rho_g)
+    h64 = L.lbm_init(make_cfg(L, wl, "fp64", rho_g, rho_l), mask, rho0, None, None, stream)
+    idx = L.lbm_wall_nodes(h64)
+    nw = len(idx)
     cx, cy = wl.body_center
-    idx = L.lbm_wall_nodes(h)
     ang = np.arctan2(idx // wl.shape[1] - cy, idx % wl.shape[1] - cx)
-    kappa = 0.1 + W.smooth_polar_field(ang)
-    L.lbm_set_kappa(h, kappa)
-    f0 = L.lbm_get_state(h, 9, wl.nodes)
+    kap0 = np.full(nw, float(wl.kappa))
+    kap_t = wl.kappa + W.smooth_polar_field(ang)
+    f0 = L.lbm_get_state(h64, 9, wl.nodes)
+
+    def rho_after(h, kap):
+        L.lbm_set_kappa(h, kap)
+        L.lbm_set_state(h, f0, 0)
+        L.lbm_step(h, steps)
+        rho = np.empty(wl.nodes)
+        L.lbm_observables(h, rho, None)
+        return rho
+
+    rho_t = rho_after(h64, kap_t)
+
+    def loss64(kap):
+        d = (rho_after(h64, kap) - rho_t)[fl]
+        return float(np.dot(d, d))
+
+    # FP32 forward with checkpoints and the adjoint gradient at kappa0
+    h32 = L.lbm_init(make_cfg(L, wl, "fp32", rho_g, rho_l), mask, rho0, None, None, stream)
+    L.lbm_set_kappa(h32, kap0)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     with torch.cuda.stream(stream):
         ev[0].record(stream)
-        L.lbm_record(h, steps, ckpt)
+        L.lbm_record(h32, steps, ckpt)
         ev[1].record(stream)
     rho = torch.empty(wl.nodes, dtype=torch.float64, device="cuda")
-    L.lbm_fields_device(h, rho.data_ptr(), None)
+    L.lbm_fields_device(h32, rho.data_ptr(), None)
     torch.cuda.synchronize()
-    drho = 2.0 * (rho - rho.mean()) * torch.as_tensor(mask.reshape(-1) == 0, device="cuda")
+    target = torch.as_tensor(rho_t, device="cuda")
+    drho = 2.0 * (rho - target) * torch.as_tensor(fl, device="cuda")
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         ev[2].record(stream)
-        g = L.lbm_adjoint(h, drho.data_ptr(), nw)
+        g32 = L.lbm_adjoint(h32, drho.data_ptr(), nw)
         ev[3].record(stream)
     torch.cuda.synchronize()
     fwd = ev[0].elapsed_time(ev[1])
     adj = ev[2].elapsed_time(ev[3])
-    L.lbm_destroy(h)
-    return {"workload": f"c5_adjoint_256x256_fp32 ({steps} steps, checkpoint every {ckpt})", "wall_nodes": nw,
+    # FP64 central differences at wall nodes spread around the cylinder
+    picks = [int(k) for k in np.linspace(0, nw - 1, n_fd).round()]
+    g_fd = []
+    for j in picks:
+        kp, km = kap0.copy(), kap0.copy()
+        kp[j] += dk
+        km[j] -= dk
+        g_fd.append((loss64(kp) - loss64(km)) / (2.0 * dk))
+    g_fd = np.array(g_fd)
+    g_ad = g32[picks]
+    scale = float(np.max(np.abs(g_fd)))
+    L.lbm_destroy(h32)
+    L.lbm_destroy(h64)
+    return {"workload": f"c5_adjoint_256x256_fp32 ({steps} steps, checkpoint every {ckpt}, {nw} wall nodes)",
+            "loss": "sum over fluid nodes of (rho_T - rho_target)^2; target from kappa = 0.1 + smooth polar "
+                    "field (4 modes, amplitude 0.2, seed 7)",
             "forward_ms": round(fwd, 3), "adjoint_ms": round(adj, 3), "ratio": round(adj / fwd, 3),
             "note": "adjoint = recomputation of each checkpoint segment + the reverse sweep; forward = "
-                    "the checkpointed forward pass", "grad_norm": float(np.linalg.norm(g))}
+                    "the checkpointed forward pass",
+            "err_vs_oracle": {"max_rel": float(np.max(np.abs(g_ad - g_fd)) / scale) if scale > 0 else None,
+                              "definition": f"FP32 adjoint dL/dkappa_j against FP64 central differences "
+                                            f"(dkappa = {dk}) at {n_fd} wall nodes, max |diff| / max |FD|",
+                              "fd": [float(v) for v in g_fd], "adjoint": [float(v) for v in g_ad]}}
 
 
-def device_rate(L, torch, stream, name, steps, flush, precision=None):
+def batched_vs_separate(L, torch, stream, run, cfgs, masks, rho0s, steps):
+    """One batched launch per step against one launch per instance per step (no L2 flush)."""
+    seps = [L.lbm_init(c, m, r, None, None, stream) for c, m, r in zip(cfgs, masks, rho0s)]
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn(2)
+            torch.cuda._sleep(int(2e6 + 4e5 * steps))
+            ev0.record(stream)
+            fn(steps)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    def sep(n):
+        for _ in range(n):
+            for h in seps:
+                L.lbm_enqueue_steps(h, 1)
+
+    ms_b = timed(run.enqueue)
+    ms_s = timed(sep)
+    for h in seps:
+        L.lbm_destroy(h)
+    return {"instances": len(cfgs), "steps": steps, "batched_ms_per_step": round(ms_b, 5),
+            "separate_ms_per_step": round(ms_s, 5), "speedup": round(ms_s / ms_b, 3),
+            "note": "one batched launch per step vs one launch per instance per step; L2 not flushed"}
+
+
+def e2e_rate(L, cfgs, masks, rho0s, wls, steps, stream, world=1):
+    """The metric end to end through the public API with host buffers: init from the host mask and
+    initial density, `steps` calls of the stepping entry point with one step each (each reads back
+    the 4-byte device status), then the observables with the host density and velocity fields of
+    every instance."""
+    t0 = time.perf_counter()
+    r2 = Runner(L, cfgs, masks, rho0s, stream)
+    for _ in range(steps):
+        r2.step(1)
+    d2h = 4 * steps
+    dim = 2 if wls[0].lattice == "D2Q9" else 3
+    for h, wl in zip(r2.handles, wls):
+        rho_h = np.empty(wl.nodes)
+        u_h = np.empty(wl.nodes * dim)
+        L.lbm_observables(h, rho_h, u_h)
+        d2h += rho_h.nbytes + u_h.nbytes + 8 * 18
+    r2.close()
+    e2e_s = time.perf_counter() - t0
+    nodes = sum(wl.nodes for wl in wls)
+    h2d = sum(m.size + r.size * 8 for m, r in zip(masks, rho0s))
+    return {"value": round(world * nodes * steps / e2e_s / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+            "seconds": round(e2e_s, 4),
+            "definition": "init from host mask/rho0 + K x step(1) (4-byte status read each) + observables "
+                          "with host rho and u of every instance"}
+
+
+def device_rate(L, torch, stream, name, steps, flush, precision=None, extras=None):
     """Device-timed MLUPS and HBM-roofline fraction of another workload (same protocol as the
-    headline: L2 flushed before each timed step, CUDA events around each step); `precision`
-    overrides the workload's."""
+    headline: L2 flushed before each timed step when the state fits in L2, else back-to-back steps
+    between one pair of events); `precision` overrides the workload's.  Adds the fluid-only rate,
+    the error against the FP64 oracle (one step from the GPU state of instance 0) and, through
+    `extras(run, wls, cfgs, masks, rho0s)`, workload-specific fields."""
     wls, prec0, label = workload(name)
     precision = precision or prec0
     if precision != prec0:
@@ -381,46 +550,62 @@ def device_rate(L, torch, stream, name, steps, flush, precision=None):
             if wl.kappa < 0:
                 wl.kappa *= (rho_l - rho_g)
     cfgs = [make_cfg(L, wl, precision, rho_g, rho_l) for wl in wls]
-    run = Runner(L, cfgs, [wl.mask() for wl in wls], [wl.rho0(rho_l, rho_g) for wl in wls], stream)
+    masks = [wl.mask() for wl in wls]
+    rho0s = [wl.rho0(rho_l, rho_g) for wl in wls]
+    run = Runner(L, cfgs, masks, rho0s, stream)
     nodes = sum(wl.nodes for wl in wls)
+    fluid = int(sum(int((m == 0).sum()) for m in masks))
     with torch.cuda.stream(stream):
         run.enqueue(3)
     run.step(0)
-    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
     use_flush = bytes_per_lu(wls[0].lattice, precision) * nodes < 2 * l2
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps if use_flush else 1)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps if use_flush else 1)]
     with torch.cuda.stream(stream):
         torch.cuda._sleep(int(2e6 + 4e5 * steps))
-        for k in range(steps):
-            if use_flush:
+        if use_flush:
+            for k in range(steps):
                 flush.zero_()
-            st[k].record(stream)
-            run.enqueue(1)
-            en[k].record(stream)
+                st[k].record(stream)
+                run.enqueue(1)
+                en[k].record(stream)
+        else:
+            st[0].record(stream)
+            run.enqueue(steps)
+            en[0].record(stream)
     torch.cuda.synchronize()
     run.step(0)
-    run.close()
     ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / steps
+    kernel = run.kernel_name()
+    err = err_one_step(L, run.handles[0], wls[0], lambda: run.step(1), windows=40 if wls[0].nodes > 4e6 else 0)
+    more = extras(run, wls, cfgs, masks, rho0s) if extras else {}
+    run.close()
     peak = 6800.0
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         with open(pk_path) as fh:
             peak = json.load(fh).get("hbm_gbs", peak)
     gbs = bytes_per_lu(wls[0].lattice, precision) * nodes / (ms * 1e-3) / 1e9
-    out = {"workload": label, "nodes": nodes, "steps": steps, "ms_per_step": round(ms, 5),
+    out = {"workload": label, "kernel": kernel, "nodes": nodes, "fluid_nodes": fluid, "steps": steps,
+           "ms_per_step": round(ms, 5),
            "l2": "flushed before each timed step" if use_flush else "inputs larger than L2, no flush",
-           "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT, "achieved_gbs": round(gbs, 1),
-           "frac_of_measured_hbm": round(gbs / peak, 4), "bound": "hbm"}
+           "value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": UNIT,
+           "fluid_only_value": round(fluid / (ms * 1e-3) / 1e6, 1), "achieved_gbs": round(gbs, 1),
+           "frac_of_measured_hbm": round(gbs / peak, 4), "frac_of_measured_hbm_fluid_only": round(gbs * fluid / nodes / peak, 4),
+           "frac_of_nominal_hbm": round(gbs / NOMINAL_HBM_GBS, 4), "bound": "hbm", "err_vs_oracle": err}
+    out.update(more)
     if precision == "fp64":
         # GB300's FP64 rate is far below its FP32 rate: the FP64 step is bound by the FP64 pipe
         fpn = FP64_FLOPS_PER_NODE.get((name, tile_kernel_hash()))
+        fp64_peak = L.lbm_probe_fp64_rate(stream)
         out["bound"] = "alu"
         out["alu_roofline"] = {
-            "flops_per_node": fpn, "unit": "GFLOP/s", "peak": round(FP64_PEAK_GFLOPS, 1),
-            "peak_source": "derived: 152 SMs x 4 FP64 flops per SM per clock x 2.07 GHz (1.25 TFLOP/s nominal)",
+            "flops_per_node": fpn, "unit": "GFLOP/s", "peak": round(fp64_peak, 1),
+            "peak_source": "measured: lbm_probe_fp64_rate (independent FP64 FMA chains, 16 CTAs per SM)",
+            "nominal_peak": round(FP64_PEAK_GFLOPS, 1),
             "achieved": None if fpn is None else round(fpn * nodes / (ms * 1e-3) / 1e9, 1),
-            "frac": None if fpn is None else round(fpn * nodes / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, 4)}
+            "frac": None if fpn is None else round(fpn * nodes / (ms * 1e-3) / 1e9 / fp64_peak, 4)}
     return out
 
 
@@ -525,68 +710,66 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes, "kernel": run.kernel_name()}
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel": run.kernel_name(),
+                "frac_fluid_only": round(achieved * fluid / nodes / peak, 4),
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS}
+
+    # a sustained run of about one second (more clock samples than the K timed steps give)
+    sustained = None
+    if not args.no_extras:
+        n_sus = max(args.steps, min(5000, int(1000.0 / max(ms_per_step, 1e-3))))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk2:
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(int(2e6))
+                e0.record(stream)
+                run.enqueue(n_sus)
+                e1.record(stream)
+            torch.cuda.synchronize()
+        run.step(0)
+        ms_sus = e0.elapsed_time(e1) / n_sus
+        cs = clk2.summary()
+        sustained = {"steps": n_sus, "ms_per_step": round(ms_sus, 6), "value": round(nodes / (ms_sus * 1e-3) / 1e6, 1),
+                     "unit": UNIT, "frac_of_measured_hbm": round(bpl * nodes / (ms_sus * 1e-3) / 1e9 / peak, 4),
+                     "clocks": cs,
+                     "ms_x_median_sm_ghz": None if not cs["sm_mhz"] else round(ms_sus * cs["sm_mhz"] / 1e3, 6),
+                     "note": "the same step back to back for about one second (at most 5000 steps); time x "
+                             "median SM clock is comparable across runs at different clocks"}
+
+    # error against the FP64 oracle: one step from the GPU state of the first instance
+    err = err_one_step(L, run.handles[0], wls[0], lambda: run.step(1))
 
     # batched launch vs one launch per instance (no L2 flush: back-to-back steps)
-    batched_vs_separate = None
+    bvs = None
     if run.batch and not args.no_extras:
-        seps = [L.lbm_init(c, m, r, None, None, stream) for c, m, r in zip(cfgs, masks, rho0s)]
-        kk = max(16, args.steps // 2)
-        def timed(fn):
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                fn(2)
-                torch.cuda._sleep(int(2e6 + 4e5 * kk))
-                ev0.record(stream)
-                fn(kk)
-                ev1.record(stream)
-            torch.cuda.synchronize()
-            return ev0.elapsed_time(ev1) / kk
-        def sep(n):
-            for _ in range(n):
-                for h in seps:
-                    L.lbm_enqueue_steps(h, 1)
-        ms_b = timed(run.enqueue)
-        ms_s = timed(sep)
-        for h in seps:
-            L.lbm_destroy(h)
-        batched_vs_separate = {"instances": len(cfgs), "steps": kk, "batched_ms_per_step": round(ms_b, 5),
-                               "separate_ms_per_step": round(ms_s, 5), "speedup": round(ms_s / ms_b, 3),
-                               "note": "one batched launch per step vs one launch per instance per step; "
-                                       "L2 not flushed"}
+        bvs = batched_vs_separate(L, torch, stream, run, cfgs, masks, rho0s, max(16, args.steps // 2))
     run.close()
 
     adjoint = None
     if not args.no_extras and args.workload in ("c2", "c5"):
-        adjoint = adjoint_ratio(L, torch, stream, steps=args.adjoint_steps)
+        adjoint = adjoint_c5(L, torch, stream, steps=args.adjoint_steps)
     others = None
     if not args.no_extras and args.workload == "c2":
-        others = {w: device_rate(L, torch, stream, w, steps, flush) for w, steps in (("c3", 10), ("c4", 20))}
-        if args.workload == "c2":
-            others["c2_fp64"] = device_rate(L, torch, stream, "c2", 10, flush, precision="fp64")
+        def c3_extras(r, w, c, m, r0):
+            out = {"traffic": NCU_TRAFFIC.get(("c3", "fp32", ztma_kernel_hash())),
+                   "e2e": e2e_rate(L, c, m, r0, w, args.steps, stream)}
+            if rank == 0 and not args.no_cpu_baseline:
+                try:
+                    out["cpu_baseline"] = cpu_baseline("c3", target_s=10.0, all_cores=False)
+                except Exception as exc:   # a reported baseline only
+                    out["cpu_baseline"] = {"error": str(exc)[:200]}
+            return out
 
-    # end to end through the public API with host buffers: init from host arrays, K calls of the
-    # stepping entry point with one step each (each reads back the 4-byte device status), then the
-    # observables with the host density and velocity fields of every instance
+        def c4_extras(r, w, c, m, r0):
+            return {"batched_vs_separate": batched_vs_separate(L, torch, stream, r, c, m, r0, max(16, args.steps // 2))}
+
+        others = {"c3": device_rate(L, torch, stream, "c3", max(100, args.steps), flush, extras=c3_extras),
+                  "c4": device_rate(L, torch, stream, "c4", max(50, args.steps), flush, extras=c4_extras),
+                  "c2_fp64": device_rate(L, torch, stream, "c2", 10, flush, precision="fp64")}
+
+    # end to end through the public API with host buffers
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    r2 = Runner(L, cfgs, masks, rho0s, stream)
-    for _ in range(args.steps):
-        r2.step(1)
-    d2h = 4 * args.steps
-    dim = 2 if lattice == "D2Q9" else 3
-    for h, wl in zip(r2.handles, wls):
-        rho_h = np.empty(wl.nodes)
-        u_h = np.empty(wl.nodes * dim)
-        L.lbm_observables(h, rho_h, u_h)
-        d2h += rho_h.nbytes + u_h.nbytes + 8 * 18
-    r2.close()
-    e2e_s = time.perf_counter() - t0
-    h2d = sum(m.size + r.size * 8 for m, r in zip(masks, rho0s))
-    e2e = {"value": round(world * nodes * args.steps / e2e_s / 1e6, 2), "unit": UNIT,
-           "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
-           "definition": "init from host mask/rho0 + K x step(1) (4-byte status read each) + observables "
-                         "with host rho and u of every instance"}
+    e2e = e2e_rate(L, cfgs, masks, rho0s, wls, args.steps, stream, world)
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 6), "higher_is_better": True,
@@ -604,9 +787,11 @@ def run_ours(args):
                            "note": "the same rate counting fluid nodes only (solid nodes are skipped)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "wall_s_timed_region": round(t_wall, 4),
-            "kernel_hash": khash}
-    if batched_vs_separate:
-        line["batched_vs_separate"] = batched_vs_separate
+            "kernel_hash": khash, "err_vs_oracle": err}
+    if sustained:
+        line["sustained"] = sustained
+    if bvs:
+        line["batched_vs_separate"] = bvs
     if adjoint:
         line["adjoint_vs_forward"] = adjoint
     if others:

@@ -189,6 +189,14 @@ lbm_status lbm_check(lbm_handle* h);
  * up and flagged the timeout (the expected outcome), 0 otherwise.  Synchronises the stream. */
 lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* timed_out);
 
+/* FP64 rate probe (no counterpart in the paper): the FP64 step kernels are bound by the device's
+ * FP64 arithmetic, and their roofline needs its measured rate.  Launches, on `stream` (NULL: the
+ * legacy default stream), a grid of 16 CTAs per SM whose threads run eight independent chains of
+ * FP64 fused multiply-adds, times three launches after a warm-up with CUDA events and sets
+ * *gflops to the best rate (2 flops per FMA).  Allocates 8 bytes of device memory for the call;
+ * synchronises the stream.  Errors: LBM_ERR_ARG (NULL gflops), LBM_ERR_CUDA. */
+lbm_status lbm_probe_fp64_rate(void* stream, double* gflops);
+
 /* Memory-safety check, for tests (the paper has no counterpart).  Both distribution buffers and
  * the density / velocity fields of lbm_observables sit between two 4096-byte guard zones filled
  * with the byte 0xA5 when they are allocated; D2Q9 distribution rows also carry padding nodes

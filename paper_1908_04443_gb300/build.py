@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbmwet.so")
 OBJ = os.path.join(ROOT, "_build")
-SOURCES = ["step.cu", "step2p.cu", "step2d.cu", "step3d.cu", "step3p.cu", "reduce.cu", "adjoint.cu", "api.cu", "eos_host.cpp", "plan.cpp", "wall_gf.cpp"]
+SOURCES = ["step.cu", "step2p.cu", "step2d.cu", "step3d.cu", "step3p.cu", "reduce.cu", "adjoint.cu", "probe.cu", "api.cu",
+           "eos_host.cpp", "plan.cpp", "wall_gf.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXTRA_FLAGS = os.environ.get("LBMWET_NVCC_FLAGS", "").split()   # e.g. tile-shape macros for measurements
 

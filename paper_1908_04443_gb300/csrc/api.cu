@@ -749,6 +749,14 @@ lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* time
     return LBM_OK;
 }
 
+lbm_status lbm_probe_fp64_rate(void* stream, double* gflops) {
+    if (!gflops) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *gflops = 0.0;
+    cudaError_t e = probe_fp64_rate(static_cast<cudaStream_t>(stream), gflops);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "FP64 rate probe");
+    return LBM_OK;
+}
+
 lbm_status lbm_check_guards(lbm_handle* h, int64_t* guard_bad, int64_t* pad_bad) {
     if (!h || !guard_bad || !pad_bad) return LBM_ERR_ARG;
     *guard_bad = 0;

@@ -103,6 +103,9 @@ cudaError_t launch_pair_step(const void* fin, void* fout, const DevParams& p, cu
 cudaError_t launch_pair_batched(int parity, const DevParams& phys, const BatchItem* items, int n_items, int ctas,
                                 unsigned* sched, cudaStream_t s);
 void pair_tile_shape(int* tx, int* ty);
+// Measured FP64 fused multiply-add rate of the device (GFLOP/s, best of three timed launches of
+// independent FMA chains after one warm-up); synchronises the stream.
+cudaError_t probe_fp64_rate(cudaStream_t s, double* gflops);
 // Launches a kernel whose mbarrier wait cannot complete (bounded by `limit` polls); sets ERR_TIMEOUT
 // in *err.
 cudaError_t launch_wait_timeout_probe(unsigned* err, unsigned limit, cudaStream_t s);

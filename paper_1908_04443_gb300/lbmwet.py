@@ -70,6 +70,7 @@ def _load():
         "lbm_enqueue_steps": (C.c_int, [H, C.c_int64]),
         "lbm_check": (C.c_int, [H]),
         "lbm_selftest_bounded_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
+        "lbm_probe_fp64_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
         "lbm_check_guards": (C.c_int, [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
         "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
@@ -109,7 +110,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
-            "lbm_selftest_bounded_wait", "lbm_check_guards",
+            "lbm_selftest_bounded_wait", "lbm_probe_fp64_rate", "lbm_check_guards",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
             "lbm_step_kernel_used", "lbm_batch_step_kernel_used",
@@ -191,6 +192,13 @@ def lbm_selftest_bounded_wait(polls: int = 1024, stream=None) -> bool:
     t = C.c_int32(0)
     _check(_lib.lbm_selftest_bounded_wait(_stream_ptr(stream), int(polls), C.byref(t)))
     return bool(t.value)
+
+
+def lbm_probe_fp64_rate(stream=None) -> float:
+    """Measured FP64 fused multiply-add rate of the device in GFLOP/s (see the header)."""
+    g = C.c_double(0.0)
+    _check(_lib.lbm_probe_fp64_rate(_stream_ptr(stream), C.byref(g)))
+    return float(g.value)
 
 
 def lbm_check_guards(h) -> Tuple[int, int]:
