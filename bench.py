@@ -530,7 +530,7 @@ def e2e_rate(L, cfgs, masks, rho0s, wls, steps, stream, world=1):
                           "with host rho and u of every instance"}
 
 
-def device_rate(L, torch, stream, name, steps, flush, precision=None, extras=None):
+def device_rate(L, torch, stream, name, steps, flush, precision=None, extras=None, autotune=False):
     """Device-timed MLUPS and HBM-roofline fraction of another workload (same protocol as the
     headline: L2 flushed before each timed step when the state fits in L2, else back-to-back steps
     between one pair of events); `precision` overrides the workload's.  Adds the fluid-only rate,
@@ -555,6 +555,12 @@ def device_rate(L, torch, stream, name, steps, flush, precision=None, extras=Non
     run = Runner(L, cfgs, masks, rho0s, stream)
     nodes = sum(wl.nodes for wl in wls)
     fluid = int(sum(int((m == 0).sum()) for m in masks))
+    tuning = None
+    if autotune and run.batch:
+        report = L.lbm_batch_autotune(run.b, 16)
+        kinds = [L.lbm_batch_instance_kernel(run.b, i) for i in range(len(wls))]
+        tuning = {"report": report.strip().splitlines(),
+                  "instances_per_kernel": {k: kinds.count(k) for k in sorted(set(kinds))}}
     with torch.cuda.stream(stream):
         run.enqueue(3)
     run.step(0)
@@ -594,6 +600,8 @@ def device_rate(L, torch, stream, name, steps, flush, precision=None, extras=Non
            "fluid_only_value": round(fluid / (ms * 1e-3) / 1e6, 1), "achieved_gbs": round(gbs, 1),
            "frac_of_measured_hbm": round(gbs / peak, 4), "frac_of_measured_hbm_fluid_only": round(gbs * fluid / nodes / peak, 4),
            "frac_of_nominal_hbm": round(gbs / NOMINAL_HBM_GBS, 4), "bound": "hbm", "err_vs_oracle": err}
+    if tuning:
+        out["autotune"] = tuning
     out.update(more)
     if precision == "fp64":
         # GB300's FP64 rate is far below its FP32 rate: the FP64 step is bound by the FP64 pipe
@@ -765,7 +773,9 @@ def run_ours(args):
 
         others = {"c3": device_rate(L, torch, stream, "c3", max(100, args.steps), flush, extras=c3_extras),
                   "c4": device_rate(L, torch, stream, "c4", max(50, args.steps), flush, extras=c4_extras),
+                  "c4_autotuned": device_rate(L, torch, stream, "c4", max(50, args.steps), flush, autotune=True),
                   "c2_fp64": device_rate(L, torch, stream, "c2", 10, flush, precision="fp64")}
+        L.lbm_batch_autotune_forget()
 
     # end to end through the public API with host buffers
     torch.cuda.synchronize()

@@ -86,8 +86,10 @@ typedef enum { LBM_BODY_NONE = 0, LBM_BODY_BALL = 1, LBM_BODY_PLANE = 2 } lbm_bo
  *   planned on the host so that every CTA pulls about the same number of rows; bit-identical to
  *   TILE.  PAIR (FP32 only): 32 x 16 tiles, two nodes per thread computed together with packed
  *   FP32x2 instructions; equal to TILE up to FP32 rounding (the operations are regrouped).  AUTO:
- *   PAIR in FP32, TILE in FP64.  A batch uses instance 0's choice.  A y-march handle that records
- *   a trajectory for the adjoint steps with TILE from lbm_record on.
+ *   PAIR in FP32, TILE in FP64.  A batch uses instance 0's choice for every instance, except that
+ *   with AUTO each instance takes the kernel lbm_batch_autotune chose for its size class, where it
+ *   has chosen one.  A y-march handle that records a trajectory for the adjoint steps with TILE
+ *   from lbm_record on.
  * D3Q19 (every kernel marches z-planes through 32-plane chunks of x-y columns):
  *   ZTMA (FP32 only): 32 x 8 columns whose lead plane's 19 pull boxes are staged in shared memory
  *   by TMA, two planes in flight, two cells per thread in packed FP32x2 arithmetic; chunks holding
@@ -319,8 +321,33 @@ lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n);
 lbm_handle* lbm_batch_handle(lbm_batch* b, int32_t i);
 int32_t lbm_batch_size(const lbm_batch* b);
 int64_t lbm_batch_kernel_launches(const lbm_batch* b);
-/* Step kernel of the batch: LBM_KERNEL_TILE, LBM_KERNEL_YMARCH or LBM_KERNEL_PAIR (0 for NULL). */
+/* Step kernel of the batch: LBM_KERNEL_TILE, LBM_KERNEL_YMARCH or LBM_KERNEL_PAIR when every
+ * instance uses the same one, LBM_KERNEL_AUTO when they differ (after lbm_batch_autotune) or for
+ * NULL. */
 int32_t lbm_batch_step_kernel_used(const lbm_batch* b);
+/* Step kernel of instance i (LBM_KERNEL_AUTO if i is out of range). */
+int32_t lbm_batch_instance_kernel(const lbm_batch* b, int32_t i);
+
+/* Autotuner of the batch's kernels (no counterpart in the paper).  Groups the instances by size
+ * class (floor(log2(nodes))) and, for each class, times every candidate on the class's own
+ * instances from their current state: the pair kernel (FP32) with 4, 3 and 2 resident CTAs per
+ * SM, the tile kernel and the y-march, 2 warm-up steps then trial_steps (>= 2, rounded up to even)
+ * steps between CUDA events.  The state is saved before and restored after the trials, so the
+ * simulation is unchanged.  Each class then steps with its fastest candidate; instances of
+ * different choices form groups whose kernels run as parallel branches of the captured steps.
+ * The choices are kept per (device, lattice, precision, size class) for the process: a later
+ * lbm_batch_init with LBM_KERNEL_AUTO uses them.  Synchronises the batch's stream.  Errors:
+ * LBM_ERR_ARG (trial_steps < 2), LBM_ERR_CUDA, LBM_ERR_OOM. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps);
+/* Set the step kernel of every instance (kinds: n entries of LBM_KERNEL_TILE, LBM_KERNEL_YMARCH
+ * or LBM_KERNEL_PAIR, the latter FP32 only), overriding lbm_batch_init's and the autotuner's
+ * choice; instances of different kernels step as parallel groups.  Errors: LBM_ERR_ARG. */
+lbm_status lbm_batch_set_kernels(lbm_batch* b, const int32_t* kinds);
+/* Forget the choices lbm_batch_autotune made for this process (later batches use their defaults). */
+void lbm_batch_autotune_forget(void);
+/* Text report of the last lbm_batch_autotune (one line per class and candidate with its time and
+ * rate, then the choice per class); owned by the batch, "" before any. */
+const char* lbm_batch_tuning_report(const lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 

@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -963,21 +966,33 @@ extern "C" lbm_status lbm_observables_noalloc(lbm_handle* h, const double* rho_d
 // Batches: many grids of one physics stepped by one persistent kernel per time step.
 // ---------------------------------------------------------------------------------------------
 
+// One group of a batch: the instances stepped by one kernel kind, with its own work list.
+struct BatchGroup {
+    int kind = LBM_KERNEL_TILE;        // LBM_KERNEL_PAIR, LBM_KERNEL_TILE or LBM_KERNEL_YMARCH
+    int ctas_per_sm = 0;               // resident CTAs per SM of its persistent grid (0: the kernel's maximum)
+    std::vector<int> members;          // instance indices
+    BatchItem* d_items = nullptr;
+    int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
+    unsigned* d_sched = nullptr;       // pair kernel: tile-claim counters (zero between launches)
+    int n_items = 0, ctas = 1;
+    cudaStream_t side = nullptr;       // its branch of the captured steps (batches of several groups)
+    cudaEvent_t done = nullptr;
+};
+
 struct lbm_batch {
     std::vector<lbm_handle*> inst;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int lat = 0, prec = 0;
+    cudaEvent_t fork = nullptr;
+    int lat = 0, prec = 0, sms = 152, dev = 0;
     DevParams phys{};
     unsigned* d_err = nullptr;
-    unsigned* d_sched = nullptr;       // pair kernel: tile-claim counters (zero between launches)
     BatchInstance* d_insts = nullptr;
-    BatchItem* d_items = nullptr;
-    int* d_begin = nullptr;            // y-march: per-CTA ranges of d_items
     void* d_tmaps = nullptr;           // pair kernel: two TMA tensor maps per instance
-    bool ymarch = false;
-    bool pair = false;                 // FP32 pair kernel (else the tile kernel, unless y-march)
-    int n_items = 0, ctas = 1, cur = 0;
+    std::vector<char> has_map;         // the instance's rows can be addressed by TMA
+    std::vector<BatchGroup> groups;
+    std::string tuning;                // report of the last lbm_batch_autotune
+    int cur = 0;
     int64_t step = 0, launches = 0, nodes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
@@ -1009,15 +1024,35 @@ bool same_physics(const lbm_config& a, const lbm_config& b) {
            a.rho_w_const == b.rho_w_const;
 }
 
-void batch_free(lbm_batch* b) {
+void group_free(BatchGroup& g) {
+    cudaFree(g.d_items);
+    cudaFree(g.d_begin);
+    cudaFree(g.d_sched);
+    if (g.side) cudaStreamDestroy(g.side);
+    if (g.done) cudaEventDestroy(g.done);
+    g.d_items = nullptr;
+    g.d_begin = nullptr;
+    g.d_sched = nullptr;
+    g.side = nullptr;
+    g.done = nullptr;
+}
+
+void invalidate_graphs(lbm_batch* b) {
     for (int i = 0; i < 2; ++i)
-        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+        if (b->graph[i]) {
+            cudaGraphExecDestroy(b->graph[i]);
+            b->graph[i] = nullptr;
+        }
+}
+
+void batch_free(lbm_batch* b) {
+    invalidate_graphs(b);
+    for (BatchGroup& g : b->groups) group_free(g);
+    b->groups.clear();
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->d_err);
-    cudaFree(b->d_sched);
     cudaFree(b->d_insts);
-    cudaFree(b->d_items);
-    cudaFree(b->d_begin);
     cudaFree(b->d_tmaps);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
@@ -1026,41 +1061,146 @@ void batch_free(lbm_batch* b) {
     b->inst.clear();
 }
 
-cudaError_t batch_step_kernel(lbm_batch* b, cudaStream_t s, int parity) {
-    if (b->ymarch) return launch_ymarch(b->prec, parity, b->phys, b->d_items, b->d_begin, b->ctas, s);
-    if (b->pair) return launch_pair_batched(parity, b->phys, b->d_items, b->n_items, b->ctas, b->d_sched, s);
-    return launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, b->d_items, b->n_items, b->ctas, s);
+// Work list of a group: the tiles of its instances (pair kernel: 32 x 16 tiles with the instances'
+// TMA maps; tile kernel: its tiles) or the y-march runs planned over its instances; its persistent
+// grid of sms x ctas_per_sm CTAs (no more than there are items).
+cudaError_t group_build(lbm_batch* b, BatchGroup& g) {
+    std::vector<BatchItem> items;
+    std::vector<int> begin;
+    if (g.kind == LBM_KERNEL_YMARCH) {
+        std::vector<YGrid> grids;
+        for (int i : g.members) {
+            lbm_handle* h = b->inst[i];
+            YGrid yg{h->cfg.nx, h->cfg.ny, h->mask.data(), BatchItem{}};
+            yg.proto.inst = i;
+            yg.proto.f[0] = h->f[0];
+            yg.proto.f[1] = h->f[1];
+            yg.proto.fp = h->dp.fp;
+            yg.proto.fs = int(h->dp.fs);
+            yg.proto.type = h->d_type;
+            yg.proto.wall_id = h->d_wall_id;
+            yg.proto.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
+            yg.proto.kappa = h->dp.kappa;
+            grids.push_back(yg);
+        }
+        const int per_sm = g.ctas_per_sm > 0 ? g.ctas_per_sm : ymarch_ctas_per_sm(b->prec);
+        YPlan plan = plan_ymarch(grids, ymarch_threads(b->prec), b->sms * per_sm);
+        items = std::move(plan.items);
+        begin = std::move(plan.begin);
+        g.ctas = plan.ctas;
+    } else {
+        const bool pair = g.kind == LBM_KERNEL_PAIR;
+        int tx, ty, tz;
+        step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
+        if (pair) pair_tile_shape(&tx, &ty);
+        for (int i : g.members) {
+            lbm_handle* h = b->inst[i];
+            const int nx = h->cfg.nx, ny = h->cfg.ny;
+            for (int y = 0; y < ny; y += ty)
+                for (int x = 0; x < nx; x += tx) {
+                    const size_t t = (size_t)(y / ty) * ((nx + tx - 1) / tx) + x / tx;
+                    BatchItem it{};
+                    it.nx = nx;
+                    it.ny = ny;
+                    it.N = int(h->N);
+                    it.fp = h->dp.fp;
+                    it.fs = int(h->dp.fs);
+                    it.x0 = x;
+                    it.y0 = y;
+                    it.y1 = std::min(y + ty, ny);
+                    it.solid = int(pair ? h->pair_solid[t] : h->tile_solid[t]);
+                    it.inst = i;
+                    it.f[0] = h->f[0];
+                    it.f[1] = h->f[1];
+                    it.type = h->d_type;
+                    it.wall_id = h->d_wall_id;
+                    it.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
+                    it.kappa = h->dp.kappa;
+                    it.tmap = pair && b->has_map[i] ? static_cast<const char*>(b->d_tmaps) + 2 * sizeof(CUtensorMap) * i
+                                                    : nullptr;
+                    items.push_back(it);
+                }
+        }
+        const int max_per_sm = pair ? pair_ctas_per_sm() : batched_ctas_per_sm(b->lat, b->prec);
+        const int per_sm = g.ctas_per_sm > 0 && g.ctas_per_sm < max_per_sm ? g.ctas_per_sm : max_per_sm;
+        const long long cap = (long long)b->sms * per_sm;
+        g.ctas = int((long long)items.size() < cap ? (long long)items.size() : cap);
+    }
+    g.n_items = int(items.size());
+    cudaError_t e = cudaMalloc(&g.d_items, sizeof(BatchItem) * (items.empty() ? 1 : items.size()));
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpyAsync(g.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_YMARCH) e = cudaMalloc(&g.d_begin, sizeof(int) * begin.size());
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_YMARCH)
+        e = cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_PAIR) e = cudaMalloc(&g.d_sched, 2 * sizeof(unsigned));
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_PAIR) e = cudaMemsetAsync(g.d_sched, 0, 2 * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host item vectors go out of scope
+    return e;
+}
+
+cudaError_t group_launch(lbm_batch* b, const BatchGroup& g, cudaStream_t s, int parity) {
+    if (g.kind == LBM_KERNEL_YMARCH) return launch_ymarch(b->prec, parity, b->phys, g.d_items, g.d_begin, g.ctas, s);
+    if (g.kind == LBM_KERNEL_PAIR) return launch_pair_batched(parity, b->phys, g.d_items, g.n_items, g.ctas, g.d_sched, s);
+    return launch_step_batched(b->lat, b->prec, parity, b->phys, b->d_insts, g.d_items, g.n_items, g.ctas, s);
+}
+
+// One time step of every group: in sequence on s, or (fork) as parallel branches joined back into s
+cudaError_t batch_step_groups(lbm_batch* b, cudaStream_t s, int parity, bool fork) {
+    if (!fork || b->groups.size() == 1) {
+        for (const BatchGroup& g : b->groups) {
+            cudaError_t e = group_launch(b, g, s, parity);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (BatchGroup& g : b->groups) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g.side, b->fork, 0);
+        if (e == cudaSuccess) e = group_launch(b, g, g.side, parity);
+        if (e == cudaSuccess) e = cudaEventRecord(g.done, g.side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.done, 0);
+    }
+    return e;
 }
 
 lbm_status batch_launch(lbm_batch* b, cudaStream_t s, int parity) {
-    cudaError_t e = batch_step_kernel(b, s, parity);
+    cudaError_t e = batch_step_groups(b, s, parity, false);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
 lbm_status batch_graph(lbm_batch* b, int parity) {
     if (!b->cap_stream) CKB(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
+    if (b->groups.size() > 1) {
+        if (!b->fork) CKB(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (BatchGroup& g : b->groups) {
+            if (!g.side) CKB(b, cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
+            if (!g.done) CKB(b, cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+        }
+    }
+    cudaGraph_t graph = nullptr;
     CKB(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     int par = parity;
     for (int i = 0; i < GRAPH_STEPS; ++i) {
-        cudaError_t e = batch_step_kernel(b, b->cap_stream, par);
+        cudaError_t e = batch_step_groups(b, b->cap_stream, par, true);
         if (e != cudaSuccess) {
-            cudaStreamEndCapture(b->cap_stream, &g);
-            if (g) cudaGraphDestroy(g);
+            cudaStreamEndCapture(b->cap_stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
             return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         }
         par ^= 1;
     }
-    CKB(b, cudaStreamEndCapture(b->cap_stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&b->graph[parity], g, 0);
-    cudaGraphDestroy(g);
+    CKB(b, cudaStreamEndCapture(b->cap_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&b->graph[parity], graph, 0);
+    cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
 lbm_status batch_enqueue(lbm_batch* b, int64_t n) {
     if (n < 0) return bfail(b, LBM_ERR_ARG, "negative step count");
+    const int64_t per_step = (int64_t)b->groups.size();
     while (n > 0) {
         if (n >= GRAPH_STEPS) {
             if (!b->graph[b->cur]) {
@@ -1070,20 +1210,68 @@ lbm_status batch_enqueue(lbm_batch* b, int64_t n) {
             CKB(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
             n -= GRAPH_STEPS;
             b->step += GRAPH_STEPS;
-            b->launches += GRAPH_STEPS;
+            b->launches += GRAPH_STEPS * per_step;
         } else {
             lbm_status st = batch_launch(b, b->stream, b->cur);
             if (st != LBM_OK) return st;
             b->cur ^= 1;
             n -= 1;
             b->step += 1;
-            b->launches += 1;
+            b->launches += per_step;
         }
     }
     for (lbm_handle* h : b->inst) {
         h->cur = b->cur;
         h->step = b->step;
     }
+    return LBM_OK;
+}
+
+// ---- autotuning of the batch's kernels per grid-size class --------------------------------------
+
+// Size class of an instance: floor(log2(nodes)) (128^2 grids: 14, 512^2: 18).
+int size_class(long long nodes) {
+    int c = 0;
+    while ((2LL << c) <= nodes) ++c;
+    return c;
+}
+
+struct TuneChoice {
+    int kind, ctas_per_sm;
+};
+// chosen kernels per (device, lattice, precision, size class), shared by every batch of the process
+std::map<std::tuple<int, int, int, int>, TuneChoice>& tune_cache() {
+    static std::map<std::tuple<int, int, int, int>, TuneChoice> m;
+    return m;
+}
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+const char* kind_name(int kind) {
+    return kind == LBM_KERNEL_PAIR ? "pair" : (kind == LBM_KERNEL_YMARCH ? "ymarch" : "tile");
+}
+
+// (Re)build the groups from one choice per instance; instances with the same choice share a group.
+lbm_status set_groups(lbm_batch* b, const std::vector<TuneChoice>& choice) {
+    invalidate_graphs(b);
+    CKB(b, cudaStreamSynchronize(b->stream));
+    for (BatchGroup& g : b->groups) group_free(g);
+    b->groups.clear();
+    for (int i = 0; i < (int)b->inst.size(); ++i) {
+        BatchGroup* gp = nullptr;
+        for (BatchGroup& g : b->groups)
+            if (g.kind == choice[i].kind && g.ctas_per_sm == choice[i].ctas_per_sm) gp = &g;
+        if (!gp) {
+            b->groups.emplace_back();
+            gp = &b->groups.back();
+            gp->kind = choice[i].kind;
+            gp->ctas_per_sm = choice[i].ctas_per_sm;
+        }
+        gp->members.push_back(i);
+    }
+    for (BatchGroup& g : b->groups) CKB(b, group_build(b, g));
     return LBM_OK;
 }
 
@@ -1101,6 +1289,10 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             return bfail(nullptr, LBM_ERR_ARG, "instance " + std::to_string(i) + " differs from instance 0 in lattice, "
                                                 "precision or physics (only grid, kappa, body and hint may differ)");
     if (cfgs[0].lattice != LBM_D2Q9) return bfail(nullptr, LBM_ERR_ARG, "batches are implemented for D2Q9");
+    const int kernel = cfgs[0].step_kernel;
+    if (kernel == LBM_KERNEL_PAIR && cfgs[0].precision != LBM_FP32_DEV)
+        return bfail(nullptr, LBM_ERR_ARG, "the pair kernel is for D2Q9 in FP32");
+    if (kernel == LBM_KERNEL_ZTMA) return bfail(nullptr, LBM_ERR_ARG, "the TMA-staged z-march is a D3Q19 kernel");
     lbm_batch* b = new lbm_batch();
     b->stream = static_cast<cudaStream_t>(stream);
     b->lat = cfgs[0].lattice;
@@ -1108,7 +1300,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     for (int i = 0; i < n; ++i) {
         lbm_handle* h = nullptr;
         lbm_config ci = cfgs[i];
-        ci.step_kernel = LBM_KERNEL_TILE;   // the batch plans its own runs; members are not stepped alone
+        ci.step_kernel = LBM_KERNEL_TILE;   // the batch plans its own work; members are not stepped alone
         lbm_status st = lbm_init(&ci, masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
                                  kappas_per_wall ? kappas_per_wall[i] : nullptr, stream, &h);
         if (st != LBM_OK) {
@@ -1121,132 +1313,198 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         b->inst.push_back(h);
         b->nodes += h->N;
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    std::vector<BatchInstance> insts(n);
-    std::vector<BatchItem> items;
-    std::vector<int> begin;
-    b->ymarch = cfgs[0].step_kernel == LBM_KERNEL_YMARCH;
-    b->pair = !b->ymarch && b->prec == LBM_FP32_DEV &&
-              (cfgs[0].step_kernel == LBM_KERNEL_AUTO || cfgs[0].step_kernel == LBM_KERNEL_PAIR);
-    if (b->ymarch) {
-        // y-march runs of every instance, balanced over the resident CTAs
-        std::vector<YGrid> grids;
-        for (int i = 0; i < n; ++i) {
-            lbm_handle* h = b->inst[i];
-            YGrid g{h->cfg.nx, h->cfg.ny, h->mask.data(), BatchItem{}};
-            g.proto.inst = i;
-            g.proto.f[0] = h->f[0];
-            g.proto.f[1] = h->f[1];
-            g.proto.fp = h->dp.fp;
-            g.proto.fs = int(h->dp.fs);
-            g.proto.type = h->d_type;
-            g.proto.wall_id = h->d_wall_id;
-            g.proto.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
-            g.proto.kappa = h->dp.kappa;
-            grids.push_back(g);
-        }
-        YPlan plan = plan_ymarch(grids, ymarch_threads(b->prec), sms * ymarch_ctas_per_sm(b->prec));
-        items = std::move(plan.items);
-        begin = std::move(plan.begin);
-        b->ctas = plan.ctas;
-    } else {
-        int tx, ty, tz;
-        step_tile_shape(b->lat, b->prec, &tx, &ty, &tz);
-        if (b->pair) pair_tile_shape(&tx, &ty);
-        // pair kernel: TMA tensor maps of every instance whose rows TMA can address
-        std::vector<char> has_map(n, 0);
-        if (b->pair) {
-            std::vector<CUtensorMap> maps(2 * (size_t)n);
-            bool any = false;
-            for (int i = 0; i < n; ++i) {
-                lbm_handle* h = b->inst[i];
-                has_map[i] = encode_pair_map(&maps[2 * i], h->f[0], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs) &&
-                             encode_pair_map(&maps[2 * i + 1], h->f[1], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs);
-                any = any || has_map[i];
-            }
-            if (any) {
-                cudaError_t e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size());
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
-                                        cudaMemcpyHostToDevice, b->stream);
-                if (e != cudaSuccess) {
-                    const std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
-                    batch_free(b);
-                    delete b;
-                    return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
-                }
-            }
-        }
-        for (int i = 0; i < n; ++i) {
-            lbm_handle* h = b->inst[i];
-            BatchInstance& d = insts[i];
-            d.nx = h->cfg.nx;
-            d.ny = h->cfg.ny;
-            d.nz = h->cfg.nz;
-            d.N = int(h->N);
-            d.fp = h->dp.fp;
-            d.fs = int(h->dp.fs);
-            d.f[0] = h->f[0];
-            d.f[1] = h->f[1];
-            d.type = h->d_type;
-            d.wall_id = h->d_wall_id;
-            d.kappa_w = h->dp.kappa_w;
-            d.kappa = h->dp.kappa;
-            for (int y = 0; y < d.ny; y += ty)
-                for (int x = 0; x < d.nx; x += tx) {
-                    const size_t t = (size_t)(y / ty) * ((d.nx + tx - 1) / tx) + x / tx;
-                    BatchItem it{};
-                    it.nx = d.nx;
-                    it.ny = d.ny;
-                    it.N = d.N;
-                    it.fp = d.fp;
-                    it.fs = d.fs;
-                    it.x0 = x;
-                    it.y0 = y;
-                    it.y1 = std::min(y + ty, d.ny);
-                    it.solid = int(b->pair ? h->pair_solid[t] : h->tile_solid[t]);
-                    it.inst = i;
-                    it.f[0] = h->f[0];
-                    it.f[1] = h->f[1];
-                    it.type = h->d_type;
-                    it.wall_id = h->d_wall_id;
-                    it.kappa_w = h->d_kappa;   // per wall node always (holds the scalar kappa unless set)
-                    it.kappa = h->dp.kappa;
-                    it.tmap = has_map[i] ? static_cast<const char*>(b->d_tmaps) + 2 * sizeof(CUtensorMap) * i
-                                         : nullptr;
-                    items.push_back(it);
-                }
-        }
-        const long long cap = (long long)sms * (b->pair ? pair_ctas_per_sm() : batched_ctas_per_sm(b->lat, b->prec));
-        b->ctas = int((long long)items.size() < cap ? (long long)items.size() : cap);
-    }
-    b->n_items = int(items.size());
-    b->phys = b->inst[0]->dp;
-    cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sched, 0, 2 * sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
-    if (e == cudaSuccess && b->ymarch) e = cudaMalloc(&b->d_begin, sizeof(int) * begin.size());
-    if (e == cudaSuccess && b->ymarch)
-        e = cudaMemcpyAsync(b->d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) {
+    cudaGetDevice(&b->dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
+    auto setup_fail = [&](cudaError_t e) {
         const std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
         batch_free(b);
         delete b;
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+    };
+    // instance records of the tile kernel, TMA tensor maps of the pair kernel
+    std::vector<BatchInstance> insts(n);
+    b->has_map.assign(n, 0);
+    std::vector<CUtensorMap> maps(2 * (size_t)n);
+    bool any_map = false;
+    for (int i = 0; i < n; ++i) {
+        lbm_handle* h = b->inst[i];
+        BatchInstance& d = insts[i];
+        d.nx = h->cfg.nx;
+        d.ny = h->cfg.ny;
+        d.nz = h->cfg.nz;
+        d.N = int(h->N);
+        d.fp = h->dp.fp;
+        d.fs = int(h->dp.fs);
+        d.f[0] = h->f[0];
+        d.f[1] = h->f[1];
+        d.type = h->d_type;
+        d.wall_id = h->d_wall_id;
+        d.kappa_w = h->dp.kappa_w;
+        d.kappa = h->dp.kappa;
+        if (b->prec == LBM_FP32_DEV) {
+            b->has_map[i] = encode_pair_map(&maps[2 * i], h->f[0], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs) &&
+                            encode_pair_map(&maps[2 * i + 1], h->f[1], h->cfg.nx, h->cfg.ny, h->dp.fp, h->dp.fs);
+            any_map = any_map || b->has_map[i];
+        }
     }
+    cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && any_map) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size());
+    if (e == cudaSuccess && any_map)
+        e = cudaMemcpyAsync(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return setup_fail(e);
+    b->phys = b->inst[0]->dp;
     b->phys.err = b->d_err;
+    // kernels: the one asked for; with AUTO, the choice an earlier lbm_batch_autotune made for each
+    // instance's size class on this device (the pair kernel in FP32, the tile kernel in FP64 where
+    // there is none)
+    const int dflt = kernel == LBM_KERNEL_AUTO ? (b->prec == LBM_FP32_DEV ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE) : kernel;
+    std::vector<TuneChoice> choice(n, TuneChoice{dflt, 0});
+    if (kernel == LBM_KERNEL_AUTO) {
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        for (int i = 0; i < n; ++i) {
+            auto it = tune_cache().find(std::make_tuple(b->dev, b->lat, b->prec, size_class(b->inst[i]->N)));
+            if (it != tune_cache().end()) choice[i] = it->second;
+        }
+    }
+    lbm_status st = set_groups(b, choice);
+    if (st != LBM_OK) {
+        const std::string m = b->err;
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, st, m);
+    }
     *out = b;
     return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
+    NvtxRange nvtx_range("lbm_batch_autotune");
+    if (!b) return LBM_ERR_ARG;
+    if (trial_steps < 2) return bfail(b, LBM_ERR_ARG, "trial_steps must be at least 2");
+    const int trials = trial_steps + (trial_steps & 1);   // even: the state's buffer parity is kept
+    const int n = (int)b->inst.size();
+    // size classes present and their instances
+    std::map<int, std::vector<int>> classes;
+    for (int i = 0; i < n; ++i) classes[size_class(b->inst[i]->N)].push_back(i);
+    // candidates: the pair kernel at 2, 3 and 4 resident CTAs per SM (FP32), the tile kernel, the
+    // y-march
+    std::vector<TuneChoice> cand;
+    if (b->prec == LBM_FP32_DEV)
+        for (int k = pair_ctas_per_sm(); k >= 2; --k) cand.push_back(TuneChoice{LBM_KERNEL_PAIR, k});
+    cand.push_back(TuneChoice{LBM_KERNEL_TILE, 0});
+    cand.push_back(TuneChoice{LBM_KERNEL_YMARCH, 0});
+    CKB(b, cudaStreamSynchronize(b->stream));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    CKB(b, cudaEventCreate(&t0));
+    CKB(b, cudaEventCreate(&t1));
+    std::vector<TuneChoice> choice(n, TuneChoice{b->prec == LBM_FP32_DEV ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE, 0});
+    std::string report;
+    lbm_status result = LBM_OK;
+    for (auto& kv : classes) {
+        const std::vector<int>& mem = kv.second;
+        long long nodes = 0;
+        for (int i : mem) nodes += b->inst[i]->N;
+        // the members' current state, restored after the trials
+        std::vector<void*> saved(mem.size(), nullptr);
+        for (size_t k = 0; k < mem.size() && result == LBM_OK; ++k) {
+            lbm_handle* h = b->inst[mem[k]];
+            cudaError_t e = cudaMallocAsync(&saved[k], h->fbytes, b->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(saved[k], h->f[b->cur], h->fbytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
+        double best = 1e300;
+        TuneChoice pick = choice[mem[0]];
+        for (const TuneChoice& c : cand) {
+            if (result != LBM_OK) break;
+            BatchGroup g;
+            g.kind = c.kind;
+            g.ctas_per_sm = c.ctas_per_sm;
+            g.members = mem;
+            cudaError_t e = group_build(b, g);
+            int par = b->cur;
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k, par ^= 1) e = group_launch(b, g, b->stream, par);
+            if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+            for (int k = 0; k < trials && e == cudaSuccess; ++k, par ^= 1) e = group_launch(b, g, b->stream, par);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            group_free(g);
+            if (e != cudaSuccess) {
+                result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                break;
+            }
+            const double per_step = double(ms) / trials;
+            char line[200];
+            std::snprintf(line, sizeof line, "class 2^%d: %zu instances, %lld nodes, %s x %d per SM: %.5f ms/step (%.1f MLUPS)\n",
+                          kv.first, mem.size(), nodes, kind_name(c.kind), c.ctas_per_sm, per_step,
+                          nodes / (per_step * 1e3));
+            report += line;
+            if (per_step < best) {
+                best = per_step;
+                pick = c;
+            }
+        }
+        // restore the state (the trials ran an even number of steps: the state is in f[cur] again)
+        for (size_t k = 0; k < mem.size(); ++k) {
+            if (!saved[k]) continue;
+            lbm_handle* h = b->inst[mem[k]];
+            if (result == LBM_OK) {
+                cudaError_t e = cudaMemcpyAsync(h->f[b->cur], saved[k], h->fbytes, cudaMemcpyDeviceToDevice, b->stream);
+                if (e != cudaSuccess) result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            }
+            cudaFreeAsync(saved[k], b->stream);
+        }
+        if (result != LBM_OK) break;
+        for (int i : mem) choice[i] = pick;
+        char line[120];
+        std::snprintf(line, sizeof line, "class 2^%d: chosen %s x %d per SM\n", kv.first, kind_name(pick.kind),
+                      pick.ctas_per_sm);
+        report += line;
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        tune_cache()[std::make_tuple(b->dev, b->lat, b->prec, kv.first)] = pick;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (result != LBM_OK) return result;
+    // the trials left their error flags (a fault would have shown in the state): keep them
+    b->tuning = report;
+    return set_groups(b, choice);
+}
+
+const char* lbm_batch_tuning_report(const lbm_batch* b) { return b ? b->tuning.c_str() : ""; }
+
+lbm_status lbm_batch_set_kernels(lbm_batch* b, const int32_t* kinds) {
+    if (!b || !kinds) return LBM_ERR_ARG;
+    std::vector<TuneChoice> choice(b->inst.size());
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const int k = kinds[i];
+        if (k != LBM_KERNEL_TILE && k != LBM_KERNEL_YMARCH && k != LBM_KERNEL_PAIR)
+            return bfail(b, LBM_ERR_ARG, "instance " + std::to_string(i) + ": the kernel must be TILE, YMARCH or PAIR");
+        if (k == LBM_KERNEL_PAIR && b->prec != LBM_FP32_DEV)
+            return bfail(b, LBM_ERR_ARG, "the pair kernel is for FP32");
+        choice[i] = TuneChoice{k, 0};
+    }
+    return set_groups(b, choice);
+}
+
+void lbm_batch_autotune_forget(void) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    tune_cache().clear();
+}
+
+int32_t lbm_batch_instance_kernel(const lbm_batch* b, int32_t i) {
+    if (!b || i < 0 || i >= (int32_t)b->inst.size()) return LBM_KERNEL_AUTO;
+    for (const BatchGroup& g : b->groups)
+        for (int m : g.members)
+            if (m == i) return g.kind;
+    return LBM_KERNEL_AUTO;
 }
 
 lbm_status lbm_batch_enqueue_steps(lbm_batch* b, int64_t n) {
@@ -1287,9 +1545,10 @@ int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->inst.size() 
 int64_t lbm_batch_kernel_launches(const lbm_batch* b) { return b ? b->launches : 0; }
 
 int32_t lbm_batch_step_kernel_used(const lbm_batch* b) {
-    if (!b) return LBM_KERNEL_AUTO;
-    if (b->ymarch) return LBM_KERNEL_YMARCH;
-    return b->pair ? LBM_KERNEL_PAIR : LBM_KERNEL_TILE;
+    if (!b || b->groups.empty()) return LBM_KERNEL_AUTO;
+    for (const BatchGroup& g : b->groups)
+        if (g.kind != b->groups[0].kind) return LBM_KERNEL_AUTO;   // mixed kernels
+    return b->groups[0].kind;
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }

@@ -98,6 +98,11 @@ def _load():
         "lbm_batch_size": (C.c_int32, [C.c_void_p]),
         "lbm_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
         "lbm_batch_step_kernel_used": (C.c_int32, [C.c_void_p]),
+        "lbm_batch_instance_kernel": (C.c_int32, [C.c_void_p, C.c_int32]),
+        "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32]),
+        "lbm_batch_tuning_report": (C.c_char_p, [C.c_void_p]),
+        "lbm_batch_set_kernels": (C.c_int, [C.c_void_p, C.c_void_p]),
+        "lbm_batch_autotune_forget": (None, []),
         "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
         "lbm_batch_destroy": (None, [C.c_void_p]),
     }
@@ -113,7 +118,8 @@ EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step
             "lbm_selftest_bounded_wait", "lbm_probe_fp64_rate", "lbm_check_guards",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
-            "lbm_step_kernel_used", "lbm_batch_step_kernel_used",
+            "lbm_step_kernel_used", "lbm_batch_step_kernel_used", "lbm_batch_instance_kernel", "lbm_batch_autotune",
+            "lbm_batch_tuning_report", "lbm_batch_set_kernels", "lbm_batch_autotune_forget",
             "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_record", "lbm_adjoint", "lbm_batch_init", "lbm_batch_step",
             "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_handle", "lbm_batch_size",
             "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
@@ -365,6 +371,28 @@ def lbm_batch_kernel_launches(b) -> int:
 
 def lbm_batch_step_kernel_used(b) -> str:
     return KERNEL_NAMES[int(_lib.lbm_batch_step_kernel_used(b))]
+
+
+def lbm_batch_instance_kernel(b, i: int) -> str:
+    return KERNEL_NAMES[int(_lib.lbm_batch_instance_kernel(b, int(i)))]
+
+
+def lbm_batch_set_kernels(b, kinds):
+    """Step instance i with kernel kinds[i] ("tile", "ymarch" or "pair")."""
+    names = {"tile": 1, "ymarch": 2, "pair": 3}
+    arr = np.ascontiguousarray([names[k] if isinstance(k, str) else int(k) for k in kinds], dtype=np.int32)
+    _bcheck(_lib.lbm_batch_set_kernels(b, arr.ctypes.data_as(C.c_void_p)), b)
+
+
+def lbm_batch_autotune_forget():
+    _lib.lbm_batch_autotune_forget()
+
+
+def lbm_batch_autotune(b, trial_steps: int = 16) -> str:
+    """Time the candidate kernels per size class and step each class with the fastest (see the
+    header); returns the tuning report."""
+    _bcheck(_lib.lbm_batch_autotune(b, int(trial_steps)), b)
+    return (_lib.lbm_batch_tuning_report(b) or b"").decode()
 
 
 def lbm_batch_destroy(b):
