@@ -18,7 +18,9 @@
  *   - Grids are periodic in every direction; node (x, y, z) has linear index x + nx*(y + ny*z)
  *     (x fastest).  2D lattices use nz = 1.
  *   - Host pointers are read (or written) only during the call; the caller keeps ownership.
- *     Device memory is owned by the handle and freed by lbm_destroy.
+ *     Device memory is owned by the handle and freed by lbm_destroy, into the library's
+ *     stream-ordered memory pool of the device (one per device), which keeps it for the next
+ *     allocation instead of returning it to the driver; lbm_release_cached_memory returns it.
  *   - All device work is enqueued on the caller's CUDA stream given at lbm_init (NULL = the
  *     legacy default stream).  Calls that return host data synchronise that stream.
  *   - Calls return an lbm_status and never abort or throw.  lbm_last_error() gives a message.
@@ -191,6 +193,18 @@ lbm_status lbm_check(lbm_handle* h);
  * up and flagged the timeout (the expected outcome), 0 otherwise.  Synchronises the stream. */
 lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* timed_out);
 
+/* Device memory pool (no counterpart in the paper).  Handles and batches allocate from a
+ * stream-ordered pool per device (cudaMallocFromPoolAsync on their stream) whose release threshold
+ * is unlimited: memory freed by lbm_destroy / lbm_batch_destroy stays reserved for later handles,
+ * so repeated set-ups neither map fresh memory nor synchronise the device per buffer.
+ * lbm_release_cached_memory synchronises the current device (frees pending in streams hold their
+ * memory until then) and returns the unused part of every pool to the driver (memory of live
+ * handles stays).  lbm_memory_stats gives the current device's pool: bytes reserved from the
+ * driver and bytes in use by live allocations.  Errors: LBM_ERR_ARG (NULL argument),
+ * LBM_ERR_CUDA. */
+lbm_status lbm_release_cached_memory(void);
+lbm_status lbm_memory_stats(int64_t* reserved_bytes, int64_t* used_bytes);
+
 /* FP64 rate probe (no counterpart in the paper): the FP64 step kernels are bound by the device's
  * FP64 arithmetic, and their roofline needs its measured rate.  Launches, on `stream` (NULL: the
  * legacy default stream), a grid of 16 CTAs per SM whose threads run eight independent chains of
@@ -305,8 +319,10 @@ lbm_status lbm_adjoint(lbm_handle* h, const double* drho_final_dev, double* dkap
 typedef struct lbm_batch lbm_batch;
 
 /* Create a batch of n >= 1 instances: cfgs[i], masks[i], rho0s[i] (array may be NULL, entries may
- * be NULL) and kappas_per_wall[i] (array or entries may be NULL) as in lbm_init.  Errors as
- * lbm_init, plus LBM_ERR_ARG if the instances' physics differ. */
+ * be NULL) and kappas_per_wall[i] (array or entries may be NULL) as in lbm_init.  The host scans of
+ * the instances' masks (wall lists, tile flags) run in parallel on up to 16 host threads; the
+ * stream is synchronised once for the whole batch.  Errors as lbm_init, plus LBM_ERR_ARG if the
+ * instances' physics differ. */
 lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* const* masks, const double* const* rho0s,
                           const double* const* kappas_per_wall, void* stream, lbm_batch** out);
 /* Advance every instance n steps; reads the batch's device error flag once at the end. */

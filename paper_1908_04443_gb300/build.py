@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbmwet.so")
 OBJ = os.path.join(ROOT, "_build")
 SOURCES = ["step.cu", "step2p.cu", "step2d.cu", "step3d.cu", "step3p.cu", "reduce.cu", "adjoint.cu", "probe.cu", "api.cu",
-           "eos_host.cpp", "plan.cpp", "wall_gf.cpp"]
+           "eos_host.cpp", "plan.cpp", "wall_gf.cpp", "maskscan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXTRA_FLAGS = os.environ.get("LBMWET_NVCC_FLAGS", "").split()   # e.g. tile-shape macros for measurements
 

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@
 #include "eos_host.h"
 #include "kernels.h"
 #include "lattice.cuh"
+#include "maskscan.h"
 #include "plan.h"
 #include "wall_gf.h"
 
@@ -84,35 +86,6 @@ struct lbm_handle {
 };
 
 namespace {
-
-// Per tile of a t[0] x t[1] x t[2] tiling: does a solid node lie within the box of cells the tile
-// touches (the full tile, including cells of a ragged tile that wrap past the grid edge, plus a
-// 3-node halo; no z halo in 2D)?  Tiles without one skip the node-type staging.
-std::vector<uint8_t> tile_solid_flags(const uint8_t* mask, int nx, int ny, int nz, const int t[3], int D) {
-    const int n[3] = {nx, ny, nz};
-    const int tiles[3] = {(nx + t[0] - 1) / t[0], (ny + t[1] - 1) / t[1], (nz + t[2] - 1) / t[2]};
-    const int halo[3] = {3, 3, D == 3 ? 3 : 0};
-    // per axis and coordinate: the tiles whose box (tile + halo, wrapped) covers it
-    std::vector<std::vector<int>> cover[3];
-    for (int d = 0; d < 3; ++d) {
-        cover[d].assign(n[d], {});
-        for (int k = 0; k < tiles[d]; ++k)
-            for (int o = -halo[d]; o < t[d] + halo[d]; ++o) {
-                std::vector<int>& c = cover[d][((k * t[d] + o) % n[d] + n[d]) % n[d]];
-                if (c.empty() || c.back() != k) c.push_back(k);
-            }
-    }
-    std::vector<uint8_t> out((size_t)tiles[0] * tiles[1] * tiles[2], 0);
-    const long long N = (long long)nx * ny * nz;
-    for (long long g = 0; g < N; ++g) {
-        if (!mask[g]) continue;
-        const int x = int(g % nx), y = int((g / nx) % ny), z = int(g / ((long long)nx * ny));
-        for (int kz : cover[2][z])
-            for (int ky : cover[1][y])
-                for (int kx : cover[0][x]) out[((size_t)kz * tiles[1] + ky) * tiles[0] + kx] = 1;
-    }
-    return out;
-}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
@@ -183,6 +156,70 @@ bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
 
 EosHost to_host(const lbm_eos& e) { return EosHost{e.kind, e.a, e.b, e.R, e.T, e.omega}; }
 
+// Device memory of handles and batches comes from one stream-ordered pool per device that keeps
+// freed memory for the next allocation (release threshold: unlimited), so that creating and
+// destroying grids repeatedly costs neither a mapping of fresh memory nor a device-wide
+// synchronisation per buffer (cudaFree has one); lbm_release_cached_memory hands the pool's unused
+// memory back to the driver.  Every allocation is checked to start on a 256-byte boundary (TMA
+// tensor maps and vector loads rely on it).
+std::mutex& pool_mutex() {
+    static std::mutex m;
+    return m;
+}
+std::map<int, cudaMemPool_t>& pools() {
+    static std::map<int, cudaMemPool_t> p;
+    return p;
+}
+
+cudaError_t device_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(pool_mutex());
+    auto it = pools().find(dev);
+    if (it != pools().end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~uint64_t(0);
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+    }
+    pools()[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dmalloc(T** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    void* q = nullptr;
+    e = cudaMallocFromPoolAsync(&q, bytes ? bytes : 1, pool, s);
+    if (e != cudaSuccess) return e;
+    if (reinterpret_cast<uintptr_t>(q) % 256) {
+        cudaFreeAsync(q, s);
+        return cudaErrorInvalidValue;
+    }
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+}
+
+void dfree(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 // Guard zones: the distribution buffers and the observable fields sit between two GUARD-byte
 // zones filled with GUARD_BYTE, so that a kernel writing past either end of one of them leaves a
 // trace that lbm_check_guards finds (a check that needs no memory checker).  GUARD keeps the
@@ -192,42 +229,37 @@ constexpr unsigned char GUARD_BYTE = 0xA5;
 
 cudaError_t guarded_malloc(void** p, size_t bytes, cudaStream_t s) {
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, bytes + 2 * GUARD);
+    cudaError_t e = dmalloc(&base, bytes + 2 * GUARD, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(base, GUARD_BYTE, GUARD, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + GUARD + bytes, GUARD_BYTE, GUARD, s);
     if (e != cudaSuccess) {
-        cudaFree(base);
+        dfree(base, s);
         return e;
     }
     *p = base + GUARD;
     return cudaSuccess;
 }
 
-void guarded_free(void* p) {
-    if (p) cudaFree(static_cast<char*>(p) - GUARD);
+void guarded_free(void* p, cudaStream_t s) {
+    if (p) dfree(static_cast<char*>(p) - GUARD, s);
 }
 
+// (the caller has synchronised the handle's stream: nothing in flight uses these buffers)
 void free_all(lbm_handle* h) {
+    cudaStream_t s = h->stream;
     for (int i = 0; i < 2; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
-        guarded_free(h->f[i]);
+        guarded_free(h->f[i], s);
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    cudaFree(h->d_type);
-    cudaFree(h->d_tile_solid);
-    cudaFree(h->d_pair_solid);
-    cudaFree(h->d_zmaps);
-    cudaFree(h->d_yitems);
-    cudaFree(h->d_ybegin);
-    cudaFree(h->d_wall_id);
-    cudaFree(h->d_kappa);
-    cudaFree(h->d_err);
-    guarded_free(h->d_rho);
-    guarded_free(h->d_u);
-    cudaFree(h->d_partials);
-    cudaFree(h->d_red);
-    for (void* c : h->ckpt) cudaFree(c);
+    for (void* q : {(void*)h->d_type, (void*)h->d_tile_solid, (void*)h->d_pair_solid, h->d_zmaps, (void*)h->d_yitems,
+                    (void*)h->d_ybegin, (void*)h->d_wall_id, (void*)h->d_kappa, (void*)h->d_err, (void*)h->d_partials,
+                    (void*)h->d_red})
+        dfree(q, s);
+    guarded_free(h->d_rho, s);
+    guarded_free(h->d_u, s);
+    for (void* c : h->ckpt) dfree(c, s);
     h->ckpt.clear();
 }
 
@@ -248,8 +280,8 @@ lbm_status check_device_error(lbm_handle* h) {
 lbm_status ensure_obs_buffers(lbm_handle* h) {
     if (!h->d_rho) CK(h, guarded_malloc(reinterpret_cast<void**>(&h->d_rho), sizeof(double) * h->N, h->stream));
     if (!h->d_u) CK(h, guarded_malloc(reinterpret_cast<void**>(&h->d_u), sizeof(double) * h->N * h->D, h->stream));
-    if (!h->d_partials) CK(h, cudaMalloc(&h->d_partials, sizeof(double) * reduce_partials_size(h->N)));
-    if (!h->d_red) CK(h, cudaMalloc(&h->d_red, sizeof(double) * NRED));
+    if (!h->d_partials) CK(h, dmalloc(&h->d_partials, sizeof(double) * reduce_partials_size(h->N), h->stream));
+    if (!h->d_red) CK(h, dmalloc(&h->d_red, sizeof(double) * NRED, h->stream));
     return LBM_OK;
 }
 
@@ -417,12 +449,10 @@ lbm_status lbm_coexistence(const lbm_eos* eos, double* rho_g, double* rho_l) {
     return LBM_OK;
 }
 
-lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0, const double* u0,
-                    const double* kappa_per_wall, void* stream, lbm_handle** out) {
-    NvtxRange nvtx_range("lbm_init");
-    if (!cfg || !solid_mask || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
-    *out = nullptr;
-    const lbm_config& c = *cfg;
+namespace {
+
+// The checks of lbm_init on a configuration (no device work).
+lbm_status validate_config(const lbm_config& c, const double* kappa_per_wall) {
     if (c.lattice != LBM_D2Q9 && c.lattice != LBM_D3Q19) return fail(nullptr, LBM_ERR_ARG, "unknown lattice");
     if (c.precision != LBM_FP64 && c.precision != LBM_FP32_DEV) return fail(nullptr, LBM_ERR_ARG, "unknown precision");
     if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
@@ -457,6 +487,29 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     lbm_status st = lbm_critical_temperature(&c.eos, &tc);
     if (st != LBM_OK) return st;
     if (!(c.eos.T > 0 && c.eos.T < tc)) return fail(nullptr, LBM_ERR_ARG, "temperature must be in (0, Tc)");
+    return LBM_OK;
+}
+
+// The mask scan for a validated configuration: the step kernels' tile shape and, for D2Q9 in FP32,
+// the pair kernel's.
+void scan_for(const lbm_config& c, const uint8_t* solid_mask, int threads, MaskScan* out) {
+    int t[3], tp[2];
+    step_tile_shape(c.lattice, c.precision, &t[0], &t[1], &t[2]);
+    const bool pair = c.lattice == LBM_D2Q9 && c.precision == LBM_FP32_DEV;
+    if (pair) pair_tile_shape(&tp[0], &tp[1]);
+    scan_mask(solid_mask, c.nx, c.ny, c.nz, c.lattice == LBM_D2Q9 ? 2 : 3, t, pair ? tp : nullptr, threads, out);
+}
+
+// lbm_init with the mask scan done by the caller (`pre`, consumed) or here, and with or without the
+// closing stream synchronisation (a batch synchronises once for all its members).
+lbm_status init_impl(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0, const double* u0,
+                     const double* kappa_per_wall, void* stream, lbm_handle** out, MaskScan* pre, bool sync) {
+    if (!cfg || !solid_mask || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    const lbm_config& c = *cfg;
+    lbm_status st = validate_config(c, kappa_per_wall);
+    if (st != LBM_OK) return st;
+    const long long N = (long long)c.nx * c.ny * c.nz;
 
     lbm_handle* h = new lbm_handle();
     h->cfg = c;
@@ -478,34 +531,13 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         return fail(nullptr, LBM_ERR_ARG, "rho_g must be below rho_l");
     }
 
-    // wall nodes: solid nodes with a fluid lattice neighbour (host list, ascending index)
+    // wall nodes (solid nodes with a fluid lattice neighbour, ascending index) and tile flags
     const int nx = c.nx, ny = c.ny, nz = c.nz;
-    std::vector<int> wall_id(N, -1);
-    long long nfluid = 0;
-    {
-        static const int E2[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
-                                     {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
-        static const int E3[19][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
-                                      {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
-                                      {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-        const int Q = h->Q;
-        const int(*E)[3] = h->D == 2 ? E2 : E3;
-        for (long long g = 0; g < N; ++g) {
-            if (!solid_mask[g]) {
-                ++nfluid;
-                continue;
-            }
-            const int x = int(g % nx), y = int((g / nx) % ny), z = int(g / ((long long)nx * ny));
-            for (int a = 1; a < Q; ++a) {
-                const int sx = (x + E[a][0] + nx) % nx, sy = (y + E[a][1] + ny) % ny, sz = (z + E[a][2] + nz) % nz;
-                if (!solid_mask[((long long)sz * ny + sy) * nx + sx]) {
-                    wall_id[g] = int(h->wall_nodes.size());
-                    h->wall_nodes.push_back(g);
-                    break;
-                }
-            }
-        }
-    }
+    MaskScan local;
+    MaskScan& ms = pre ? *pre : local;
+    if (!pre) scan_for(c, solid_mask, scan_threads(N), &ms);
+    const long long nfluid = ms.nfluid;
+    h->wall_nodes.swap(ms.wall_nodes);
     if (nfluid == 0) {
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "the grid has no fluid node");
@@ -531,12 +563,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             h->int_tile[k] = t[k];
             h->tiles[k] = (n3[k] + t[k] - 1) / t[k];
         }
-        h->tile_solid = tile_solid_flags(solid_mask, nx, ny, nz, t, h->D);
-        if (h->D == 2 && c.precision == LBM_FP32_DEV) {
-            int tp[3] = {1, 1, 1};
-            pair_tile_shape(&tp[0], &tp[1]);
-            h->pair_solid = tile_solid_flags(solid_mask, nx, ny, nz, tp, 2);
-        }
+        h->tile_solid.swap(ms.tile_solid);
+        h->pair_solid.swap(ms.pair_solid);
     }
 
     const size_t ssize = c.precision == LBM_FP64 ? sizeof(double) : sizeof(float);
@@ -557,18 +585,19 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     if ((e = (call)) != cudaSuccess) return oom(e, what)
     CKI(guarded_malloc(&h->f[0], h->fbytes, h->stream), "cudaMalloc f");
     CKI(guarded_malloc(&h->f[1], h->fbytes, h->stream), "cudaMalloc f");
-    CKI(cudaMalloc(&h->d_type, N), "cudaMalloc type");
-    CKI(cudaMalloc(&h->d_tile_solid, h->tile_solid.size()), "cudaMalloc tile flags");
+    CKI(dmalloc(&h->d_type, N, h->stream), "cudaMalloc type");
+    CKI(dmalloc(&h->d_tile_solid, h->tile_solid.size(), h->stream), "cudaMalloc tile flags");
     CKI(cudaMemcpyAsync(h->d_tile_solid, h->tile_solid.data(), h->tile_solid.size(), cudaMemcpyHostToDevice, h->stream),
         "copy tile flags");
-    CKI(cudaMalloc(&h->d_wall_id, sizeof(int) * N), "cudaMalloc wall_id");
-    CKI(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc err");
+    CKI(dmalloc(&h->d_wall_id, sizeof(int) * N, h->stream), "cudaMalloc wall_id");
+    CKI(dmalloc(&h->d_err, sizeof(unsigned), h->stream), "cudaMalloc err");
     const size_t nw = h->wall_nodes.size();
-    CKI(cudaMalloc(&h->d_kappa, sizeof(double) * (gf ? gf_table.size() : (nw ? nw : 1))), "cudaMalloc kappa");
+    CKI(dmalloc(&h->d_kappa, sizeof(double) * (gf ? gf_table.size() : (nw ? nw : 1)), h->stream), "cudaMalloc kappa");
     CKI(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "memset err");
     CKI(cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream), "memset f");   // padding included
     CKI(cudaMemsetAsync(h->f[1], 0, h->fbytes, h->stream), "memset f");
-    CKI(cudaMemcpyAsync(h->d_wall_id, wall_id.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream), "copy wall_id");
+    CKI(cudaMemcpyAsync(h->d_wall_id, ms.wall_id.get(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream),
+        "copy wall_id");
     {
         std::vector<double> kap(nw ? nw : 1, c.kappa);
         if (kappa_per_wall)
@@ -582,10 +611,10 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     // synchronisation for its allocation and release)
     {
         uint8_t* d_mask = nullptr;
-        CKI(cudaMallocAsync(reinterpret_cast<void**>(&d_mask), N, h->stream), "cudaMalloc mask");
+        CKI(dmalloc(&d_mask, N, h->stream), "cudaMalloc mask");
         e = cudaMemcpyAsync(d_mask, solid_mask, N, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = launch_classify(h->lat, d_mask, h->d_type, nx, ny, nz, h->stream);
-        cudaFreeAsync(d_mask, h->stream);
+        dfree(d_mask, h->stream);
         if (e != cudaSuccess) return oom(e, "classify");
         h->launches += 1;
     }
@@ -639,9 +668,9 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         ztma_box_dims(&bx, &by);
         CUtensorMap maps[2];
         if (encode_z_map(&maps[0], h->f[0], nx, ny, nz, bx, by) && encode_z_map(&maps[1], h->f[1], nx, ny, nz, bx, by)) {
-            CKI(cudaMalloc(&h->d_zmaps, sizeof(maps)), "cudaMalloc tensor maps");
+            CKI(dmalloc(&h->d_zmaps, sizeof(maps), h->stream), "cudaMalloc tensor maps");
+            // (from pageable memory: staged before the call returns, so `maps` may go out of scope)
             CKI(cudaMemcpyAsync(h->d_zmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, h->stream), "copy tensor maps");
-            CKI(cudaStreamSynchronize(h->stream), "sync");
             p.ztmap = h->d_zmaps;
         }
     }
@@ -650,7 +679,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     {
         double* d_rho0 = nullptr;
         double* d_u0 = nullptr;
-        CKI(cudaMallocAsync(reinterpret_cast<void**>(&d_rho0), sizeof(double) * N, h->stream), "cudaMalloc rho0");
+        CKI(dmalloc(&d_rho0, sizeof(double) * N, h->stream), "cudaMalloc rho0");
         std::vector<double> r0;
         const double* src = rho0;
         if (!rho0) {
@@ -659,14 +688,14 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         }
         e = cudaMemcpyAsync(d_rho0, src, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess && u0) {
-            e = cudaMallocAsync(reinterpret_cast<void**>(&d_u0), sizeof(double) * N * h->D, h->stream);
+            e = dmalloc(&d_u0, sizeof(double) * N * h->D, h->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_u0, u0, sizeof(double) * N * h->D, cudaMemcpyHostToDevice, h->stream);
         }
         if (e == cudaSuccess) e = launch_init(h->lat, h->prec, h->f[0], p, d_rho0, d_u0, h->stream);
-        cudaFreeAsync(d_rho0, h->stream);
-        if (d_u0) cudaFreeAsync(d_u0, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dfree(d_rho0, h->stream);
+        dfree(d_u0, h->stream);
+        if (e == cudaSuccess && sync) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return oom(e, "initial state");
         h->launches += 1;
     }
@@ -687,8 +716,8 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
             grid.proto.kappa_w = h->d_kappa;   // holds the scalar kappa at every wall node unless set per node
             grid.proto.kappa = c.kappa;
             const YPlan plan = plan_ymarch({grid}, ymarch_threads(h->prec), sms * ymarch_ctas_per_sm(h->prec));
-            CKI(cudaMalloc(&h->d_yitems, sizeof(BatchItem) * plan.items.size()), "cudaMalloc runs");
-            CKI(cudaMalloc(&h->d_ybegin, sizeof(int) * plan.begin.size()), "cudaMalloc runs");
+            CKI(dmalloc(&h->d_yitems, sizeof(BatchItem) * plan.items.size(), h->stream), "cudaMalloc runs");
+            CKI(dmalloc(&h->d_ybegin, sizeof(int) * plan.begin.size(), h->stream), "cudaMalloc runs");
             CKI(cudaMemcpyAsync(h->d_yitems, plan.items.data(), sizeof(BatchItem) * plan.items.size(),
                                 cudaMemcpyHostToDevice, h->stream), "copy runs");
             CKI(cudaMemcpyAsync(h->d_ybegin, plan.begin.data(), sizeof(int) * plan.begin.size(),
@@ -699,7 +728,7 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
         }
         // FP32: the pair kernel unless the tile kernel (or the y-march) was asked for
         if (c.precision == LBM_FP32_DEV && (c.step_kernel == LBM_KERNEL_AUTO || c.step_kernel == LBM_KERNEL_PAIR)) {
-            CKI(cudaMalloc(&h->d_pair_solid, h->pair_solid.size()), "cudaMalloc tile flags");
+            CKI(dmalloc(&h->d_pair_solid, h->pair_solid.size(), h->stream), "cudaMalloc tile flags");
             CKI(cudaMemcpyAsync(h->d_pair_solid, h->pair_solid.data(), h->pair_solid.size(), cudaMemcpyHostToDevice,
                                 h->stream),
                 "copy tile flags");
@@ -711,6 +740,14 @@ lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const doub
     h->step = 0;
     *out = h;
     return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_init(const lbm_config* cfg, const uint8_t* solid_mask, const double* rho0, const double* u0,
+                    const double* kappa_per_wall, void* stream, lbm_handle** out) {
+    NvtxRange nvtx_range("lbm_init");
+    return init_impl(cfg, solid_mask, rho0, u0, kappa_per_wall, stream, out, nullptr, true);
 }
 
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
@@ -741,14 +778,41 @@ lbm_status lbm_selftest_bounded_wait(void* stream, uint32_t polls, int32_t* time
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned* d_flag = nullptr;
     unsigned flag = 0;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_flag), sizeof(unsigned), s);
+    cudaError_t e = dmalloc(&d_flag, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_wait_timeout_probe(d_flag, polls, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    if (d_flag) cudaFreeAsync(d_flag, s);
+    dfree(d_flag, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait self-test");
     *timed_out = (flag & ERR_TIMEOUT) ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_release_cached_memory(void) {
+    // frees still pending in streams hold their memory until the streams reach them
+    const cudaError_t es = cudaDeviceSynchronize();
+    if (es != cudaSuccess) return cuda_fail(nullptr, es, "synchronising before trimming the memory pool");
+    std::lock_guard<std::mutex> lock(pool_mutex());
+    for (auto& kv : pools()) {
+        const cudaError_t e = cudaMemPoolTrimTo(kv.second, 0);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "trimming the device memory pool");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_memory_stats(int64_t* reserved_bytes, int64_t* used_bytes) {
+    if (!reserved_bytes || !used_bytes) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *reserved_bytes = 0;
+    *used_bytes = 0;
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(&pool);
+    uint64_t r = 0, u = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "memory pool statistics");
+    *reserved_bytes = int64_t(r);
+    *used_bytes = int64_t(u);
     return LBM_OK;
 }
 
@@ -839,12 +903,12 @@ lbm_status lbm_wall_nodes(const lbm_handle* h, int64_t* idx_out, int64_t* count)
 lbm_status lbm_get_state(lbm_handle* h, double* f_host) {
     if (!h || !f_host) return LBM_ERR_ARG;
     double* d = nullptr;
-    CK(h, cudaMalloc(&d, sizeof(double) * h->Q * h->N));
+    CK(h, dmalloc(&d, sizeof(double) * h->Q * h->N, h->stream));
     cudaError_t e = launch_get_state(h->lat, h->prec, h->f[h->cur], h->dp, d, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f_host, d, sizeof(double) * h->Q * h->N, cudaMemcpyDeviceToHost, h->stream);
+    dfree(d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
     h->launches += 1;
     return LBM_OK;
@@ -853,11 +917,11 @@ lbm_status lbm_get_state(lbm_handle* h, double* f_host) {
 lbm_status lbm_set_state(lbm_handle* h, const double* f_host, int64_t step) {
     if (!h || !f_host) return LBM_ERR_ARG;
     double* d = nullptr;
-    CK(h, cudaMalloc(&d, sizeof(double) * h->Q * h->N));
+    CK(h, dmalloc(&d, sizeof(double) * h->Q * h->N, h->stream));
     cudaError_t e = cudaMemcpyAsync(d, f_host, sizeof(double) * h->Q * h->N, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = launch_set_state(h->lat, h->prec, h->f[h->cur], h->dp, d, h->stream);
+    dfree(d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
     h->launches += 1;
     h->step = step;
@@ -1024,10 +1088,11 @@ bool same_physics(const lbm_config& a, const lbm_config& b) {
            a.rho_w_const == b.rho_w_const;
 }
 
-void group_free(BatchGroup& g) {
-    cudaFree(g.d_items);
-    cudaFree(g.d_begin);
-    cudaFree(g.d_sched);
+// (stream-ordered frees on the batch's stream, behind every launch that reads the lists)
+void group_free(BatchGroup& g, cudaStream_t s) {
+    dfree(g.d_items, s);
+    dfree(g.d_begin, s);
+    dfree(g.d_sched, s);
     if (g.side) cudaStreamDestroy(g.side);
     if (g.done) cudaEventDestroy(g.done);
     g.d_items = nullptr;
@@ -1047,13 +1112,13 @@ void invalidate_graphs(lbm_batch* b) {
 
 void batch_free(lbm_batch* b) {
     invalidate_graphs(b);
-    for (BatchGroup& g : b->groups) group_free(g);
+    for (BatchGroup& g : b->groups) group_free(g, b->stream);
     b->groups.clear();
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->fork) cudaEventDestroy(b->fork);
-    cudaFree(b->d_err);
-    cudaFree(b->d_insts);
-    cudaFree(b->d_tmaps);
+    dfree(b->d_err, b->stream);
+    dfree(b->d_insts, b->stream);
+    dfree(b->d_tmaps, b->stream);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -1127,13 +1192,13 @@ cudaError_t group_build(lbm_batch* b, BatchGroup& g) {
         g.ctas = int((long long)items.size() < cap ? (long long)items.size() : cap);
     }
     g.n_items = int(items.size());
-    cudaError_t e = cudaMalloc(&g.d_items, sizeof(BatchItem) * (items.empty() ? 1 : items.size()));
+    cudaError_t e = dmalloc(&g.d_items, sizeof(BatchItem) * (items.empty() ? 1 : items.size()), b->stream);
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpyAsync(g.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && g.kind == LBM_KERNEL_YMARCH) e = cudaMalloc(&g.d_begin, sizeof(int) * begin.size());
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_YMARCH) e = dmalloc(&g.d_begin, sizeof(int) * begin.size(), b->stream);
     if (e == cudaSuccess && g.kind == LBM_KERNEL_YMARCH)
         e = cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && g.kind == LBM_KERNEL_PAIR) e = cudaMalloc(&g.d_sched, 2 * sizeof(unsigned));
+    if (e == cudaSuccess && g.kind == LBM_KERNEL_PAIR) e = dmalloc(&g.d_sched, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess && g.kind == LBM_KERNEL_PAIR) e = cudaMemsetAsync(g.d_sched, 0, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host item vectors go out of scope
     return e;
@@ -1257,7 +1322,7 @@ const char* kind_name(int kind) {
 lbm_status set_groups(lbm_batch* b, const std::vector<TuneChoice>& choice) {
     invalidate_graphs(b);
     CKB(b, cudaStreamSynchronize(b->stream));
-    for (BatchGroup& g : b->groups) group_free(g);
+    for (BatchGroup& g : b->groups) group_free(g, b->stream);
     b->groups.clear();
     for (int i = 0; i < (int)b->inst.size(); ++i) {
         BatchGroup* gp = nullptr;
@@ -1293,6 +1358,17 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
     if (kernel == LBM_KERNEL_PAIR && cfgs[0].precision != LBM_FP32_DEV)
         return bfail(nullptr, LBM_ERR_ARG, "the pair kernel is for D2Q9 in FP32");
     if (kernel == LBM_KERNEL_ZTMA) return bfail(nullptr, LBM_ERR_ARG, "the TMA-staged z-march is a D3Q19 kernel");
+    // host set-up first: every configuration checked, then the members' mask scans spread over the
+    // host's cores (one grid per thread), then the device set-up of each member without a
+    // synchronisation of its own (one for the batch below)
+    for (int i = 0; i < n; ++i) {
+        if (!masks[i]) return bfail(nullptr, LBM_ERR_ARG, "instance " + std::to_string(i) + ": null mask");
+        lbm_status st = validate_config(cfgs[i], kappas_per_wall ? kappas_per_wall[i] : nullptr);
+        if (st != LBM_OK) return bfail(nullptr, st, "instance " + std::to_string(i) + ": " + g_init_error);
+    }
+    std::vector<MaskScan> scans(n);
+    parallel_for(n, int(std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()))),
+                 [&](int i) { scan_for(cfgs[i], masks[i], 1, &scans[i]); });
     lbm_batch* b = new lbm_batch();
     b->stream = static_cast<cudaStream_t>(stream);
     b->lat = cfgs[0].lattice;
@@ -1301,8 +1377,9 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
         lbm_handle* h = nullptr;
         lbm_config ci = cfgs[i];
         ci.step_kernel = LBM_KERNEL_TILE;   // the batch plans its own work; members are not stepped alone
-        lbm_status st = lbm_init(&ci, masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
-                                 kappas_per_wall ? kappas_per_wall[i] : nullptr, stream, &h);
+        lbm_status st = init_impl(&ci, masks[i], rho0s ? rho0s[i] : nullptr, nullptr,
+                                  kappas_per_wall ? kappas_per_wall[i] : nullptr, stream, &h, &scans[i], false);
+        scans[i] = MaskScan();
         if (st != LBM_OK) {
             const std::string m = "instance " + std::to_string(i) + ": " + g_init_error;
             batch_free(b);
@@ -1347,12 +1424,12 @@ lbm_status lbm_batch_init(int32_t n, const lbm_config* cfgs, const uint8_t* cons
             any_map = any_map || b->has_map[i];
         }
     }
-    cudaError_t e = cudaMalloc(&b->d_err, sizeof(unsigned));
+    cudaError_t e = dmalloc(&b->d_err, sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInstance) * n);
+    if (e == cudaSuccess) e = dmalloc(&b->d_insts, sizeof(BatchInstance) * n, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && any_map) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size());
+    if (e == cudaSuccess && any_map) e = dmalloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size(), b->stream);
     if (e == cudaSuccess && any_map)
         e = cudaMemcpyAsync(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                             b->stream);
@@ -1414,7 +1491,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
         std::vector<void*> saved(mem.size(), nullptr);
         for (size_t k = 0; k < mem.size() && result == LBM_OK; ++k) {
             lbm_handle* h = b->inst[mem[k]];
-            cudaError_t e = cudaMallocAsync(&saved[k], h->fbytes, b->stream);
+            cudaError_t e = dmalloc(&saved[k], h->fbytes, b->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(saved[k], h->f[b->cur], h->fbytes, cudaMemcpyDeviceToDevice, b->stream);
             if (e != cudaSuccess) result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
         }
@@ -1435,7 +1512,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
             if (e == cudaSuccess) e = cudaEventSynchronize(t1);
             float ms = 0.0f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-            group_free(g);
+            group_free(g, b->stream);
             if (e != cudaSuccess) {
                 result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
                 break;
@@ -1459,7 +1536,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
                 cudaError_t e = cudaMemcpyAsync(h->f[b->cur], saved[k], h->fbytes, cudaMemcpyDeviceToDevice, b->stream);
                 if (e != cudaSuccess) result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
             }
-            cudaFreeAsync(saved[k], b->stream);
+            dfree(saved[k], b->stream);
         }
         if (result != LBM_OK) break;
         for (int i : mem) choice[i] = pick;
@@ -1585,13 +1662,13 @@ extern "C" lbm_status lbm_record(lbm_handle* h, int64_t n_steps, int64_t ckpt_ev
                 h->graph[i] = nullptr;
             }
     }
-    for (void* c : h->ckpt) cudaFree(c);
+    for (void* c : h->ckpt) dfree(c, h->stream);
     h->ckpt.clear();
     h->rec_steps = 0;
     const int64_t nck = (n_steps + ckpt_every - 1) / ckpt_every;
     for (int64_t c = 0; c < nck; ++c) {
         void* buf = nullptr;
-        CK(h, cudaMalloc(&buf, h->fbytes));
+        CK(h, dmalloc(&buf, h->fbytes, h->stream));
         h->ckpt.push_back(buf);
         CK(h, cudaMemcpyAsync(buf, h->f[h->cur], h->fbytes, cudaMemcpyDeviceToDevice, h->stream));
         const int64_t len = std::min(ckpt_every, n_steps - c * ckpt_every);

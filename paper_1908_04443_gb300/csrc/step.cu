@@ -552,16 +552,26 @@ __device__ __forceinline__ double feq_a(int a, double rho, double ux, double uy,
     return L::w(a) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
 }
 
+// (32-bit division: a grid holds fewer than 2^31 / 19 nodes, checked at initialisation)
 __device__ __forceinline__ void coords(long long g, int nx, int ny, int& x, int& y, int& z) {
-    x = int(g % nx);
-    const long long t = g / nx;
-    y = int(t % ny);
-    z = int(t / ny);
+    const unsigned u = unsigned(g), t = u / unsigned(nx);
+    x = int(u - t * unsigned(nx));
+    y = int(t % unsigned(ny));
+    z = int(t / unsigned(ny));
 }
 
 // Stored f* whose pull gives f_post: f*_b(y) = f_post_b(y + e_b) if y + e_b is fluid, else
 // f_post_bbar(y) (the inverse of the pull with bounce-back).  Source is either f^eq(rho0, u0) or
 // explicit post-streaming values.
+template <class L>
+constexpr bool opposite_weights_equal() {
+    for (int a = 0; a < L::Q; ++a)
+        if (L::w(a) != L::w(L::opp(a))) return false;
+    return true;
+}
+static_assert(opposite_weights_equal<D2Q9>() && opposite_weights_equal<D3Q19>(),
+              "the initial state takes w_b for the weight of the opposite direction");
+
 template <class L, class S, bool FROM_FEQ>
 __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double* __restrict__ src0,
                                 const double* __restrict__ src1) {
@@ -575,28 +585,28 @@ __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double*
             for (int b = 0; b < Q; ++b) fout[b * fs + fg] = S(0);
             continue;
         }
+        // (unrolled: every lattice constant is a compile-time value; a runtime-indexed weight table
+        // would sit in local memory)
+#pragma unroll
         for (int b = 0; b < Q; ++b) {
             const int tx = wrap1(x + L::ex(b), p.nx), ty = wrap1(y + L::ey(b), p.ny);
             const int tz = (L::D == 3) ? wrap1(z + L::ez(b), p.nz) : 0;
             const long long t = ((long long)tz * p.ny + ty) * p.nx + tx;
-            long long src;
-            int a;
-            if (!(p.type[t] & T_SOLID)) {
-                src = t;
-                a = b;
-            } else {
-                src = g;
-                a = L::opp(b);
-            }
+            const bool bounce = (p.type[t] & T_SOLID) != 0;
+            const long long src = bounce ? g : t;
             double v;
-            if (FROM_FEQ) {
+            if (FROM_FEQ && src1 == nullptr) {
+                // u0 = 0: every velocity term of the bracket is an exact zero, so this is feq_a's
+                // value bit for bit (w of the opposite direction equals w_b)
+                v = L::w(b) * src0[src];
+            } else if (FROM_FEQ) {
                 const double* rho0 = src0;
                 const double* u0 = src1;
-                const double ux = u0 ? u0[src] : 0.0, uy = u0 ? u0[N + src] : 0.0;
-                const double uz = (u0 && L::D == 3) ? u0[2 * N + src] : 0.0;
-                v = feq_a<L>(a, rho0[src], ux, uy, uz);
+                const double ux = u0[src], uy = u0[N + src];
+                const double uz = L::D == 3 ? u0[2 * N + src] : 0.0;
+                v = bounce ? feq_a<L>(L::opp(b), rho0[src], ux, uy, uz) : feq_a<L>(b, rho0[src], ux, uy, uz);
             } else {
-                v = src0[(long long)a * N + src];
+                v = src0[(long long)(bounce ? L::opp(b) : b) * N + src];
             }
             fout[b * fs + fg] = S(v - L::w(b) * p.rho_ref);
         }
@@ -647,17 +657,24 @@ __global__ void classify_kernel(const uint8_t* __restrict__ mask, uint8_t* __res
                 }
             }
         }
-        // within Euclidean distance 3 of a solid node
+        // within Euclidean distance 3 of a solid node (wrapped offsets computed once per axis)
         bool near = false;
         const int rz = (L::D == 3) ? 3 : 0;
+        int wx[7], wy[7], wz[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+            wx[d] = wrap_full(x + d - 3, nx);
+            wy[d] = wrap_full(y + d - 3, ny);
+            wz[d] = (L::D == 3) ? wrap_full(z + d - 3, nz) : 0;
+        }
         for (int dz = -rz; dz <= rz && !near; ++dz)
-            for (int dy = -3; dy <= 3 && !near; ++dy)
+            for (int dy = -3; dy <= 3 && !near; ++dy) {
+                const uint8_t* row = mask + ((long long)wz[dz + 3] * ny + wy[dy + 3]) * nx;
                 for (int dx = -3; dx <= 3 && !near; ++dx) {
                     if (dx * dx + dy * dy + dz * dz > 9) continue;
-                    const int sx = wrap_full(x + dx, nx), sy = wrap_full(y + dy, ny);
-                    const int sz = (L::D == 3) ? wrap_full(z + dz, nz) : 0;
-                    if (mask[((long long)sz * ny + sy) * nx + sx]) near = true;
+                    if (row[wx[dx + 3]]) near = true;
                 }
+            }
         if (near) t |= T_NEARWALL;
         if (!solid) {
             bool bulk = true;

@@ -71,6 +71,8 @@ def _load():
         "lbm_check": (C.c_int, [H]),
         "lbm_selftest_bounded_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
         "lbm_probe_fp64_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+        "lbm_release_cached_memory": (C.c_int, []),
+        "lbm_memory_stats": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_check_guards": (C.c_int, [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_observables": (C.c_int, [H, C.POINTER(lbm_obs), C.c_void_p, C.c_void_p]),
         "lbm_fields_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
@@ -115,7 +117,8 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step", "lbm_enqueue_steps", "lbm_check",
-            "lbm_selftest_bounded_wait", "lbm_probe_fp64_rate", "lbm_check_guards",
+            "lbm_selftest_bounded_wait", "lbm_probe_fp64_rate", "lbm_release_cached_memory", "lbm_memory_stats",
+            "lbm_check_guards",
             "lbm_observables", "lbm_fields_device", "lbm_observables_noalloc", "lbm_wall_nodes", "lbm_get_state", "lbm_set_state",
             "lbm_save_state", "lbm_load_state", "lbm_set_kappa", "lbm_limiter_bounds", "lbm_kernel_launches",
             "lbm_step_kernel_used", "lbm_batch_step_kernel_used", "lbm_batch_instance_kernel", "lbm_batch_autotune",
@@ -133,6 +136,15 @@ def _check(status: int, handle=None):
     if status != LBM_OK:
         msg = _lib.lbm_last_error(handle)
         raise LbmError(status, (msg or b"").decode() or _lib.lbm_status_string(status).decode())
+
+
+def _mask_bytes(m) -> np.ndarray:
+    """A solid mask as the C ABI takes it (one byte per node, nonzero = solid): a C-contiguous uint8
+    array passes through uncopied, anything else is converted."""
+    a = np.asarray(m).reshape(-1)
+    if a.dtype == np.uint8 and a.flags.c_contiguous:
+        return a
+    return (a != 0).astype(np.uint8)
 
 
 def _ptr(a: Optional[np.ndarray], dtype):
@@ -166,7 +178,7 @@ def lbm_critical_temperature(eos: lbm_eos) -> float:
 
 def lbm_init(cfg: lbm_config, solid_mask: np.ndarray, rho0=None, u0=None, kappa_per_wall=None, stream=None):
     n = cfg.nx * cfg.ny * cfg.nz
-    mask, pm = _ptr(np.asarray(solid_mask).reshape(-1) != 0, np.uint8)
+    mask, pm = _ptr(_mask_bytes(solid_mask), np.uint8)
     if mask.size != n:
         raise ValueError("solid_mask size does not match the grid")
     r, pr = _ptr(None if rho0 is None else np.asarray(rho0).reshape(-1), np.float64)
@@ -205,6 +217,18 @@ def lbm_probe_fp64_rate(stream=None) -> float:
     g = C.c_double(0.0)
     _check(_lib.lbm_probe_fp64_rate(_stream_ptr(stream), C.byref(g)))
     return float(g.value)
+
+
+def lbm_release_cached_memory() -> None:
+    """Return the unused memory of the library's device memory pools to the driver."""
+    _check(_lib.lbm_release_cached_memory())
+
+
+def lbm_memory_stats() -> Tuple[int, int]:
+    """(bytes reserved, bytes in use) of the current device's memory pool."""
+    r, u = C.c_int64(0), C.c_int64(0)
+    _check(_lib.lbm_memory_stats(C.byref(r), C.byref(u)))
+    return int(r.value), int(u.value)
 
 
 def lbm_check_guards(h) -> Tuple[int, int]:
@@ -331,7 +355,7 @@ def lbm_batch_init(cfgs, masks, rho0s=None, kappas_per_wall=None, stream=None):
                 out[i] = x.ctypes.data
         return out
 
-    pm = ptrs([np.asarray(m).reshape(-1) != 0 for m in masks], np.uint8)
+    pm = ptrs([_mask_bytes(m) for m in masks], np.uint8)
     pr = ptrs(rho0s, np.float64)
     pk = ptrs(kappas_per_wall, np.float64)
     b = C.c_void_p()
