@@ -44,8 +44,10 @@ UNIT = "MLUPS"
 # of the kernel sources: when the sources change the figure is stale and reported as null.
 NCU_TRAFFIC = {
     # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
-    # one launch (214,332,672 + 157,231,872 bytes)
-    ("c2", "fp32", "ed013185aff0a47f"): 371564544,
+    # one launch (214,298,112 + 160,227,072 bytes)
+    ("c2", "fp32", "e78f2b8f22cd8a98"): 374525184,
+    # ztma_step, 256^3 sphere: one launch (1,644,406,016 + 1,217,767,168 bytes)
+    ("c3", "fp32", "062444ad6ec36c6c"): 2862173184,
 }
 
 
@@ -54,7 +56,7 @@ NCU_TRAFFIC = {
 # instructions of one launch) / nodes = (2 x 478,996,920 + 503,049,168 + 231,630,840) / 5,760,000;
 # keyed by a hash of the tile kernel's sources.
 FP64_FLOPS_PER_NODE = {
-    ("c2", "6614596315506827"): 293.87,
+    ("c2", "0e4ae39f9e63a2fa"): 293.87,
 }
 # FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
 # SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
@@ -503,6 +505,35 @@ def batched_vs_separate(L, torch, stream, run, cfgs, masks, rho0s, steps):
             "note": "one batched launch per step vs one launch per instance per step; L2 not flushed"}
 
 
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "c2_600x400_kappa0.15_20000.npz")
+
+
+def err_c2_golden(L, stream):
+    """The 600 x 400 workload (kappa = 0.15, 0.6 Tc) run for its 20000 steps in FP32 on one grid with the
+    bench's step kernel, against the FP64 oracle's stored result (tests/golden, written by a script
+    that calls only the oracle): the density error split into bulk nodes (relative) and the interface
+    band (in units of rho_l), and the contact angle."""
+    from tests.fp32_bounds import split_errors
+    ref = np.load(GOLDEN_C2)
+    rho_g, rho_l = float(ref["rho_g"]), float(ref["rho_l"])
+    wl = W.c2_cylinder_600x400(kappa=float(ref["kappa"]))
+    cfg = make_cfg(L, wl, "fp32", rho_g, rho_l)
+    t0 = time.perf_counter()
+    with L.Simulation(cfg, wl.mask(), wl.rho0(rho_l, rho_g), None, None, stream) as sim:
+        sim.step(int(ref["steps"]))
+        o, rho, _ = sim.observables(fields=True)
+        kernel = sim.step_kernel()
+    sec = time.perf_counter() - t0
+    bulk, band, nb, ni = split_errors(rho, ref["rho"], wl.mask(), rho_l, rho_g)
+    return {"steps": int(ref["steps"]), "kernel": kernel, "bulk_max_rel": float(bulk), "bulk_nodes": int(nb),
+            "band_max_over_rho_l": float(band), "band_nodes": int(ni),
+            "theta_deg": round(o.theta_deg, 6), "theta_oracle_deg": round(float(ref["theta_deg"]), 6),
+            "mass_rel": float(abs(o.mass / float(ref["mass"]) - 1)), "seconds": round(sec, 3),
+            "definition": "FP32 GPU vs the stored FP64 oracle result after the workload's 20000 steps: max "
+                          "|drho|/rho at bulk nodes (more than 3 nodes from the rho_mid contour and from solids), "
+                          "max |drho|/rho_l in that interface band"}
+
+
 def e2e_rate(L, cfgs, masks, rho0s, wls, steps, stream, world=1):
     """The metric end to end through the public API with host buffers: init from the host mask and
     initial density, `steps` calls of the stepping entry point with one step each (each reads back
@@ -770,6 +801,8 @@ def run_ours(args):
 
     # error against the FP64 oracle: one step from the GPU state of the first instance
     err = err_one_step(L, run.handles[0], wls[0], lambda: run.step(1))
+    if args.workload == "c2" and precision == "fp32" and not args.no_extras:
+        err = {"one_step": err, "after_20000_steps": err_c2_golden(L, stream)}
 
     # batched launch vs one launch per instance (no L2 flush: back-to-back steps)
     bvs = None

@@ -88,9 +88,10 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
         }
         v[3] = fmax(v[3], u2);
         if (t & T_NEARWALL) continue;
-        const int x = int(g % nx);
-        const long long q = g / nx;
-        const int y = int(q % ny), z = int(q / ny);
+        // (32-bit division: a grid holds fewer than 2^31 / 19 nodes)
+        const unsigned gu = unsigned(g), q = gu / unsigned(nx);
+        const int x = int(gu - q * unsigned(nx));
+        const int y = int(q % unsigned(ny)), z = int(q / unsigned(ny));
         // links +x, +y (, +z) to a fluid neighbour away from walls whose density straddles rho_mid
         for (int axis = 0; axis < DIM; ++axis) {
             const int xn = axis == 0 ? wrapp(x + 1, nx) : x;
@@ -145,8 +146,10 @@ __global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ pa
     block_combine(v, out);
 }
 
+// About 8 nodes per thread: each block ends with warp reductions of NRED doubles on the FP64 pipe,
+// whose low rate makes one block per 256 nodes cost more than the nodes themselves on small grids.
 int n_blocks(long long N) {
-    long long b = (N + RB - 1) / RB;
+    long long b = (N + 8LL * RB - 1) / (8LL * RB);
     const long long cap = 152LL * 8;
     if (b > cap) b = cap;
     return int(b < 1 ? 1 : b);

@@ -54,6 +54,27 @@ def test_noalloc_matches_observables_twice(precision):
         assert results[0] != results[1]     # the second call reflects the new state, not stale scratch
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_matches_observables_3d(precision):
+    """A drop on a sphere (D3Q19): the sphere-fit branch of the shared contact-angle code."""
+    import torch
+    from paper_1908_04443_gb300 import lbmwet as L
+
+    case = drop_on_cylinder((32, 36, 40), (12.0, 18.0, 20.0), 7.0, (24.0, 18.0, 20.0), 8.0, kappa=0.1,
+                            lattice="D3Q19")
+    stream = torch.cuda.current_stream()
+    with case.gpu(precision, stream=stream) as sim:
+        n = sim.n
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        u = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+        sim.step(30)
+        L.lbm_fields_device(sim.h, rho.data_ptr(), u.data_ptr())
+        o = L.lbm_observables_noalloc(sim.h, rho.data_ptr(), u.data_ptr())
+        ref = L.lbm_observables(sim.h)
+        assert ref.n_interface > 0
+        _compare(o, ref)
+
+
 def test_noalloc_rejects_grid_above_its_static_scratch():
     import torch
     from paper_1908_04443_gb300 import lbmwet as L
