@@ -27,8 +27,8 @@ SCHEMES = {"VD": dict(wall="VD", rho_w_const=3.45), "GF": dict(wall="GF", theta_
            "IVD": dict(kappa=0.135), "SF": dict(wall="SF", Gw=-0.6)}
 
 
-def _run(kw):
-    case = drop_on_cylinder(SHAPE, C, R, (150.0, 230.0), 50.0, eos_kind="PR", t_over_tc=0.86, sigma=0.11, **kw)
+def _run(kw, sigma=0.11):
+    case = drop_on_cylinder(SHAPE, C, R, (150.0, 230.0), 50.0, eos_kind="PR", t_over_tc=0.86, sigma=sigma, **kw)
     case.rho_ref = case.bounds()[0]
     with case.gpu("fp32") as sim:
         sim.step(30000)
@@ -83,6 +83,24 @@ def test_fig4_fig5_angles(kw, paper, tol):
     3.25, 1.5 give 31, 65, 121 degrees) and for the improved scheme (Fig. 5: phi = 1.4, phi = 1 and
     drho = 0.5 give 34, 88, 125), with the readings taken here for the unprinted constants (sigma =
     0.11, default rates).  Measured after 30,000 steps: 30, 64, 121 and 33, 89, 134 degrees - the
-    hydrophobic drho branch is 9 degrees above the paper's value, hence its wider bound."""
+    hydrophobic drho branch is 9 degrees above the paper's value, hence its wider bound (the offset
+    follows sigma: see test_fig5_angles_follow_sigma)."""
     o, _, _ = _run(kw)
     assert abs(o.theta_deg - paper) < tol
+
+
+# Fig. 5 with sigma = 0.09 instead of the flat-interface calibration 0.11 (the paper prints no sigma)
+FIG5_SIGMA009 = [(dict(kappa=0.4), 34.0), (dict(kappa=0.0), 88.0), (dict(kappa=-0.5), 125.0)]
+
+
+@pytest.mark.parametrize("kw,paper", FIG5_SIGMA009)
+def test_fig5_angles_follow_sigma(kw, paper):
+    """The 9-degree offset of the hydrophobic case above comes from the unprinted sigma of Eq. 7, not
+    from the relaxation rates or the limiter: measured on this cylinder, the drho = 0.5 angle moves
+    by about 3.4 degrees per 0.01 of sigma (115 at sigma = 0, 124 at 0.08, 134 at 0.11, 141 at 0.14)
+    and by under 0.1 degree when s_e = s_eps go from 0.6 to 1.2 or s_q from 1.1 to 1.9.  With sigma =
+    0.09 the three Fig. 5 cases come within 4 degrees of the paper's 34, 88 and 125 (measured 35.2,
+    about 90.5 and 123.9), at the price of a gas density about 7 % below the Maxwell value, which
+    is why the flat-interface calibration (0.11) stays the default."""
+    o, _, _ = _run(kw, sigma=0.09)
+    assert abs(o.theta_deg - paper) < 4.0
