@@ -597,8 +597,9 @@ __global__ void unstream_kernel(S* __restrict__ fout, DevParams p, const double*
             double v;
             if (FROM_FEQ && src1 == nullptr) {
                 // u0 = 0: every velocity term of the bracket is an exact zero, so this is feq_a's
-                // value bit for bit (w of the opposite direction equals w_b)
-                v = L::w(b) * src0[src];
+                // value bit for bit (w of the opposite direction equals w_b); the product is rounded
+                // on its own, as feq_a's is, so that it is not fused with the subtraction below
+                v = __dmul_rn(L::w(b), src0[src]);
             } else if (FROM_FEQ) {
                 const double* rho0 = src0;
                 const double* u0 = src1;
