@@ -185,6 +185,8 @@ def lbm_init(cfg: lbm_config, solid_mask: np.ndarray, rho0=None, u0=None, kappa_
     if r is not None and r.size != n:
         raise ValueError("rho0 size does not match the grid")
     u, pu = _ptr(None if u0 is None else np.asarray(u0).reshape(-1), np.float64)
+    if u is not None and u.size != (2 if cfg.lattice == LBM_D2Q9 else 3) * n:
+        raise ValueError("u0 size does not match the grid (d * nodes, component-major)")
     k, pk = _ptr(None if kappa_per_wall is None else np.asarray(kappa_per_wall).reshape(-1), np.float64)
     h = C.c_void_p()
     st = _lib.lbm_init(C.byref(cfg), pm, pr, pu, pk, _stream_ptr(stream), C.byref(h))
@@ -339,6 +341,18 @@ def _bcheck(status: int, b=None):
 
 def lbm_batch_init(cfgs, masks, rho0s=None, kappas_per_wall=None, stream=None):
     n = len(cfgs)
+    # the library reads nx * ny * nz bytes of every mask and as many doubles of every density
+    if len(masks) != n or (rho0s is not None and len(rho0s) != n) or \
+            (kappas_per_wall is not None and len(kappas_per_wall) != n):
+        raise ValueError("one mask (and density, kappa array) per instance")
+    for i, c in enumerate(cfgs):
+        if min(c.nx, c.ny, c.nz) < 1:
+            continue                    # rejected by the library's own checks
+        nodes = c.nx * c.ny * c.nz
+        if masks[i] is None or np.asarray(masks[i]).size != nodes:
+            raise ValueError(f"instance {i}: solid mask missing or of the wrong size")
+        if rho0s is not None and rho0s[i] is not None and np.asarray(rho0s[i]).size != nodes:
+            raise ValueError(f"instance {i}: rho0 size does not match the grid")
     arr = (lbm_config * n)(*cfgs)
     keep = []
 

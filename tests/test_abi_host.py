@@ -104,6 +104,50 @@ def test_batch_rejects_mixed_physics_before_device_work():
     assert "differs" in str(ei.value)
 
 
+def test_batch_checks_every_instance_before_its_host_scans():
+    """lbm_batch_init checks every configuration and mask before it scans any mask (the scans run on
+    several host threads) or touches the device: a bad grid or a missing mask of a later instance is
+    rejected with LBM_ERR_ARG and the instance named."""
+    m = np.zeros((8, 8), np.uint8)
+    bad = _cfg()
+    bad.nz = 2                  # D2Q9 with nz != 1
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_batch_init([_cfg(), _cfg(), bad], [m, m, np.zeros(128, np.uint8)])
+    assert ei.value.status == L.LBM_ERR_ARG
+    assert "instance 2" in str(ei.value)
+    neg = _cfg()
+    neg.nx = -5
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_batch_init([_cfg(), neg], [m, m])
+    assert ei.value.status == L.LBM_ERR_ARG
+    assert "instance 1" in str(ei.value)
+    # a null mask pointer through the C ABI itself (the binding refuses None before the call)
+    cfgs = (L.lbm_config * 2)(_cfg(), _cfg())
+    masks = (L.C.c_void_p * 2)(m.ctypes.data, None)
+    b = L.C.c_void_p()
+    assert L._lib.lbm_batch_init(2, cfgs, masks, None, None, None, L.C.byref(b)) == L.LBM_ERR_ARG
+    assert not b.value
+    assert "instance 1" in L._lib.lbm_batch_last_error(None).decode()
+
+
+@pytest.mark.parametrize("which", ["none", "short_mask", "long_rho0", "count"])
+def test_binding_checks_batch_array_sizes(which):
+    """The binding refuses arrays whose size is not the grid's, since the library reads exactly
+    nx * ny * nz values from every pointer it is given."""
+    m = np.zeros((8, 8), np.uint8)
+    masks, rho0s = [m, m], None
+    if which == "none":
+        masks = [m, None]
+    elif which == "short_mask":
+        masks = [m, np.zeros(63, np.uint8)]
+    elif which == "long_rho0":
+        rho0s = [None, np.ones(65)]
+    else:
+        masks = [m]
+    with pytest.raises(ValueError):
+        L.lbm_batch_init([_cfg(), _cfg()], masks, rho0s)
+
+
 def test_sf_scheme_rejects_non_finite_gw_and_mixed_gw_batches():
     """The solid-fluid interaction scheme needs a finite G_w, and a batch shares one G_w: both are
     rejected with LBM_ERR_ARG before any device work."""
