@@ -27,7 +27,9 @@
  *   - A handle is not thread-safe; distinct handles are independent.
  *   - Device-side numerical faults (a non-positive square-root argument in Eq. 6, a non-positive
  *     or non-finite density) set a sticky flag on the device; lbm_step and lbm_observables read
- *     it once per call and return LBM_ERR_UNSTABLE.  Nothing on the device waits or traps.
+ *     it once per call and return LBM_ERR_UNSTABLE.  Nothing on the device traps, and its only
+ *     waits (on the mbarriers of TMA copies) give up after a bounded number of polls: a copy that
+ *     never lands sets another flag, which the same calls report as LBM_ERR_CUDA.
  */
 #ifndef LBMWET_H
 #define LBMWET_H

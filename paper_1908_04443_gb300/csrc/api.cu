@@ -272,7 +272,8 @@ lbm_status check_device_error(lbm_handle* h) {
         if (flags & ERR_PSI) m += " non-positive square-root argument in Eq. 6;";
         if (flags & ERR_RHO) m += " non-positive or non-finite density;";
         if (flags & ERR_TIMEOUT) m += " a wait for a shared-memory copy gave up;";
-        return fail(h, LBM_ERR_UNSTABLE, m);
+        // a copy that never landed is a device failure, not a numerical one (as for batches)
+        return fail(h, (flags & ERR_TIMEOUT) ? LBM_ERR_CUDA : LBM_ERR_UNSTABLE, m);
     }
     return LBM_OK;
 }
