@@ -56,6 +56,7 @@ struct lbm_handle {
     std::vector<uint8_t> pair_solid;   // the same per tile of the FP32 pair kernel (D2Q9)
     uint8_t* d_pair_solid = nullptr;   // set when this handle steps with the pair kernel
     void* d_zmaps = nullptr;           // D3Q19 FP32: TMA tensor maps of f[0] and f[1]
+    ZItem* d_zitems = nullptr;         // and the work list of the TMA-staged z-march
     int tiles[3] = {1, 1, 1};
     int int_tile[3] = {1, 1, 1};
     int* d_wall_id = nullptr;
@@ -253,6 +254,7 @@ void free_all(lbm_handle* h) {
         guarded_free(h->f[i], s);
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    dfree(h->d_zitems, s);
     for (void* q : {(void*)h->d_type, (void*)h->d_tile_solid, (void*)h->d_pair_solid, h->d_zmaps, (void*)h->d_yitems,
                     (void*)h->d_ybegin, (void*)h->d_wall_id, (void*)h->d_kappa, (void*)h->d_err, (void*)h->d_partials,
                     (void*)h->d_red})
@@ -672,6 +674,12 @@ lbm_status init_impl(const lbm_config* cfg, const uint8_t* solid_mask, const dou
             CKI(dmalloc(&h->d_zmaps, sizeof(maps), h->stream), "cudaMalloc tensor maps");
             // (from pageable memory: staged before the call returns, so `maps` may go out of scope)
             CKI(cudaMemcpyAsync(h->d_zmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, h->stream), "copy tensor maps");
+            const std::vector<ZItem> items = ztma_work_list(solid_mask, nx, ny, nz);
+            CKI(dmalloc(&h->d_zitems, sizeof(ZItem) * items.size(), h->stream), "cudaMalloc work list");
+            CKI(cudaMemcpyAsync(h->d_zitems, items.data(), sizeof(ZItem) * items.size(), cudaMemcpyHostToDevice,
+                                h->stream), "copy work list");
+            p.zitems = h->d_zitems;
+            p.nzitems = int(items.size());
             p.ztmap = h->d_zmaps;
         }
     }

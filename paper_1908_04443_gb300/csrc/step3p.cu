@@ -13,11 +13,13 @@
 //      consistency source (Eqs. 2, 7) in the increment form f += M^-1 (m* - m), coalesced stores.
 // Rings indexed by the absolute plane: densities 4 planes, psi 8, node types 8, wall queues 4 (and,
 // with LBMWET_ZP_REPULL = 0, the own distributions, 4 planes).  Results equal the scalar z-march's up to FP32 rounding (operations regrouped).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
 #include "kernels.h"
 #include "lattice.cuh"
+#include "maskscan.h"
 #include "pack2.cuh"
 #include "tile_common.cuh"
 
@@ -607,14 +609,14 @@ struct OutBand {
 // and the collided plane.
 __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, float* __restrict__ fout,
                                                 const void* tmap, const Geo& g, const Phys<float>& ph,
-                                                const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
+                                                const Rates3P& kr, int x0, int y0, int zb, int ze, unsigned* err,
                                                 ZTBulk& S, uint64_t* bar) {
     using L = D3Q19;
     constexpr int Q = 19;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const long long fs = g.fs;
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TTX + lx;
-    const int zlo = zb - 1, zhi = min(zb + TCH, nz);   // lead planes zlo .. zhi, collided planes zb .. zhi - 1
+    const int zlo = zb - 1, zhi = ze;   // lead planes zlo .. zhi, collided planes zb .. ze - 1
     const int nlead = zhi - zlo + 1;
 
     // out-of-range cells of the used window (rows 0 .. 11, columns 2 .. 37): at most
@@ -759,14 +761,13 @@ __device__ __forceinline__ void ztma_chunk_bulk(const float* __restrict__ fin, f
 template <bool SF>
 __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, float* __restrict__ fout,
                                                  const void* tmap, const Geo& g, const Phys<float>& ph,
-                                                 const Rates3P& kr, int x0, int y0, int zb, unsigned* err,
+                                                 const Rates3P& kr, int x0, int y0, int zb, int ze, unsigned* err,
                                                  ZTSolid& S, uint64_t* bar) {
     using L = D3Q19;
     constexpr int Q = 19, NT = TTX * ZTY;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const long long fs = g.fs;
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TTX + lx;
-    const int ze = min(zb + TCH, nz);
     const int zlo = zb - 2, zhi = ze + 1;   // lead planes; collided planes zb .. ze - 1
     const int nlead = zhi - zlo + 1;
     auto wz = [&](int z) { return wrap1(wrap1(z, nz), nz); };
@@ -1061,19 +1062,19 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
     }
 }
 
+// Can the march box column (x0, y0) with TMA loads?  (Full 32 x 8 columns of grids at least 64 x 16 x 4;
+// the host's work list uses the same test.)
+__host__ __device__ __forceinline__ bool ztma_boxed(int x0, int y0, int nx, int ny, int nz) {
+    return x0 + TTX <= nx && y0 + TTY <= ny && nx >= 64 && ny >= 16 && nz >= 4;
+}
+
 __global__ void __launch_bounds__(TTX* ZTY, 2)
     ztma_step(const float* __restrict__ fin, float* __restrict__ fout, const void* tmap, Geo g, Phys<float> ph,
-              Rates3P kr, unsigned* err) {
+              Rates3P kr, unsigned* err, const ZItem* __restrict__ items) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int x0 = blockIdx.x * TTX, y0 = blockIdx.y * TTY, zb = blockIdx.z * TCH;
-    // chunk flags of the two 32 x 4 halves (the z-pair tiling)
-    const int ty4 = (g.ny + ZTY - 1) / ZTY, tx = gridDim.x;
-    const int h0 = (blockIdx.z * ty4 + 2 * blockIdx.y) * tx + blockIdx.x;
-    const bool has1 = y0 + ZTY < g.ny;
-    const bool s0 = g.tile_solid ? g.tile_solid[h0] != 0 : true;
-    const bool s1 = has1 && (g.tile_solid ? g.tile_solid[h0 + tx] != 0 : true);
-    const bool boxed = tmap != nullptr && x0 + TTX <= g.nx && y0 + TTY <= g.ny && g.nx >= 64 && g.ny >= 16 &&
-                       g.nz >= 4;
+    const ZItem it = items[blockIdx.x];
+    const int x0 = it.bx * TTX, y0 = it.by * TTY, zb = it.z0, ze = it.z1;
+    const bool boxed = tmap != nullptr && ztma_boxed(x0, y0, g.nx, g.ny, g.nz);
     const bool sf = ph.wall_kind == 2;
     if (boxed) {
         ZTSmem& S = *reinterpret_cast<ZTSmem*>(smem_raw);
@@ -1084,14 +1085,21 @@ __global__ void __launch_bounds__(TTX* ZTY, 2)
         }
         __syncthreads();
         // tmap: the input buffer's map (box TBX x TBY x 1)
-        if (!s0 && !s1)
-            ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.b, S.bar);
+        if (!it.solid)
+            ztma_chunk_bulk(fin, fout, tmap, g, ph, kr, x0, y0, zb, ze, err, S.b, S.bar);
         else if (sf)
-            ztma_chunk_solid<true>(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
+            ztma_chunk_solid<true>(fin, fout, tmap, g, ph, kr, x0, y0, zb, ze, err, S.s, S.bar);
         else
-            ztma_chunk_solid<false>(fin, fout, tmap, g, ph, kr, x0, y0, zb, err, S.s, S.bar);
+            ztma_chunk_solid<false>(fin, fout, tmap, g, ph, kr, x0, y0, zb, ze, err, S.s, S.bar);
         return;
     }
+    // a column the march cannot box: its 32-plane chunk by the z-pair march on the two 32 x 4 halves,
+    // with their chunk flags
+    const int ty4 = (g.ny + ZTY - 1) / ZTY, tx = (g.nx + ZTX - 1) / ZTX;
+    const int h0 = ((zb / ZCH) * ty4 + 2 * it.by) * tx + it.bx;
+    const bool has1 = y0 + ZTY < g.ny;
+    const bool s0 = g.tile_solid ? g.tile_solid[h0] != 0 : true;
+    const bool s1 = has1 && (g.tile_solid ? g.tile_solid[h0 + tx] != 0 : true);
     ZPSmem<ZTX, ZTY>& sm = *reinterpret_cast<ZPSmem<ZTX, ZTY>*>(smem_raw);
     for (int h = 0; h < (has1 ? 2 : 1); ++h) {
         const bool solid = h ? s1 : s0;
@@ -1141,15 +1149,76 @@ cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, cons
         if (e != cudaSuccess) return e;
         attr[dev] = true;
     }
-    dim3 grid((p.nx + TTX - 1) / TTX, (p.ny + TTY - 1) / TTY, (p.nz + TCH - 1) / TCH);
-    ztma_step<<<grid, dim3(TTX, ZTY, 1), ZT_SMEM, s>>>(static_cast<const float*>(fin), static_cast<float*>(fout), tmap,
-                                                      g, make_phys<float>(p), make_rates3p(p), p.err);
+    if (!p.zitems || p.nzitems < 1) return cudaErrorInvalidValue;
+    ztma_step<<<p.nzitems, dim3(TTX, ZTY, 1), ZT_SMEM, s>>>(static_cast<const float*>(fin), static_cast<float*>(fout),
+                                                           tmap, g, make_phys<float>(p), make_rates3p(p), p.err,
+                                                           p.zitems);
     return cudaGetLastError();
 }
 
 void ztma_box_dims(int* bx, int* by) {
     *bx = TBX;
     *by = TBY;
+}
+
+#ifndef LBMWET_ZWL_MIN_BULK   // shortest bulk run kept on the bulk path (planes)
+#define LBMWET_ZWL_MIN_BULK 8
+#endif
+#ifndef LBMWET_ZWL_MAX_BULK   // longest bulk item (planes; solid items take at most TCH)
+#define LBMWET_ZWL_MAX_BULK 32
+#endif
+
+std::vector<ZItem> ztma_work_list(const uint8_t* mask, int nx, int ny, int nz) {
+    constexpr int HALO = 3, MIN_BULK = LBMWET_ZWL_MIN_BULK, MAX_BULK = LBMWET_ZWL_MAX_BULK;
+    const int gx = (nx + TTX - 1) / TTX, gy = (ny + TTY - 1) / TTY;
+    // per plane and column: a solid within 3 nodes of the column's cells in x and y (periodic)
+    const int t[3] = {TTX, TTY, 1};
+    const std::vector<uint8_t> col = tile_solid_flags(mask, nx, ny, nz, t, 2, scan_threads((long long)nx * ny * nz));
+    std::vector<ZItem> items;
+    std::vector<uint8_t> need(nz);
+    for (int by = 0; by < gy; ++by)
+        for (int bx = 0; bx < gx; ++bx) {
+            if (!ztma_boxed(bx * TTX, by * TTY, nx, ny, nz)) {
+                for (int z0 = 0; z0 < nz; z0 += ZCH) items.push_back(ZItem{bx, by, z0, std::min(z0 + ZCH, nz), 1});
+                continue;
+            }
+            // planes within 3 planes (periodic) of a plane with a solid near the column
+            for (int z = 0; z < nz; ++z) {
+                uint8_t n = 0;
+                for (int d = -HALO; d <= HALO && !n; ++d) {
+                    const int zz = ((z + d) % nz + nz) % nz;
+                    n = col[((size_t)zz * gy + by) * gx + bx];
+                }
+                need[z] = n;
+            }
+            // runs of equal need; short bulk runs join the solid path
+            std::vector<ZItem> runs;
+            for (int z0 = 0; z0 < nz;) {
+                int z1 = z0 + 1;
+                while (z1 < nz && need[z1] == need[z0]) ++z1;
+                runs.push_back(ZItem{bx, by, z0, z1, need[z0] ? 1 : 0});
+                z0 = z1;
+            }
+            for (ZItem& r : runs)
+                if (!r.solid && r.z1 - r.z0 < MIN_BULK && runs.size() > 1) r.solid = 1;
+            std::vector<ZItem> merged;
+            for (const ZItem& r : runs) {
+                if (!merged.empty() && merged.back().solid == r.solid) merged.back().z1 = r.z1;
+                else merged.push_back(r);
+            }
+            // near-equal items of at most TCH planes (MAX_BULK for bulk runs)
+            for (const ZItem& r : merged) {
+                const int cap = r.solid ? TCH : MAX_BULK;
+                const int len = r.z1 - r.z0, n = (len + cap - 1) / cap;
+                for (int k = 0; k < n; ++k)
+                    items.push_back(ZItem{bx, by, r.z0 + int((long long)len * k / n),
+                                          r.z0 + int((long long)len * (k + 1) / n), r.solid});
+            }
+        }
+    std::stable_sort(items.begin(), items.end(), [](const ZItem& a, const ZItem& b) {
+        return a.z0 != b.z0 ? a.z0 < b.z0 : (a.by != b.by ? a.by < b.by : a.bx < b.bx);
+    });
+    return items;
 }
 
 }  // namespace lbmwet
