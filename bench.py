@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -41,22 +42,22 @@ METRIC = "MLUPS (million lattice updates per second) of the fused time step"
 UNIT = "MLUPS"
 
 # DRAM bytes per launch of the step kernel measured by ncu on the workload below, keyed by a hash
-# of the kernel sources: when the sources change the figure is stale and reported as null.
+# of the kernel code: when the code changes the figure is stale and reported as null.
 NCU_TRAFFIC = {
     # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
-    # one launch (214,298,112 + 160,227,072 bytes)
-    ("c2", "fp32", "e78f2b8f22cd8a98"): 374525184,
-    # ztma_step, 256^3 sphere: one launch (1,644,406,016 + 1,217,767,168 bytes)
-    ("c3", "fp32", "062444ad6ec36c6c"): 2862173184,
+    # one launch (214,383,104 + 159,419,648 bytes)
+    ("c2", "fp32", "71b039197257b4f9"): 373802752,
+    # ztma_step, 256^3 sphere: one launch (1,611,316,224 + 1,218,131,200 bytes)
+    ("c3", "fp32", "648dfc22b4f8bef5"): 2829447424,
 }
 
 
 # FP64 floating-point operations per node update of the FP64 batched tile kernel
 # (fused_step_batched<D2Q9, double>) on the 600 x 400 sweep, from ncu: (2 x DFMA + DADD + DMUL thread
 # instructions of one launch) / nodes = (2 x 478,996,920 + 503,049,168 + 231,630,840) / 5,760,000;
-# keyed by a hash of the tile kernel's sources.
+# keyed by a hash of the tile kernel's code.
 FP64_FLOPS_PER_NODE = {
-    ("c2", "0e4ae39f9e63a2fa"): 293.87,
+    ("c2", "58124fc042b67c45"): 293.87,
 }
 # FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
 # SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
@@ -66,28 +67,29 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 NOMINAL_HBM_GBS = 7900.0
 
 
-def tile_kernel_hash() -> str:
+def _code_hash(files) -> str:
+    """Hash of the code of the given csrc files, comments and whitespace removed (a comment edit does
+    not make a measured figure stale; any code edit does)."""
     h = hashlib.sha256()
-    for f in ("step.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the tile kernel's sources
-        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
+
+
+def tile_kernel_hash() -> str:
+    return _code_hash(("step.cu", "tile_common.cuh", "lattice.cuh", "kernels.h"))   # the tile kernel's sources
 
 
 def kernel_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("step2p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the pair kernel's sources
-        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    return _code_hash(("step2p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"))   # the pair kernel's
 
 
 def ztma_kernel_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("step3p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"):   # the 3D kernel's sources
-        with open(os.path.join(ROOT, "paper_1908_04443_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    return _code_hash(("step3p.cu", "pack2.cuh", "tile_common.cuh", "lattice.cuh", "kernels.h"))   # the 3D kernel's
 
 
 WORKLOADS = ("c2", "c2single", "c1", "c3", "c4")

@@ -43,7 +43,7 @@ struct DevParams {
 };
 
 // One work item of the TMA-staged z-march: the 32 x 8 column (bx, by) over planes z0 .. z1 - 1 (at
-// most 32), and whether those planes need the path of chunks holding solids (a solid within 3 nodes
+// most 39), and whether those planes need the path of chunks holding solids (a solid within 3 nodes
 // of the column's cells on a plane within 3 planes of the range).  Columns the march cannot box (the
 // ragged ones and grids smaller than a box) come as the z-pair march's 32-plane chunks.
 struct ZItem {
@@ -147,9 +147,9 @@ cudaError_t launch_ztma_step(const void* fin, void* fout, const void* tmap, cons
 void ztma_box_dims(int* bx, int* by);
 // Work list of the TMA-staged z-march for a grid with solid mask `mask` (host, nx*ny*nz bytes):
 // every boxed 32 x 8 column cut along z into runs that need the solid path and runs that do not
-// (bulk runs shorter than 8 planes join the solid path), each run split into near-equal items of at
-// most 32 planes; the other columns as the z-pair march's 32-plane chunks; ordered by first plane,
-// then column.
+// (bulk runs shorter than 8 planes join the solid path), each run cut at the multiples of 32 planes
+// (a first or last piece shorter than 8 planes joins its neighbour); the other columns as the z-pair
+// march's 32-plane chunks; ordered by first plane, then column.
 std::vector<ZItem> ztma_work_list(const uint8_t* mask, int nx, int ny, int nz);
 // Tile shape (x, y, z) of the step kernels and the resident CTAs per SM of the batched kernel.
 void step_tile_shape(int lat, int prec, int* tx, int* ty, int* tz);

@@ -1161,15 +1161,12 @@ void ztma_box_dims(int* bx, int* by) {
     *by = TBY;
 }
 
-#ifndef LBMWET_ZWL_MIN_BULK   // shortest bulk run kept on the bulk path (planes)
-#define LBMWET_ZWL_MIN_BULK 8
-#endif
-#ifndef LBMWET_ZWL_MAX_BULK   // longest bulk item (planes; solid items take at most TCH)
-#define LBMWET_ZWL_MAX_BULK 32
+#ifndef LBMWET_ZWL_MIN_RUN   // shortest bulk run kept on the bulk path, and shortest piece (planes)
+#define LBMWET_ZWL_MIN_RUN 8
 #endif
 
 std::vector<ZItem> ztma_work_list(const uint8_t* mask, int nx, int ny, int nz) {
-    constexpr int HALO = 3, MIN_BULK = LBMWET_ZWL_MIN_BULK, MAX_BULK = LBMWET_ZWL_MAX_BULK;
+    constexpr int HALO = 3, MIN_RUN = LBMWET_ZWL_MIN_RUN;
     const int gx = (nx + TTX - 1) / TTX, gy = (ny + TTY - 1) / TTY;
     // per plane and column: a solid within 3 nodes of the column's cells in x and y (periodic)
     const int t[3] = {TTX, TTY, 1};
@@ -1200,19 +1197,24 @@ std::vector<ZItem> ztma_work_list(const uint8_t* mask, int nx, int ny, int nz) {
                 z0 = z1;
             }
             for (ZItem& r : runs)
-                if (!r.solid && r.z1 - r.z0 < MIN_BULK && runs.size() > 1) r.solid = 1;
+                if (!r.solid && r.z1 - r.z0 < MIN_RUN && runs.size() > 1) r.solid = 1;
             std::vector<ZItem> merged;
             for (const ZItem& r : runs) {
                 if (!merged.empty() && merged.back().solid == r.solid) merged.back().z1 = r.z1;
                 else merged.push_back(r);
             }
-            // near-equal items of at most TCH planes (MAX_BULK for bulk runs)
+            // pieces cut at the multiples of TCH planes, so that items of neighbouring columns start
+            // on the same planes and share their halo reads in L2; a first or last piece shorter than
+            // MIN_RUN joins its neighbour (items of up to TCH + MIN_RUN - 1 planes)
             for (const ZItem& r : merged) {
-                const int cap = r.solid ? TCH : MAX_BULK;
-                const int len = r.z1 - r.z0, n = (len + cap - 1) / cap;
-                for (int k = 0; k < n; ++k)
-                    items.push_back(ZItem{bx, by, r.z0 + int((long long)len * k / n),
-                                          r.z0 + int((long long)len * (k + 1) / n), r.solid});
+                std::vector<int> cuts{r.z0};
+                for (int z = (r.z0 / TCH + 1) * TCH; z < r.z1; z += TCH) cuts.push_back(z);
+                cuts.push_back(r.z1);
+                if (cuts.size() > 2 && cuts[1] - cuts[0] < MIN_RUN) cuts.erase(cuts.begin() + 1);
+                if (cuts.size() > 2 && cuts[cuts.size() - 1] - cuts[cuts.size() - 2] < MIN_RUN)
+                    cuts.erase(cuts.end() - 2);
+                for (size_t k = 0; k + 1 < cuts.size(); ++k)
+                    items.push_back(ZItem{bx, by, cuts[k], cuts[k + 1], r.solid});
             }
         }
     std::stable_sort(items.begin(), items.end(), [](const ZItem& a, const ZItem& b) {
