@@ -490,7 +490,8 @@ __global__ void __launch_bounds__(ZTX* ZTY, LBMWET_ZP_MINB)
 //   * phase A of lead plane zl: rho (Eq. 4) and psi (Eq. 6) of the column and its halo into rings of
 //     planes; the column's own pulled values stay in registers;
 //   * chunks holding solids: bounce-back (Fig. 3) replaces a pulled value whose source is solid by
-//     the cell's own post-collision value in the opposite direction (plain loads, rare), and phase B
+//     the cell's own post-collision value in the opposite direction (from this plane's boxes when
+//     e_z = 0, from the next plane's when e_z = -1, plain loads otherwise), and phase B
 //     gives the wall cells of plane zl - 1 their virtual density (Eqs. 16-17 with the limiter, or the
 //     constant one) from the densities of planes zl - 2 .. zl;
 //   * phase C collides plane zl - 1 (zl - 2 in chunks holding solids) once its psi neighbours are
@@ -814,7 +815,11 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
     };
     // pull of a fluid cell (rb, c) of plane zl with its type t; RING2: the cell may lie on box row 0
     // or 11, whose pulls reach the rows beyond the box
-    auto pull = [&](auto ring2, const float* st, int zl, int rb, int c, uint8_t t, float (&v)[Q]) {
+    // stn: the other stage (lead plane zl + 1, waited for) or null.  Bounce-back sources f*_abar of the
+    // cell's own plane: for e_az = 0 in this stage's box of abar, for e_az = -1 in the next stage's
+    // (its box of abar holds plane zl), otherwise plain loads.
+    auto pull = [&](auto ring2, const float* st, const float* stn, int zl, int rb, int c, uint8_t t,
+                    float (&v)[Q]) {
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const int ey = L::ey(a), sr = rb - ey;
@@ -827,7 +832,14 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 #pragma unroll
             for (int a = 1; a < Q; ++a) {
                 const uint8_t tu = S.type[(zl - L::ez(a)) & 7][(rb - L::ey(a) + 1) * TYX + c - L::ex(a) - 1];
-                if (tu & T_SOLID) v[a] = bb_src(a, zl, rb, c);
+                if (tu & T_SOLID) {
+                    if (L::ez(a) == 0)
+                        v[a] = st[L::opp(a) * TBSLOT + rb * TBX + c];
+                    else if (L::ez(a) < 0 && stn)
+                        v[a] = stn[L::opp(a) * TBSLOT + rb * TBX + c];
+                    else
+                        v[a] = bb_src(a, zl, rb, c);
+                }
             }
         }
     };
@@ -868,6 +880,12 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             fence_proxy_async();
             __syncthreads();
         }
+        // the next stage (lead plane zl + 1) for bounce-back sources, where it holds them unpatched
+        const float* stn = nullptr;
+        if (!edge && zl + 1 <= zhi) {
+            if (!mbar_wait(&bar[s ^ 1], unsigned((i + 1) >> 1) & 1u, ZT_POLL_LIMIT)) atomicOr(err, ERR_TIMEOUT);
+            stn = S.stage[s ^ 1][0];
+        }
         // A. densities of the density window, psi of the psi window (fluid cells), own values kept
         const uint8_t* ty = S.type[zl & 7];
         float* rr = S.rho[zl & 3];
@@ -879,7 +897,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             const bool fl0 = !(t0 & T_SOLID), fl1 = !(t1 & T_SOLID);
             float d0 = 0.0f, d1 = 0.0f;
             if (fl0) {
-                pull(NoRing2{}, st, zl, ly + 2, lx + 4, t0, v);
+                pull(NoRing2{}, st, stn, zl, ly + 2, lx + 4, t0, v);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d0 += v[a];
             } else {
@@ -889,7 +907,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
 #pragma unroll
             for (int a = 0; a < Q; ++a) fcur[a].v.x = v[a];
             if (fl1) {
-                pull(NoRing2{}, st, zl, ly + 6, lx + 4, t1, v);
+                pull(NoRing2{}, st, stn, zl, ly + 6, lx + 4, t1, v);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d1 += v[a];
             } else {
@@ -922,7 +940,7 @@ __device__ __forceinline__ void ztma_chunk_solid(const float* __restrict__ fin, 
             float rho = 0.0f;
             if (fl) {
                 float v[Q];
-                pull(Ring2{}, st, zl, rb, c, t, v);
+                pull(Ring2{}, st, stn, zl, rb, c, t, v);
                 float d = 0.0f;
 #pragma unroll
                 for (int a = 0; a < Q; ++a) d += v[a];
