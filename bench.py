@@ -589,8 +589,10 @@ def e2e_rate(L, cfgs, masks, rho0s, wls, steps, stream, world=1):
         for _ in range(steps):
             r2.step(1)
         t_steps = time.perf_counter() - t0 - t_init
-        for h, (rho_h, u_h) in zip(r2.handles, outs):
-            L.lbm_observables(h, rho_h, u_h)
+        if r2.batch:        # one call, one synchronisation for the whole batch
+            L.lbm_batch_observables_fields(r2.b, [o[0] for o in outs], [o[1] for o in outs])
+        else:
+            L.lbm_observables(r2.h, outs[0][0], outs[0][1])
         r2.close()
         e2e_s = time.perf_counter() - t0
         return e2e_s, {"init": round(1e3 * t_init, 2), "steps": round(1e3 * t_steps, 2),
@@ -610,7 +612,7 @@ def e2e_rate(L, cfgs, masks, rho0s, wls, steps, stream, world=1):
             "warm_pool": {"value": rate(warm_s), "seconds": round(warm_s, 4), "breakdown_ms": warm_parts,
                           "note": "the same run again with the device memory pool holding the first run's memory"},
             "definition": "init from pinned host mask/rho0 + K x step(1) (4-byte status read each) + "
-                          "observables with pinned host rho and u of every instance + destroy; "
+                          "observables with pinned host rho and u of every instance (one batched call) + destroy; "
                           "value: first run after the library's memory pool was emptied"}
 
 

@@ -281,6 +281,11 @@ lbm_status lbm_set_kappa(lbm_handle* h, const double* kappa_per_wall);
 /* Resolved coexistence densities used by the limiter (after a Maxwell construction if asked). */
 lbm_status lbm_limiter_bounds(const lbm_handle* h, double* rho_g, double* rho_l);
 
+/* Grid of a handle: shape4 = {nx, ny, nz, d} (d = 2 for D2Q9, 3 for D3Q19), so that a caller can size
+ * the host arrays of lbm_observables, lbm_get_state and lbm_set_state (N = nx*ny*nz nodes, Q = 9 or
+ * 19 directions).  Errors: LBM_ERR_ARG (NULL argument). */
+lbm_status lbm_grid_shape(const lbm_handle* h, int32_t* shape4);
+
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
@@ -333,6 +338,17 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
 lbm_status lbm_batch_enqueue_steps(lbm_batch* b, int64_t n);
 /* Observables of every instance (out_n has lbm_batch_size() entries). */
 lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n);
+/* The same with, optionally, every instance's density and velocity fields copied to the host:
+ * rho_hosts[i] (N_i doubles) and u_hosts[i] (d*N_i doubles, component-major) as in lbm_observables;
+ * either array, or any entry, may be NULL.  All instances' fields, reductions and copies are enqueued
+ * on the batch's stream and the stream is synchronised once (lbm_observables on each instance
+ * synchronises per instance); the reduction results land in pinned memory owned by the batch.
+ * Copies into pinned host buffers run asynchronously; the runtime completes a copy into pageable
+ * memory before it returns.  lbm_batch_observables is this call without fields.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_UNSTABLE or LBM_ERR_CUDA for an instance whose device flag is set (its index
+ * in the message), LBM_ERR_OOM. */
+lbm_status lbm_batch_observables_fields(lbm_batch* b, lbm_obs* out_n, double* const* rho_hosts,
+                                        double* const* u_hosts);
 /* Handle of instance i, owned by the batch: valid for lbm_observables, lbm_fields_device,
  * lbm_get_state, lbm_set_state, lbm_save_state/lbm_load_state, lbm_wall_nodes; lbm_step and
  * lbm_enqueue_steps on it return LBM_ERR_STATE and lbm_destroy ignores it.  NULL if i is out of range. */

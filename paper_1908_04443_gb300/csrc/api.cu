@@ -265,17 +265,25 @@ void free_all(lbm_handle* h) {
     h->ckpt.clear();
 }
 
+// Status and message of a nonzero device error word.  A copy that never landed is a device failure,
+// not a numerical one.
+lbm_status flag_status(unsigned flags, std::string* msg) {
+    std::string m = "device flagged:";
+    if (flags & ERR_PSI) m += " non-positive square-root argument in Eq. 6;";
+    if (flags & ERR_RHO) m += " non-positive or non-finite density;";
+    if (flags & ERR_TIMEOUT) m += " a wait for a shared-memory copy gave up;";
+    *msg = m;
+    return (flags & ERR_TIMEOUT) ? LBM_ERR_CUDA : LBM_ERR_UNSTABLE;
+}
+
 lbm_status check_device_error(lbm_handle* h) {
     unsigned flags = 0;
     CK(h, cudaMemcpyAsync(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (flags) {
-        std::string m = "device flagged:";
-        if (flags & ERR_PSI) m += " non-positive square-root argument in Eq. 6;";
-        if (flags & ERR_RHO) m += " non-positive or non-finite density;";
-        if (flags & ERR_TIMEOUT) m += " a wait for a shared-memory copy gave up;";
-        // a copy that never landed is a device failure, not a numerical one (as for batches)
-        return fail(h, (flags & ERR_TIMEOUT) ? LBM_ERR_CUDA : LBM_ERR_UNSTABLE, m);
+        std::string m;
+        const lbm_status st = flag_status(flags, &m);
+        return fail(h, st, m);
     }
     return LBM_OK;
 }
@@ -1069,6 +1077,7 @@ struct lbm_batch {
     int64_t step = 0, launches = 0, nodes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
+    double* h_stage = nullptr;         // pinned: per instance the reduction sums and the error word
 };
 
 namespace {
@@ -1128,6 +1137,8 @@ void batch_free(lbm_batch* b) {
     dfree(b->d_err, b->stream);
     dfree(b->d_insts, b->stream);
     dfree(b->d_tmaps, b->stream);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    b->h_stage = nullptr;
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -1612,12 +1623,57 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
     return LBM_OK;
 }
 
-lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n) {
+lbm_status lbm_batch_observables_fields(lbm_batch* b, lbm_obs* out_n, double* const* rho_hosts,
+                                        double* const* u_hosts) {
+    NvtxRange nvtx_range("lbm_batch_observables_fields");
     if (!b || !out_n) return LBM_ERR_ARG;
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        lbm_status st = lbm_observables(b->inst[i], &out_n[i], nullptr, nullptr);
-        if (st != LBM_OK) return bfail(b, st, "instance " + std::to_string(i) + ": " + b->inst[i]->err);
+    const size_t n = b->inst.size(), W = NRED + 1;
+    if (!b->h_stage)
+        CKB(b, cudaHostAlloc(reinterpret_cast<void**>(&b->h_stage), sizeof(double) * W * n, cudaHostAllocDefault));
+    // every instance's fields, reduction and copies on the batch's stream, then one synchronisation
+    for (size_t i = 0; i < n; ++i) {
+        lbm_handle* h = b->inst[i];
+        lbm_status st = ensure_obs_buffers(h);
+        if (st != LBM_OK) return bfail(b, st, "instance " + std::to_string(i) + ": " + h->err);
+        CKB(b, launch_fields(h->lat, h->prec, h->f[h->cur], h->dp, h->d_rho, h->d_u, h->stream));
+        const double mid = 0.5 * (h->rho_l + h->rho_g);
+        CKB(b, launch_reduce(h->D, h->d_rho, h->d_u, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid,
+                             h->cfg.drop_hint, h->d_partials, h->d_red, h->stream));
+        h->launches += 3;
+        double* slot = b->h_stage + W * i;
+        CKB(b, cudaMemcpyAsync(slot, h->d_red, sizeof(double) * NRED, cudaMemcpyDeviceToHost, h->stream));
+        CKB(b, cudaMemcpyAsync(slot + NRED, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        if (rho_hosts && rho_hosts[i])
+            CKB(b, cudaMemcpyAsync(rho_hosts[i], h->d_rho, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+        if (u_hosts && u_hosts[i])
+            CKB(b, cudaMemcpyAsync(u_hosts[i], h->d_u, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost,
+                                   h->stream));
     }
+    CKB(b, cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < n; ++i) {
+        unsigned flags = 0;
+        std::memcpy(&flags, b->h_stage + W * i + NRED, sizeof(flags));
+        if (flags) {
+            std::string m;
+            const lbm_status st = flag_status(flags, &m);
+            b->inst[i]->err = m;
+            return bfail(b, st, "instance " + std::to_string(i) + ": " + m);
+        }
+        obs_from_reduction(b->inst[i], b->h_stage + W * i, &out_n[i]);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out_n) {
+    return lbm_batch_observables_fields(b, out_n, nullptr, nullptr);
+}
+
+lbm_status lbm_grid_shape(const lbm_handle* h, int32_t* shape4) {
+    if (!h || !shape4) return LBM_ERR_ARG;
+    shape4[0] = h->cfg.nx;
+    shape4[1] = h->cfg.ny;
+    shape4[2] = h->cfg.nz;
+    shape4[3] = h->D;
     return LBM_OK;
 }
 

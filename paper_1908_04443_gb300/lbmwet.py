@@ -96,6 +96,9 @@ def _load():
         "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
         "lbm_batch_enqueue_steps": (C.c_int, [C.c_void_p, C.c_int64]),
         "lbm_batch_observables": (C.c_int, [C.c_void_p, C.POINTER(lbm_obs)]),
+        "lbm_batch_observables_fields": (C.c_int, [C.c_void_p, C.POINTER(lbm_obs), C.POINTER(C.c_void_p),
+                                                   C.POINTER(C.c_void_p)]),
+        "lbm_grid_shape": (C.c_int, [H, C.POINTER(C.c_int32)]),
         "lbm_batch_handle": (C.c_void_p, [C.c_void_p, C.c_int32]),
         "lbm_batch_size": (C.c_int32, [C.c_void_p]),
         "lbm_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
@@ -124,7 +127,8 @@ EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step
             "lbm_step_kernel_used", "lbm_batch_step_kernel_used", "lbm_batch_instance_kernel", "lbm_batch_autotune",
             "lbm_batch_tuning_report", "lbm_batch_set_kernels", "lbm_batch_autotune_forget",
             "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_record", "lbm_adjoint", "lbm_batch_init", "lbm_batch_step",
-            "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_handle", "lbm_batch_size",
+            "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_observables_fields", "lbm_grid_shape",
+            "lbm_batch_handle", "lbm_batch_size",
             "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
@@ -241,13 +245,34 @@ def lbm_check_guards(h) -> Tuple[int, int]:
     return int(g.value), int(p.value)
 
 
+def lbm_grid_shape(h) -> Tuple[int, int, int, int]:
+    """(nx, ny, nz, d) of a handle."""
+    a = (C.c_int32 * 4)()
+    _check(_lib.lbm_grid_shape(h, a), h)
+    return int(a[0]), int(a[1]), int(a[2]), int(a[3])
+
+
+def _nodes_dim(h) -> Tuple[int, int]:
+    nx, ny, nz, d = lbm_grid_shape(h)
+    return nx * ny * nz, d
+
+
+def _out_field(a, size: int, what: str):
+    """A host output array the library writes `size` doubles into."""
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
+        raise ValueError(f"{what} must be a writeable C-contiguous float64 array")
+    if a.size != size:
+        raise ValueError(f"{what} must hold {size} values, not {a.size}")
+    return a.ctypes.data
+
+
 def lbm_observables(h, rho_host: Optional[np.ndarray] = None, u_host: Optional[np.ndarray] = None) -> lbm_obs:
     o = lbm_obs()
-    pr = rho_host.ctypes.data_as(C.c_void_p) if rho_host is not None else None
-    pu = u_host.ctypes.data_as(C.c_void_p) if u_host is not None else None
-    for a in (rho_host, u_host):
-        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
-            raise ValueError("output arrays must be C-contiguous float64")
+    n, d = _nodes_dim(h) if (rho_host is not None or u_host is not None) else (0, 0)
+    pr = _out_field(rho_host, n, "rho_host")
+    pu = _out_field(u_host, d * n, "u_host")
     _check(_lib.lbm_observables(h, C.byref(o), pr, pu), h)
     return o
 
@@ -271,14 +296,23 @@ def lbm_wall_nodes(h) -> np.ndarray:
     return out
 
 
-def lbm_get_state(h, q: int, n: int) -> np.ndarray:
-    out = np.zeros(q * n, dtype=np.float64)
+def lbm_get_state(h, q: Optional[int] = None, n: Optional[int] = None) -> np.ndarray:
+    """The post-streaming distributions, q * n doubles ([a][node]); q and n, if given, must be the
+    handle's."""
+    nn, d = _nodes_dim(h)
+    qq = 9 if d == 2 else 19
+    if (q is not None and q != qq) or (n is not None and n != nn):
+        raise ValueError(f"the handle holds q = {qq} directions on n = {nn} nodes")
+    out = np.zeros(qq * nn, dtype=np.float64)
     _check(_lib.lbm_get_state(h, out.ctypes.data_as(C.c_void_p)), h)
     return out
 
 
 def lbm_set_state(h, f_post: np.ndarray, step: int = 0):
+    nn, d = _nodes_dim(h)
     f, pf = _ptr(np.asarray(f_post).reshape(-1), np.float64)
+    if f.size != (9 if d == 2 else 19) * nn:
+        raise ValueError("f_post size does not match the handle's q * n")
     _check(_lib.lbm_set_state(h, pf, int(step)), h)
 
 
@@ -297,6 +331,10 @@ def lbm_load_state(h, data: bytes):
 
 def lbm_set_kappa(h, kappa_per_wall: np.ndarray):
     k, pk = _ptr(np.asarray(kappa_per_wall).reshape(-1), np.float64)
+    cnt = C.c_int64()
+    _check(_lib.lbm_wall_nodes(h, None, C.byref(cnt)), h)
+    if k.size != cnt.value:
+        raise ValueError(f"kappa_per_wall must hold one value per wall node ({cnt.value})")
     _check(_lib.lbm_set_kappa(h, pk), h)
 
 
@@ -389,6 +427,30 @@ def lbm_batch_observables(b):
     n = _lib.lbm_batch_size(b)
     out = (lbm_obs * n)()
     _bcheck(_lib.lbm_batch_observables(b, out), b)
+    return list(out)
+
+
+def lbm_batch_observables_fields(b, rho_hosts=None, u_hosts=None):
+    """Observables of every instance, and their density / velocity fields written into the given host
+    arrays (lists of n arrays or None), with one synchronisation for the whole batch."""
+    n = _lib.lbm_batch_size(b)
+    out = (lbm_obs * n)()
+
+    def ptrs(arrs, comp, what):
+        if arrs is None:
+            return None
+        if len(arrs) != n:
+            raise ValueError(f"{what}: one array (or None) per instance")
+        p = (C.c_void_p * n)()
+        for i, a in enumerate(arrs):
+            if a is not None:
+                nn, d = _nodes_dim(lbm_batch_handle(b, i))
+                p[i] = _out_field(a, (d if comp else 1) * nn, f"{what}[{i}]")
+        return p
+
+    pr = ptrs(rho_hosts, False, "rho_hosts")
+    pu = ptrs(u_hosts, True, "u_hosts")
+    _bcheck(_lib.lbm_batch_observables_fields(b, out, pr, pu), b)
     return list(out)
 
 

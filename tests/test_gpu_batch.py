@@ -179,3 +179,59 @@ def test_batch_sf_scheme():
             assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref)), i
     finally:
         L.lbm_batch_destroy(bt)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_observables_fields_equal_per_instance_calls(precision):
+    """lbm_batch_observables_fields (one synchronisation for the batch) gives every instance the same
+    observables and fields as lbm_observables called on that instance, with pinned and pageable host
+    arrays and with some entries left out."""
+    import torch
+    from paper_1908_04443_gb300 import lbmwet as L
+    cases = _cases("pair" if precision == "fp32" else "tile")
+    b = _batch(cases, precision)
+    try:
+        L.lbm_batch_step(b, 12)
+        n = [cs.mask.size for cs in cases]
+        pinned = lambda k: torch.zeros(k, dtype=torch.float64).pin_memory().numpy()
+        rho = [pinned(n[0]), np.zeros(n[1]), None, np.zeros(n[3])]
+        u = [pinned(2 * n[0]), None, np.zeros(2 * n[2]), np.zeros(2 * n[3])]
+        obs = L.lbm_batch_observables_fields(b, rho, u)
+        assert [o.mass for o in L.lbm_batch_observables(b)] == [o.mass for o in obs]
+        for i in range(len(cases)):
+            r_ref, u_ref = np.zeros(n[i]), np.zeros(2 * n[i])
+            ref = L.lbm_observables(L.lbm_batch_handle(b, i), r_ref, u_ref)
+            for f in ("mass", "rho_max", "rho_min", "u_max", "n_interface", "step"):
+                assert getattr(obs[i], f) == getattr(ref, f), (i, f)
+            assert obs[i].theta_deg == ref.theta_deg or (np.isnan(obs[i].theta_deg) and np.isnan(ref.theta_deg))
+            if rho[i] is not None:
+                assert np.array_equal(rho[i], r_ref)
+            if u[i] is not None:
+                assert np.array_equal(u[i], u_ref)
+    finally:
+        L.lbm_batch_destroy(b)
+
+
+def test_binding_checks_host_array_sizes():
+    """The binding refuses host arrays whose size is not the grid's before the library writes or reads
+    N (or q*N, d*N, one per wall node) values through them."""
+    from paper_1908_04443_gb300 import lbmwet as L
+    cs = _cases("tile")[1]
+    with cs.gpu("fp64") as sim:
+        n = cs.mask.size
+        assert L.lbm_grid_shape(sim.h) == (cs.shape[1], cs.shape[0], 1, 2)
+        with pytest.raises(ValueError):
+            L.lbm_observables(sim.h, np.zeros(n - 1))
+        with pytest.raises(ValueError):
+            L.lbm_observables(sim.h, None, np.zeros(n))             # u holds 2 * n values
+        with pytest.raises(ValueError):
+            L.lbm_get_state(sim.h, 19, n)
+        with pytest.raises(ValueError):
+            L.lbm_set_state(sim.h, np.zeros(9 * n - 9))
+        nw = len(L.lbm_wall_nodes(sim.h))
+        with pytest.raises(ValueError):
+            L.lbm_set_kappa(sim.h, np.zeros(nw + 1))
+        f = L.lbm_get_state(sim.h)                                     # q and n from the handle
+        assert f.size == 9 * n
+        L.lbm_set_state(sim.h, f)
+        L.lbm_set_kappa(sim.h, np.full(nw, 0.1))
