@@ -192,42 +192,53 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import workloads as W
 from oracle import eos as E, lbm
-wl = W.{ctor}
-e = (E.cs_config() if wl.eos == "CS" else E.pr_paper()).at_reduced_temperature(wl.t_over_tc)
-g, l = E.maxwell(e)
-mask, rho0 = wl.mask(), wl.rho0(l, g)
-crop = {crop}
-if crop:   # a window of the workload (mask and initial density) around the lower part of the body
-    # and the gas below it: no liquid-gas interface crosses the window's (periodic) faces
-    c = [int(round(v)) for v in wl.body_center[::-1]]
-    c[0] -= 24
-    win = tuple(slice(ci - crop // 2, ci + crop // 2) for ci in c)
-    mask, rho0 = np.ascontiguousarray(mask[win]), np.ascontiguousarray(rho0[win])
-geo = lbm.Geometry(mask, wl.lattice)
-p = lbm.Params(wl.lattice, e, sigma={sigma}, rho_l=l, rho_g=g, kappa=wl.kappa)
-f = lbm.init_state(rho0, geo)
+wls = W.{ctor}
+wls = wls if isinstance(wls, list) else [wls]
+grids, nodes = [], 0
+for wl in wls:
+    e = (E.cs_config() if wl.eos == "CS" else E.pr_paper()).at_reduced_temperature(wl.t_over_tc)
+    g, l = E.maxwell(e)
+    if {scale_kappa} and wl.kappa < 0:   # drawn in units of (rho_l - rho_g)
+        wl.kappa *= (l - g)
+    mask, rho0 = wl.mask(), wl.rho0(l, g)
+    crop = {crop}
+    if crop:   # a window of the workload (mask and initial density) around the lower part of the body
+        # and the gas below it: no liquid-gas interface crosses the window's (periodic) faces
+        c = [int(round(v)) for v in wl.body_center[::-1]]
+        c[0] -= 24
+        win = tuple(slice(ci - crop // 2, ci + crop // 2) for ci in c)
+        mask, rho0 = np.ascontiguousarray(mask[win]), np.ascontiguousarray(rho0[win])
+    geo = lbm.Geometry(mask, wl.lattice)
+    p = lbm.Params(wl.lattice, e, sigma={sigma}, rho_l=l, rho_g=g, kappa=wl.kappa)
+    grids.append([geo, p, lbm.init_state(rho0, geo)])
+    nodes += int(mask.size)
 for _ in range({warmup}):
-    f = lbm.step(f, geo, p)
+    for gr in grids:
+        gr[2] = lbm.step(gr[2], gr[0], gr[1])
 times = []
 for _ in range({steps}):
     t = time.perf_counter()
-    f = lbm.step(f, geo, p)
+    for gr in grids:
+        gr[2] = lbm.step(gr[2], gr[0], gr[1])
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times, "nodes": int(mask.size)}}))
+print(json.dumps({{"times": times, "nodes": nodes}}))
 """
 
 
 # the 256^3 sphere's oracle sample: a 96^3 window of it around the sphere's lower half
 C3_ORACLE_WINDOW = 96
+# the 96-grid batch's oracle sample: its first instances, stepped in turn
+C4_ORACLE_INSTANCES = 4
 
 
 def run_oracle(wl_name: str, steps: int, warmup: int, procs: int = 1):
     """Step times of `procs` concurrent single-thread oracle processes (one list per process) and
     the grid's node count."""
-    ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()", "c4": "c4_batch(96)[0]"}.get(
+    ctor = {"c1": "c1_parity_cylinder()", "c3": "c3_sphere_256()", "c4": f"c4_batch(96)[:{C4_ORACLE_INSTANCES}]"}.get(
         wl_name, "c2_cylinder_600x400(kappa=0.15)")
     crop = C3_ORACLE_WINDOW if wl_name == "c3" else 0
-    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps, crop=crop)
+    code = ORACLE_SNIPPET.format(root=ROOT, ctor=ctor, sigma=0.12, warmup=warmup, steps=steps, crop=crop,
+                                 scale_kappa=wl_name == "c4")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
                            env=env) for _ in range(procs)]
@@ -248,7 +259,8 @@ def cpu_baseline(wl_name: str, target_s: float = 15.0, all_cores: bool = True):
     total = sum(times)
     what = (f"a {C3_ORACLE_WINDOW}^3 window of the 256^3 sphere workload (mask and initial density of "
             f"z 28..123 around the sphere's lower half, periodic)" if wl_name == "c3"
-            else f"one {nodes}-node grid of the workload")
+            else (f"the first {C4_ORACLE_INSTANCES} instances of the batch ({nodes} nodes), stepped in turn"
+                  if wl_name == "c4" else f"one {nodes}-node grid of the workload"))
     res = {"value": round(nodes * n / total / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{n} FP64 oracle steps of {what}, one thread"}
     procs = os.cpu_count() or 1
@@ -806,7 +818,9 @@ def run_ours(args):
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": alg_bytes, "kernel": run.kernel_name(),
                 "frac_fluid_only": round(achieved * fluid / nodes / peak, 4),
-                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS}
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS,
+                "bytes_per_lu": {"minimum": bytes_per_lu(lattice, precision),
+                                 "measured_ncu": None if traffic is None else round(traffic / nodes, 2)}}
 
     # a sustained run of about one second (more clock samples than the K timed steps give)
     sustained = None
@@ -847,7 +861,10 @@ def run_ours(args):
     others = None
     if not args.no_extras and args.workload == "c2":
         def c3_extras(r, w, c, m, r0):
-            out = {"traffic": NCU_TRAFFIC.get(("c3", "fp32", ztma_kernel_hash())),
+            tr = NCU_TRAFFIC.get(("c3", "fp32", ztma_kernel_hash()))
+            out = {"traffic": tr,
+                   "bytes_per_lu": {"minimum": bytes_per_lu("D3Q19", "fp32"),
+                                    "measured_ncu": None if tr is None else round(tr / sum(x.nodes for x in w), 2)},
                    "e2e": e2e_rate(L, c, m, r0, w, args.steps, stream)}
             if rank == 0 and not args.no_cpu_baseline:
                 try:
@@ -857,7 +874,13 @@ def run_ours(args):
             return out
 
         def c4_extras(r, w, c, m, r0):
-            return {"batched_vs_separate": batched_vs_separate(L, torch, stream, r, c, m, r0, max(16, args.steps // 2))}
+            out = {"batched_vs_separate": batched_vs_separate(L, torch, stream, r, c, m, r0, max(16, args.steps // 2))}
+            if rank == 0 and not args.no_cpu_baseline:
+                try:
+                    out["cpu_baseline"] = cpu_baseline("c4", target_s=10.0, all_cores=False)
+                except Exception as exc:   # a reported baseline only
+                    out["cpu_baseline"] = {"error": str(exc)[:200]}
+            return out
 
         others = {"c3": device_rate(L, torch, stream, "c3", max(100, args.steps), flush, extras=c3_extras),
                   "c4": device_rate(L, torch, stream, "c4", max(50, args.steps), flush, extras=c4_extras),
