@@ -874,7 +874,8 @@ def run_ours(args):
             return out
 
         def c4_extras(r, w, c, m, r0):
-            out = {"batched_vs_separate": batched_vs_separate(L, torch, stream, r, c, m, r0, max(16, args.steps // 2))}
+            out = {"batched_vs_separate": batched_vs_separate(L, torch, stream, r, c, m, r0, max(16, args.steps // 2)),
+                   "e2e": e2e_rate(L, c, m, r0, w, args.steps, stream)}
             if rank == 0 and not args.no_cpu_baseline:
                 try:
                     out["cpu_baseline"] = cpu_baseline("c4", target_s=10.0, all_cores=False)
