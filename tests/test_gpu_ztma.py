@@ -129,3 +129,24 @@ def test_ztma_state_round_trip():
         L.lbm_load_state(sim.h, blob)
         sim.step(1)
         assert np.array_equal(sim.get_state(), s6)
+
+
+@pytest.mark.parametrize("plate", [(0, 2), (35, 37)])
+def test_ztma_plate_band(plate):
+    """A flat plate filling whole planes (at the bottom, so that its neighbourhood wraps to the top
+    planes, or in the middle of the z-range) with a drop on it: every column's z-range is cut into a
+    band on the path for planes near solids and bulk pieces on both sides of it, the last bulk piece
+    shorter than the minimum and joined to its neighbour.  One step from a common state against the
+    oracle covers every plane exactly once."""
+    from oracle import eos as E
+    shape = (70, 16, 64)                                   # (nz, ny, nx): 2 x 2 boxed columns
+    eos = E.cs_config().at_reduced_temperature(0.7)
+    g, l = E.maxwell(eos)
+    mask = np.zeros(shape, np.uint8)
+    mask[plate[0]:plate[1]] = 1
+    dc = (32.0, 8.0, float(plate[1] + 5))
+    rho = W.tanh_drop_density(shape, dc, 6.0, l, g) + W.density_noise(shape, 1e-6)
+    rho = np.where(mask != 0, g, rho)
+    case = Case("D3Q19", shape, mask, rho, kappa=0.1, drop_hint=dc, rho_ref=g)
+    s0, s1, ref = _one_step(case, "ztma")
+    assert np.max(np.abs(s1 - ref)) <= 2e-6 * np.max(np.abs(ref))
