@@ -607,8 +607,25 @@ lbm_status init_impl(const lbm_config* cfg, const uint8_t* solid_mask, const dou
     CKI(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "memset err");
     CKI(cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream), "memset f");   // padding included
     CKI(cudaMemsetAsync(h->f[1], 0, h->fbytes, h->stream), "memset f");
-    CKI(cudaMemcpyAsync(h->d_wall_id, ms.wall_id.get(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream),
-        "copy wall_id");
+    {
+        // the per-node wall index map, built on the device from the wall list
+        const size_t nwl = h->wall_nodes.size();
+        std::vector<int32_t> idx(nwl);
+        for (size_t i = 0; i < nwl; ++i) idx[i] = int32_t(h->wall_nodes[i]);
+        int* d_idx = nullptr;
+        if (nwl) {
+            CKI(dmalloc(&d_idx, sizeof(int32_t) * nwl, h->stream), "cudaMalloc wall list");
+            e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * nwl, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) {
+                dfree(d_idx, h->stream);
+                return oom(e, "copy wall list");
+            }
+        }
+        e = launch_wall_ids(d_idx, int(nwl), h->d_wall_id, N, h->stream);
+        dfree(d_idx, h->stream);
+        if (e != cudaSuccess) return oom(e, "wall ids");
+        if (nwl) h->launches += 1;
+    }
     {
         std::vector<double> kap(nw ? nw : 1, c.kappa);
         if (kappa_per_wall)

@@ -158,6 +158,9 @@ int batched_ctas_per_sm(int lat, int prec);
 // T_NEARWALL (within Euclidean distance 3 of a solid node) and T_BULK (fluid with every lattice
 // neighbour fluid).
 cudaError_t launch_classify(int lat, const uint8_t* mask, uint8_t* type, int nx, int ny, int nz, cudaStream_t s);
+// Per-node wall index map of N nodes: -1 everywhere, then wall_id[idx[i]] = i for the nw wall nodes
+// idx (device, ascending linear indices).
+cudaError_t launch_wall_ids(const int* idx, int nw, int* wall_id, long long N, cudaStream_t s);
 
 // Observables reduction over rho/u/type: out[0..3] = mass, rho_max, rho_min, max |u|^2;
 // out[4..17] = interface-point moments (n, Sx, Sy, Sz, Sxx, Syy, Szz, Sxy, Sxz, Syz, Sx r2, Sy r2,

@@ -141,17 +141,7 @@ void scan_mask(const uint8_t* mask, int nx, int ny, int nz, int D, const int t[3
     nw = off[nt];
     out->nfluid = N - ns;
     out->wall_nodes.resize(nw);
-    out->wall_id.reset(new int32_t[(size_t)N]);   // filled by the threads, not zeroed first
-    parallel_for(nt, nt, [&](int k) {
-        const long long g0 = N * k / nt, g1 = N * (k + 1) / nt;
-        std::fill(out->wall_id.get() + g0, out->wall_id.get() + g1, -1);
-    });
-    parallel_for(nt, nt, [&](int k) {
-        for (size_t i = 0; i < part[k].size(); ++i) {
-            out->wall_nodes[off[k] + i] = part[k][i];
-            out->wall_id[(size_t)part[k][i]] = int32_t(off[k] + i);
-        }
-    });
+    parallel_for(nt, nt, [&](int k) { std::copy(part[k].begin(), part[k].end(), out->wall_nodes.begin() + off[k]); });
     out->tile_solid = tile_solid_flags(mask, nx, ny, nz, t, D, nt);
     if (pair_t) {
         const int tp[3] = {pair_t[0], pair_t[1], 1};

@@ -1,9 +1,8 @@
 // Host pass over a solid mask at initialisation: the wall nodes (solid nodes with a fluid lattice
-// neighbour, the nodes that carry virtual densities, Eqs. 16-17) and the solid flags per tile of the
-// step kernels.  Row-based (no per-node index arithmetic), optionally split over threads by rows.
+// neighbour, the nodes that carry virtual densities, Eqs. 16-17; the per-node index map is built from
+// them on the device) and the solid flags per tile of the step kernels.  Row-based (no per-node index arithmetic), optionally split over threads by rows.
 #pragma once
 #include <cstdint>
-#include <memory>
 #include <thread>
 #include <vector>
 
@@ -12,7 +11,6 @@ namespace lbmwet {
 struct MaskScan {
     long long nfluid = 0;
     std::vector<int64_t> wall_nodes;   // ascending linear indices
-    std::unique_ptr<int32_t[]> wall_id;   // per node: its index in wall_nodes, -1 off the wall
     std::vector<uint8_t> tile_solid;   // per tile of the step kernels
     std::vector<uint8_t> pair_solid;   // per tile of the D2Q9 FP32 pair kernel (empty unless asked for)
 };
@@ -23,7 +21,7 @@ struct MaskScan {
 std::vector<uint8_t> tile_solid_flags(const uint8_t* mask, int nx, int ny, int nz, const int t[3], int D,
                                       int threads = 1);
 
-// The full scan: fluid count, wall list and ids (neighbourhood of the D2Q9 or D3Q19 velocity set,
+// The full scan: fluid count, wall list (neighbourhood of the D2Q9 or D3Q19 velocity set,
 // periodic wrap), the step-kernel tile flags for tile shape t and, when pair_t is given, the pair
 // kernel's.  `threads` > 1 splits the rows over that many threads.
 void scan_mask(const uint8_t* mask, int nx, int ny, int nz, int D, const int t[3], const int* pair_t, int threads,

@@ -844,6 +844,18 @@ cudaError_t launch_get_state(int lat, int prec, const void* fin, const DevParams
     return cudaGetLastError();
 }
 
+// wall_id[idx[i]] = i for the nw wall nodes (every other entry was set to -1 before)
+__global__ void wall_id_scatter(const int* __restrict__ idx, int nw, int* __restrict__ wall_id) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) wall_id[idx[i]] = i;
+}
+
+cudaError_t launch_wall_ids(const int* idx, int nw, int* wall_id, long long N, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(wall_id, 0xFF, sizeof(int) * (size_t)N, s);   // -1 everywhere
+    if (e != cudaSuccess || nw == 0) return e;
+    wall_id_scatter<<<grid_for(nw), 256, 0, s>>>(idx, nw, wall_id);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_classify(int lat, const uint8_t* mask, uint8_t* type, int nx, int ny, int nz, cudaStream_t s) {
     const unsigned g = grid_for((long long)nx * ny * nz);
     if (lat == LAT_D2Q9) classify_kernel<D2Q9><<<g, 256, 0, s>>>(mask, type, nx, ny, nz);

@@ -7,17 +7,15 @@
 
 extern "C" {
 
-// Returns the wall count; fills nfluid, wall_nodes (capacity N), wall_id (N), tile flags (capacity
+// Returns the wall count; fills nfluid, wall_nodes (capacity N) and the tile flags (capacity
 // max_tiles, count in *n_tiles) for tile shape t.
 long long maskscan_run(const uint8_t* mask, int nx, int ny, int nz, int D, const int* t, int threads,
-                       long long* nfluid, long long* wall_nodes, int* wall_id, uint8_t* tiles, long long max_tiles,
+                       long long* nfluid, long long* wall_nodes, uint8_t* tiles, long long max_tiles,
                        long long* n_tiles) {
     lbmwet::MaskScan s;
     lbmwet::scan_mask(mask, nx, ny, nz, D, t, nullptr, threads, &s);
     *nfluid = s.nfluid;
-    const long long N = (long long)nx * ny * nz;
     for (size_t i = 0; i < s.wall_nodes.size(); ++i) wall_nodes[i] = s.wall_nodes[i];
-    std::memcpy(wall_id, s.wall_id.get(), sizeof(int) * (size_t)N);
     *n_tiles = (long long)s.tile_solid.size();
     if (*n_tiles <= max_tiles) std::memcpy(tiles, s.tile_solid.data(), s.tile_solid.size());
     return (long long)s.wall_nodes.size();

@@ -1,10 +1,10 @@
-"""The host scan of the solid mask that lbm_init runs (csrc/maskscan.cpp): wall nodes, wall ids and the
-per-tile solid flags, against a direct numpy statement of their definitions, on random and ball
+"""The host scan of the solid mask that lbm_init runs (csrc/maskscan.cpp): wall nodes and the per-tile
+solid flags, against a direct numpy statement of their definitions, on random and ball
 masks in 2D and 3D, with the row split over one and several threads.
 
 Definitions checked: a wall node is a solid node with at least one fluid node among its lattice
 neighbours x + e_a (D2Q9: the 8 around it; D3Q19: the 18 of the velocity set), periodic in every
-axis; wall ids number the wall nodes in ascending linear index; a tile (t0 x t1 x t2, ragged at the
+axis, listed in ascending linear index; a tile (t0 x t1 x t2, ragged at the
 far edges) is flagged when a solid node lies in its box: the cells it covers, wrapped, plus 3 cells
 on each side (no z halo in 2D), wrapped."""
 import ctypes as C
@@ -47,13 +47,12 @@ def run(lib, mask, D, t, threads):
     tt = (C.c_int * 3)(*t)
     nfluid, ntiles = C.c_longlong(), C.c_longlong()
     walls = np.zeros(N, np.int64)
-    wid = np.zeros(N, np.int32)
     cap = 1 << 20
     tiles = np.zeros(cap, np.uint8)
     nw = lib.maskscan_run(m.ctypes.data_as(C.c_void_p), nx, ny, nz, D, tt, threads, C.byref(nfluid),
-                          walls.ctypes.data_as(C.c_void_p), wid.ctypes.data_as(C.c_void_p),
-                          tiles.ctypes.data_as(C.c_void_p), C.c_longlong(cap), C.byref(ntiles))
-    return nfluid.value, walls[:nw], wid, tiles[:ntiles.value]
+                          walls.ctypes.data_as(C.c_void_p), tiles.ctypes.data_as(C.c_void_p), C.c_longlong(cap),
+                          C.byref(ntiles))
+    return nfluid.value, walls[:nw], tiles[:ntiles.value]
 
 
 def reference(mask, D, t):
@@ -65,8 +64,6 @@ def reference(mask, D, t):
         fluid_nb |= np.roll(~solid, shift=(-ez, -ey, -ex), axis=(0, 1, 2))
     wall = solid & fluid_nb
     walls = np.flatnonzero(wall.reshape(-1))
-    wid = np.full(mask.size, -1, np.int64)
-    wid[walls] = np.arange(len(walls))
     nz, ny, nx = mask.shape
     n = (nx, ny, nz)
     halo = (3, 3, 3 if D == 3 else 0)
@@ -76,7 +73,7 @@ def reference(mask, D, t):
         k = (kx, ky, kz)
         idx = [np.unique([(k[d] * t[d] + o) % n[d] for o in range(-halo[d], t[d] + halo[d])]) for d in range(3)]
         flags[kz, ky, kx] = solid[np.ix_(idx[2], idx[1], idx[0])].any()
-    return int((~solid).sum()), walls, wid, flags.reshape(-1)
+    return int((~solid).sum()), walls, flags.reshape(-1)
 
 
 def masks():
@@ -97,12 +94,11 @@ def masks():
 @pytest.mark.parametrize("threads", [1, 3])
 def test_mask_scan_matches_definitions(lib, name, mask, D, threads):
     t = (32, 16, 1) if D == 2 else (32, 4, 8)
-    nf, walls, wid, tiles = run(lib, mask, D, t, threads)
-    rf, rwalls, rwid, rtiles = reference(mask, D, t)
+    nf, walls, tiles = run(lib, mask, D, t, threads)
+    rf, rwalls, rtiles = reference(mask, D, t)
     assert nf == rf
     assert np.array_equal(walls, rwalls)
-    assert np.array_equal(wid, rwid)
     assert np.array_equal(tiles, rtiles)
     if D == 2:   # a second tile shape, with ragged tiles on a narrow grid
-        _, _, _, tiles2 = run(lib, mask, D, (3, 2, 1), threads)
-        assert np.array_equal(tiles2, reference(mask, D, (3, 2, 1))[3])
+        _, _, tiles2 = run(lib, mask, D, (3, 2, 1), threads)
+        assert np.array_equal(tiles2, reference(mask, D, (3, 2, 1))[2])
