@@ -45,10 +45,10 @@ UNIT = "MLUPS"
 # of the kernel code: when the code changes the figure is stale and reported as null.
 NCU_TRAFFIC = {
     # pair_step_batched, 600 x 400 sweep of 24 grids: dram__bytes_read.sum + dram__bytes_write.sum of
-    # one launch (214,383,104 + 159,419,648 bytes)
-    ("c2", "fp32", "71b039197257b4f9"): 373802752,
-    # ztma_step, 256^3 sphere: one launch (1,582,688,256 + 1,218,136,832 bytes)
-    ("c3", "fp32", "9905e59a49d761de"): 2800825088,
+    # one launch (214.32 + 159.71 MB as ncu prints them)
+    ("c2", "fp32", "96c84a23e00f20c2"): 374030000,
+    # ztma_step, 256^3 sphere: one launch (1.59 + 1.22 GB as ncu prints them)
+    ("c3", "fp32", "0cdbad1c831bf63f"): 2810000000,
 }
 
 
@@ -57,7 +57,7 @@ NCU_TRAFFIC = {
 # instructions of one launch) / nodes = (2 x 478,996,920 + 503,049,168 + 231,630,840) / 5,760,000;
 # keyed by a hash of the tile kernel's code.
 FP64_FLOPS_PER_NODE = {
-    ("c2", "58124fc042b67c45"): 293.87,
+    ("c2", "f7839bf8d649589f"): 293.87,
 }
 # FP64 peak of a GB300 from its unit counts and clock: 1.25 TFLOP/s nominal is 4 FP64 flops (2 FMA) per
 # SM per clock at 2.07 GHz, so 152 SMs x 4 x 2.07 GHz = 1258.6 GFLOP/s.
