@@ -163,6 +163,16 @@ def c3_sphere_256() -> Workload:
                     (128.0, 128.0, 185.0), 45.0, "CS", 0.7, 0.2, 5000)
 
 
+def sphere_drop_64(steps: int = 1000, kappa: float = 0.2) -> Workload:
+    """64^3 D3Q19 drop on a sphere, for runs the oracle can finish: the 256^3 workload's sphere scaled
+    by 1/4 (R = 10, at (32, 32, 20)) with a tangent drop r = 16 at (32, 32, 46), C-S 0.7 Tc, wall
+    parameter kappa (0.2 as in the full workload).  The drop is larger than the scaled 11.25: at that
+    radius the Laplace pressure raises the equilibrium vapour density enough that the whole drop
+    evaporates into the box within 1000 steps (Kelvin effect), leaving no interface to fit."""
+    return Workload("d3q19_sphere_drop_64cube", "D3Q19", (64, 64, 64), (32.0, 32.0, 20.0), 10.0,
+                    (32.0, 32.0, 46.0), 16.0, "CS", 0.7, kappa, steps)
+
+
 def c4_batch(n_instances: int = 96, seed: int = BATCH_SEED) -> list:
     """Batched 2D instances: square N ~ U{128..512}, cylinder radius U(0.15,0.25) N at the centre,
     drop radius U(1.1,1.4) x cylinder radius placed tangent above it, kappa per instance.
