@@ -95,9 +95,11 @@ typedef enum { LBM_BODY_NONE = 0, LBM_BODY_BALL = 1, LBM_BODY_PLANE = 2 } lbm_bo
  *   has chosen one.  A y-march handle that records a trajectory for the adjoint steps with TILE
  *   from lbm_record on.
  * D3Q19 (every kernel marches z-planes through 32-plane chunks of x-y columns):
- *   ZTMA (FP32 only): 32 x 8 columns whose lead plane's 19 pull boxes are staged in shared memory
- *   by TMA, two planes in flight, two cells per thread in packed FP32x2 arithmetic; chunks holding
- *   solids run the z-pair march.  PAIR (FP32 only): the z-pair march, 32 x 4 columns, two planes
+ *   ZTMA (FP32 only): 32 x 8 columns cut along z into the work items of lbm_d3q19_work_list, one
+ *   CTA per item; the lead plane's 19 pull boxes are staged in shared memory by TMA, two planes in
+ *   flight, two cells per thread in packed FP32x2 arithmetic; items on planes near a solid also
+ *   stage node types and do the bounce-back and virtual-density work; columns cut by the grid's
+ *   edge (ragged) run the z-pair march.  PAIR (FP32 only): the z-pair march, 32 x 4 columns, two planes
  *   per thread.  TILE: the scalar z-march (the only D3Q19 kernel in FP64).  AUTO: ZTMA in FP32
  *   (PAIR where the rows are not a multiple of 16 bytes), TILE in FP64.  The FP32 kernels agree up
  *   to FP32 rounding. */
@@ -288,6 +290,22 @@ lbm_status lbm_grid_shape(const lbm_handle* h, int32_t* shape4);
 
 /* Number of kernel launches this handle has issued (step kernels and others), for accounting. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
+
+/* The work list of the TMA-staged D3Q19 z-march (LBM_KERNEL_ZTMA) for a solid mask: host code only
+ * (no device, no handle), the list lbm_init builds for an FP32 D3Q19 handle on that kernel.  One
+ * time step (Eqs. 1-7 with the Eq. 16-17 walls) is split into items, one CTA each: item i is the 5
+ * int32 values items[5i .. 5i+4] = {bx, by, z0, z1, solid}: the column of cells x in [32 bx,
+ * 32 bx + 32), y in [8 by, 8 by + 8) (clipped to the grid), planes z0 <= z < z1, and solid = 1 where
+ * the item takes the path for planes within 3 planes of a solid near the column (node types,
+ * bounce-back, virtual densities) or, for a column cut by the grid's edge, the z-pair march.  Every
+ * (column, plane) lies in exactly one item; items run in ascending z0, then by, then bx.
+ *   solid_mask: host, nz*ny*nx bytes (x fastest), nonzero = solid; read only during the call.
+ *   items: host array of 5 * capacity int32, owned by the caller, or NULL to ask for the count.
+ *   count: receives the number of items.
+ * Errors: LBM_ERR_ARG (NULL mask or count, a size below 1, more than 2^31 / 19 nodes, or items
+ * given with capacity below the count; nothing is written to items then). */
+lbm_status lbm_d3q19_work_list(const uint8_t* solid_mask, int32_t nx, int32_t ny, int32_t nz, int32_t* items,
+                               int64_t capacity, int64_t* count);
 
 /* Step kernel the handle's lbm_step uses now (see lbm_step_kernel): LBM_KERNEL_TILE,
  * LBM_KERNEL_YMARCH or LBM_KERNEL_PAIR for D2Q9; LBM_KERNEL_ZTMA, LBM_KERNEL_PAIR or

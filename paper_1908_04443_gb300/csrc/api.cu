@@ -1694,6 +1694,26 @@ lbm_status lbm_grid_shape(const lbm_handle* h, int32_t* shape4) {
     return LBM_OK;
 }
 
+lbm_status lbm_d3q19_work_list(const uint8_t* solid_mask, int32_t nx, int32_t ny, int32_t nz, int32_t* items,
+                               int64_t capacity, int64_t* count) {
+    if (!solid_mask || !count) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
+    if ((long long)nx * ny * nz > (1LL << 31) / 19) return fail(nullptr, LBM_ERR_ARG, "grid too large");
+    const std::vector<ZItem> v = ztma_work_list(solid_mask, nx, ny, nz);
+    *count = (int64_t)v.size();
+    if (!items) return LBM_OK;
+    if (capacity < (int64_t)v.size()) return fail(nullptr, LBM_ERR_ARG, "capacity below the item count");
+    for (size_t i = 0; i < v.size(); ++i) {
+        int32_t* o = items + 5 * i;
+        o[0] = v[i].bx;
+        o[1] = v[i].by;
+        o[2] = v[i].z0;
+        o[3] = v[i].z1;
+        o[4] = v[i].solid;
+    }
+    return LBM_OK;
+}
+
 lbm_handle* lbm_batch_handle(lbm_batch* b, int32_t i) {
     if (!b || i < 0 || i >= (int32_t)b->inst.size()) return nullptr;
     return b->inst[i];

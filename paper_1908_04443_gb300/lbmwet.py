@@ -99,6 +99,8 @@ def _load():
         "lbm_batch_observables_fields": (C.c_int, [C.c_void_p, C.POINTER(lbm_obs), C.POINTER(C.c_void_p),
                                                    C.POINTER(C.c_void_p)]),
         "lbm_grid_shape": (C.c_int, [H, C.POINTER(C.c_int32)]),
+        "lbm_d3q19_work_list": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                          C.POINTER(C.c_int64)]),
         "lbm_batch_handle": (C.c_void_p, [C.c_void_p, C.c_int32]),
         "lbm_batch_size": (C.c_int32, [C.c_void_p]),
         "lbm_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
@@ -128,7 +130,7 @@ EXPORTED = ("lbm_coexistence", "lbm_critical_temperature", "lbm_init", "lbm_step
             "lbm_batch_tuning_report", "lbm_batch_set_kernels", "lbm_batch_autotune_forget",
             "lbm_destroy", "lbm_last_error", "lbm_status_string", "lbm_record", "lbm_adjoint", "lbm_batch_init", "lbm_batch_step",
             "lbm_batch_enqueue_steps", "lbm_batch_observables", "lbm_batch_observables_fields", "lbm_grid_shape",
-            "lbm_batch_handle", "lbm_batch_size",
+            "lbm_d3q19_work_list", "lbm_batch_handle", "lbm_batch_size",
             "lbm_batch_kernel_launches", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
@@ -250,6 +252,22 @@ def lbm_grid_shape(h) -> Tuple[int, int, int, int]:
     a = (C.c_int32 * 4)()
     _check(_lib.lbm_grid_shape(h, a), h)
     return int(a[0]), int(a[1]), int(a[2]), int(a[3])
+
+
+def lbm_d3q19_work_list(mask) -> np.ndarray:
+    """Work items of the TMA-staged D3Q19 z-march for a solid mask of shape (nz, ny, nx): an
+    (items, 5) int32 array of rows (bx, by, z0, z1, solid).  Host code only (no device needed)."""
+    m = np.asarray(mask)
+    if m.ndim != 3:
+        raise ValueError(f"mask must have shape (nz, ny, nx), got {m.shape}")
+    nz, ny, nx = m.shape
+    mb = _mask_bytes(m)
+    mp = mb.ctypes.data_as(C.c_void_p)
+    n = C.c_int64(0)
+    _check(_lib.lbm_d3q19_work_list(mp, nx, ny, nz, None, 0, C.byref(n)))
+    out = np.zeros((n.value, 5), np.int32)
+    _check(_lib.lbm_d3q19_work_list(mp, nx, ny, nz, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+    return out
 
 
 def _nodes_dim(h) -> Tuple[int, int]:
