@@ -104,3 +104,30 @@ def test_fig5_angles_follow_sigma(kw, paper):
     is why the flat-interface calibration (0.11) stays the default."""
     o, _, _ = _run(kw, sigma=0.09)
     assert abs(o.theta_deg - paper) < 4.0
+
+
+# Fig. 14: the sphere of Sec. IV.C (200 x 200 x 280, R = 50 at (100, 100, 100), drop r = 45 at (100, 100,
+# 180), the Sec. IV.A PR EOS at 0.86 Tc): (wall parameter, the paper's angle, bound in degrees)
+FIG14 = [(0.2, 53.0, 3.0), (0.0, 88.0, 3.0)]
+
+
+@pytest.mark.parametrize("kappa,paper,tol", FIG14)
+def test_fig14_sphere_angles(kappa, paper, tol):
+    """The improved scheme on the sphere (phi = 1.2 and phi = 1 give 53 and 88 degrees in the paper),
+    FP32 with the default D3Q19 step (the TMA-staged z-march, its ragged x columns on the z-pair
+    march), sigma = 0.11 as in 2D, after 20,000 steps: measured 53.2 and 86.6 degrees (53.3 and 86.9
+    after 40,000).  The paper's third case (drho = 0.55, 145 degrees) is not held to a bound: that
+    drop keeps moving on the sphere and its angle swings between about 146 and 169 degrees from one
+    5,000-step sample to the next (bench.py reports the range)."""
+    import workloads as W
+    wl = W.sphere_fig14(kappa)
+    case = drop_on_cylinder(wl.shape, wl.body_center, wl.body_radius, wl.drop_center, wl.drop_radius,
+                            kappa=kappa, eos_kind="PR", t_over_tc=0.86, sigma=0.11, lattice="D3Q19")
+    case.rho_ref = case.bounds()[0]
+    with case.gpu("fp32") as sim:
+        assert sim.step_kernel() == "ztma"
+        sim.step(20000)
+        o = sim.observables()[0]
+    assert abs(o.theta_deg - paper) < tol
+    assert o.u_max < 0.006
+

@@ -163,6 +163,14 @@ def c3_sphere_256() -> Workload:
                     (128.0, 128.0, 185.0), 45.0, "CS", 0.7, 0.2, 5000)
 
 
+def sphere_fig14(kappa: float, steps: int = 30000) -> Workload:
+    """The Sec. IV.C sphere as the paper sets it up (Fig. 14): 200 x 200 x 280 D3Q19, sphere R = 50 at
+    (100, 100, 100), drop r = 45 at (100, 100, 180), Peng-Robinson at 0.86 Tc (the Sec. IV.A EOS and
+    densities), wall parameter kappa (0.2: phi = 1.2; 0: phi = 1; -0.55: drho = 0.55)."""
+    return Workload("fig14_sphere_200x200x280", "D3Q19", (280, 200, 200), (100.0, 100.0, 100.0), 50.0,
+                    (100.0, 100.0, 180.0), 45.0, "PR", 0.86, kappa, steps)
+
+
 def sphere_drop_64(steps: int = 1000, kappa: float = 0.2) -> Workload:
     """64^3 D3Q19 drop on a sphere, for runs the oracle can finish: the 256^3 workload's sphere scaled
     by 1/4 (R = 10, at (32, 32, 20)) with a tangent drop r = 16 at (32, 32, 46), C-S 0.7 Tc, wall
