@@ -602,6 +602,58 @@ def paper_context(L, stream, steps=30000):
                     "calibrated on a flat interface; sigma = 0.09 brings the three angles within 4 degrees)"}
 
 
+def observables_rate(L, torch, run, wls, precision, stream, calls=20):
+    """The observables (mass, density extremes, max |u|, contact angle: on demand, not per step)
+    through the public call without fields, on every instance of the run: wall time per call after
+    warm-up, against the minimum of one read of the distributions (Q values per node); with the
+    fields pass of the first instance alone (device time) and its reductions through the
+    allocation-free call (wall time: two kernels, an 18-double copy and a synchronisation)."""
+    obs = (lambda: L.lbm_batch_observables(run.b)) if run.batch else (lambda: L.lbm_observables(run.handles[0]))
+    for _ in range(3):
+        obs()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        obs()
+    ms = (time.perf_counter() - t0) / calls * 1e3
+    h, n0 = run.handles[0], wls[0].nodes
+    d = 2 if wls[0].lattice == "D2Q9" else 3
+    rho = torch.empty(n0, dtype=torch.float64, device="cuda")
+    u = torch.empty(d * n0, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        L.lbm_fields_device(h, rho.data_ptr(), u.data_ptr())
+    torch.cuda.synchronize()
+    ev[0].record(stream)     # the library's stream, on which the fields pass runs
+    for _ in range(calls):
+        L.lbm_fields_device(h, rho.data_ptr(), u.data_ptr())
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    fields_ms = ev[0].elapsed_time(ev[1]) / calls
+    for _ in range(3):
+        L.lbm_observables_noalloc(h, rho.data_ptr(), u.data_ptr())
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        L.lbm_observables_noalloc(h, rho.data_ptr(), u.data_ptr())
+    reduce_ms = (time.perf_counter() - t0) / calls * 1e3
+    q = 9 if d == 2 else 19
+    nodes = sum(wl.nodes for wl in wls)
+    min_bytes = q * (8 if precision == "fp64" else 4) * nodes
+    peak = 6800.0
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        with open(pk_path) as fh:
+            peak = json.load(fh).get("hbm_gbs", peak)
+    gbs = min_bytes / (ms * 1e-3) / 1e9
+    return {"call": "lbm_batch_observables" if run.batch else "lbm_observables", "instances": len(wls),
+            "ms_per_call": round(ms, 4), "algorithmic_bytes": min_bytes, "achieved_gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 4),
+            "first_instance": {"nodes": n0, "fields_pass_ms": round(fields_ms, 4),
+                               "reductions_noalloc_ms": round(reduce_ms, 4)},
+            "definition": "wall time per call without fields (fields pass, reductions, contact-angle fit, one "
+                          "synchronisation) over the minimum of one read of f (Q x 4 B per node in FP32)"}
+
+
 def paper_context_3d(L, stream, steps=30000, samples=(20000, 25000, 30000)):
     """The paper's static contact angles on a sphere (Sec. IV.C, Fig. 14: phi = 1.2, phi = 1 and drho =
     0.55 give 53, 88 and 145 degrees) beside the same runs here: 200 x 200 x 280 D3Q19, sphere R = 50,
@@ -909,6 +961,8 @@ def run_ours(args):
     if args.workload == "c2" and precision == "fp32" and not args.no_extras:
         err = {"one_step": err, "after_20000_steps": err_c2_golden(L, stream)}
 
+    observables = observables_rate(L, torch, run, wls, precision, stream)
+
     # batched launch vs one launch per instance (no L2 flush: back-to-back steps)
     bvs = None
     if run.batch and not args.no_extras:
@@ -925,7 +979,8 @@ def run_ours(args):
             out = {"traffic": tr,
                    "bytes_per_lu": {"minimum": bytes_per_lu("D3Q19", "fp32"),
                                     "measured_ncu": None if tr is None else round(tr / sum(x.nodes for x in w), 2)},
-                   "e2e": e2e_rate(L, c, m, r0, w, args.steps, stream)}
+                   "e2e": e2e_rate(L, c, m, r0, w, args.steps, stream),
+                   "observables": observables_rate(L, torch, r, w, "fp32", stream)}
             if rank == 0 and not args.no_cpu_baseline:
                 try:
                     out["cpu_baseline"] = cpu_baseline("c3", target_s=10.0, all_cores=False)
@@ -971,7 +1026,7 @@ def run_ours(args):
                            "note": "the same rate counting fluid nodes only (solid nodes are skipped)"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "wall_s_timed_region": round(t_wall, 4),
-            "kernel_hash": khash, "err_vs_oracle": err}
+            "kernel_hash": khash, "err_vs_oracle": err, "observables": observables}
     if sustained:
         line["sustained"] = sustained
     if bvs:

@@ -66,6 +66,13 @@ __device__ __forceinline__ void init_slots(double (&v)[NRED]) {
 
 __device__ __forceinline__ int wrapp(int v, int n) { return v >= n ? v - n : v; }
 
+// A double's bits as an int64 in the same order as the doubles (finite values; -0 below +0): the
+// sign-magnitude pattern of a negative value has its magnitude bits flipped.  The map is its own
+// inverse.  Comparisons and extremes then run on the integer pipe: the FP64 pipe of this GPU issues
+// under 2 operations per clock per SM, and the per-node compares would otherwise bound the pass.
+__device__ __forceinline__ long long ord_bits(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
+__device__ __forceinline__ long long ord(double x) { return ord_bits(__double_as_longlong(x)); }
+
 template <int DIM>
 __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ rho, const double* __restrict__ u,
                                                      const uint8_t* __restrict__ type, int nx, int ny, int nz,
@@ -74,34 +81,54 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
     const long long N = (long long)nx * ny * nz;
     double v[NRED];
     init_slots(v);
+    // density extremes and the largest |u|^2 as ordered integers (see ord); u^2 >= +0, whose bits
+    // are already in order
+    long long kmax = ord(-DBL_MAX), kmin = ord(DBL_MAX), ku = 0;
+    const long long kmid = ord(rho_mid);
     for (long long g = blockIdx.x * (long long)RB + threadIdx.x; g < N; g += (long long)gridDim.x * RB) {
-        const uint8_t t = type[g];
-        if (t & T_SOLID) continue;
-        const double r = rho[g];
-        v[0] += r;
-        v[1] = fmax(v[1], r);
-        v[2] = fmin(v[2], r);
-        double u2 = 0.0;
-        for (int c = 0; c < DIM; ++c) {
-            const double uc = u[(long long)c * N + g];
-            u2 += uc * uc;
-        }
-        v[3] = fmax(v[3], u2);
-        if (t & T_NEARWALL) continue;
         // (32-bit division: a grid holds fewer than 2^31 / 19 nodes)
         const unsigned gu = unsigned(g), q = gu / unsigned(nx);
         const int x = int(gu - q * unsigned(nx));
         const int y = int(q % unsigned(ny)), z = int(q / unsigned(ny));
+        // every load of the node and of its +x, +y (, +z) neighbours is issued before any branch, so
+        // that they are in flight together rather than one dependent round trip after another (the
+        // fields hold values at every node, solid ones included)
+        long long gn[DIM];
+        gn[0] = g - x + wrapp(x + 1, nx);
+        gn[1] = ((long long)z * ny + wrapp(y + 1, ny)) * nx + x;
+        if (DIM == 3) gn[DIM - 1] = ((long long)wrapp(z + 1, nz) * ny + y) * nx + x;
+        const uint8_t t = type[g];
+        const double r = rho[g];
+        double uc[DIM], rnb[DIM];
+        uint8_t tnb[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) uc[c] = u[(long long)c * N + g];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            tnb[a] = type[gn[a]];
+            rnb[a] = rho[gn[a]];
+        }
+        if (t & T_SOLID) continue;
+        const long long kr = ord(r);
+        v[0] += r;
+        kmax = kr > kmax ? kr : kmax;
+        kmin = kr < kmin ? kr : kmin;
+        double u2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) u2 += uc[c] * uc[c];
+        const long long k2 = __double_as_longlong(u2);
+        ku = k2 > ku ? k2 : ku;
+        if (t & T_NEARWALL) continue;
+        const int side = (kr > kmid) - (kr < kmid);   // sign of r - rho_mid
+        if (side == 0) continue;                      // a link from r == rho_mid never straddles
         // links +x, +y (, +z) to a fluid neighbour away from walls whose density straddles rho_mid
+#pragma unroll
         for (int axis = 0; axis < DIM; ++axis) {
-            const int xn = axis == 0 ? wrapp(x + 1, nx) : x;
-            const int yn = axis == 1 ? wrapp(y + 1, ny) : y;
-            const int zn = axis == 2 ? wrapp(z + 1, nz) : z;
-            const long long gn = ((long long)zn * ny + yn) * nx + xn;
-            const uint8_t tn = type[gn];
-            if (tn & (T_SOLID | T_NEARWALL)) continue;
-            const double rn = rho[gn];
-            if (!((r - rho_mid) * (rn - rho_mid) < 0.0)) continue;
+            if (tnb[axis] & (T_SOLID | T_NEARWALL)) continue;
+            const double rn = rnb[axis];
+            // the link straddles rho_mid: r - rho_mid and rn - rho_mid of opposite signs
+            const long long kn = ord(rn);
+            if (!(side > 0 ? kn < kmid : kn > kmid)) continue;
             const double tt = (rho_mid - r) / (rn - r);
             double px = x, py = y, pz = z;
             if (axis == 0) px += tt;
@@ -129,6 +156,9 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
             v[17] += r2;
         }
     }
+    v[1] = __longlong_as_double(ord_bits(kmax));
+    v[2] = __longlong_as_double(ord_bits(kmin));
+    v[3] = __longlong_as_double(ku);
     block_combine(v, partials + (long long)blockIdx.x * NRED);
 }
 
