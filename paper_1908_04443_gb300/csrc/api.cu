@@ -21,6 +21,7 @@
 #include "kernels.h"
 #include "lattice.cuh"
 #include "maskscan.h"
+#include "reduce.h"
 #include "plan.h"
 #include "wall_gf.h"
 
@@ -1095,6 +1096,7 @@ struct lbm_batch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
     double* h_stage = nullptr;         // pinned: per instance the reduction sums and the error word
+    double* d_stage = nullptr;         // the same on the device, filled by the reductions, copied at once
 };
 
 namespace {
@@ -1156,6 +1158,7 @@ void batch_free(lbm_batch* b) {
     dfree(b->d_tmaps, b->stream);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     b->h_stage = nullptr;
+    dfree(b->d_stage, b->stream);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -1647,25 +1650,25 @@ lbm_status lbm_batch_observables_fields(lbm_batch* b, lbm_obs* out_n, double* co
     const size_t n = b->inst.size(), W = NRED + 1;
     if (!b->h_stage)
         CKB(b, cudaHostAlloc(reinterpret_cast<void**>(&b->h_stage), sizeof(double) * W * n, cudaHostAllocDefault));
-    // every instance's fields, reduction and copies on the batch's stream, then one synchronisation
+    if (!b->d_stage) CKB(b, dmalloc(&b->d_stage, sizeof(double) * W * n, b->stream));
+    // every instance's fields and reduction on the batch's stream, each instance's sums and error
+    // word into its slot of one device array, one copy of the array, then one synchronisation
     for (size_t i = 0; i < n; ++i) {
         lbm_handle* h = b->inst[i];
         lbm_status st = ensure_obs_buffers(h);
         if (st != LBM_OK) return bfail(b, st, "instance " + std::to_string(i) + ": " + h->err);
         CKB(b, launch_fields(h->lat, h->prec, h->f[h->cur], h->dp, h->d_rho, h->d_u, h->stream));
         const double mid = 0.5 * (h->rho_l + h->rho_g);
-        CKB(b, launch_reduce(h->D, h->d_rho, h->d_u, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid,
-                             h->cfg.drop_hint, h->d_partials, h->d_red, h->stream));
+        CKB(b, launch_reduce_slot(h->D, h->d_rho, h->d_u, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid,
+                                  h->cfg.drop_hint, h->d_partials, h->d_err, b->d_stage + W * i, h->stream));
         h->launches += 3;
-        double* slot = b->h_stage + W * i;
-        CKB(b, cudaMemcpyAsync(slot, h->d_red, sizeof(double) * NRED, cudaMemcpyDeviceToHost, h->stream));
-        CKB(b, cudaMemcpyAsync(slot + NRED, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         if (rho_hosts && rho_hosts[i])
             CKB(b, cudaMemcpyAsync(rho_hosts[i], h->d_rho, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
         if (u_hosts && u_hosts[i])
             CKB(b, cudaMemcpyAsync(u_hosts[i], h->d_u, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost,
                                    h->stream));
     }
+    CKB(b, cudaMemcpyAsync(b->h_stage, b->d_stage, sizeof(double) * W * n, cudaMemcpyDeviceToHost, b->stream));
     CKB(b, cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < n; ++i) {
         unsigned flags = 0;

@@ -8,6 +8,7 @@
 
 #include "kernels.h"
 #include "lattice.cuh"
+#include "reduce.h"
 
 namespace lbmwet {
 
@@ -162,7 +163,9 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
     block_combine(v, partials + (long long)blockIdx.x * NRED);
 }
 
-__global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+// err (optional): the grid's error word, stored after the NRED results
+__global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out,
+                                                   const unsigned* __restrict__ err = nullptr) {
     double v[NRED];
     init_slots(v);
     for (int i = threadIdx.x; i < nparts; i += RB) {
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ pa
         }
     }
     block_combine(v, out);
+    if (err && threadIdx.x == 0) *reinterpret_cast<unsigned*>(out + NRED) = *err;
 }
 
 // About 8 nodes per thread: each block ends with warp reductions of NRED doubles on the FP64 pipe,
@@ -200,6 +204,21 @@ cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uin
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_final<<<1, RB, 0, s>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_slot(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny,
+                               int nz, double rho_mid, const double* hint, double* partials, const unsigned* err,
+                               double* out, cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    const int nb = n_blocks(N);
+    if (dim == 2)
+        reduce_partial<2><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    else
+        reduce_partial<3><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_final<<<1, RB, 0, s>>>(partials, nb, out, err);
     return cudaGetLastError();
 }
 
