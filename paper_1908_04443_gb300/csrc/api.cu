@@ -1097,6 +1097,7 @@ struct lbm_batch {
     std::string err;
     double* h_stage = nullptr;         // pinned: per instance the reduction sums and the error word
     double* d_stage = nullptr;         // the same on the device, filled by the reductions, copied at once
+    RedGrid* d_redgrids = nullptr;     // the instances' reduction table (one reduction launch for all)
 };
 
 namespace {
@@ -1159,6 +1160,7 @@ void batch_free(lbm_batch* b) {
     if (b->h_stage) cudaFreeHost(b->h_stage);
     b->h_stage = nullptr;
     dfree(b->d_stage, b->stream);
+    dfree(b->d_redgrids, b->stream);
     for (lbm_handle* h : b->inst) {
         h->batch_member = false;
         lbm_destroy(h);
@@ -1651,17 +1653,40 @@ lbm_status lbm_batch_observables_fields(lbm_batch* b, lbm_obs* out_n, double* co
     if (!b->h_stage)
         CKB(b, cudaHostAlloc(reinterpret_cast<void**>(&b->h_stage), sizeof(double) * W * n, cudaHostAllocDefault));
     if (!b->d_stage) CKB(b, dmalloc(&b->d_stage, sizeof(double) * W * n, b->stream));
-    // every instance's fields and reduction on the batch's stream, each instance's sums and error
-    // word into its slot of one device array, one copy of the array, then one synchronisation
+    if (!b->d_redgrids) CKB(b, dmalloc(&b->d_redgrids, sizeof(RedGrid) * n, b->stream));
+    // every instance's fields pass on the batch's stream, then the reductions of all instances in one
+    // pair of launches, each instance's sums and error word into its slot of one device array, one
+    // copy of the array, then one synchronisation
+    std::vector<RedGrid> tab(n);
+    int total = 0;
     for (size_t i = 0; i < n; ++i) {
         lbm_handle* h = b->inst[i];
         lbm_status st = ensure_obs_buffers(h);
         if (st != LBM_OK) return bfail(b, st, "instance " + std::to_string(i) + ": " + h->err);
         CKB(b, launch_fields(h->lat, h->prec, h->f[h->cur], h->dp, h->d_rho, h->d_u, h->stream));
-        const double mid = 0.5 * (h->rho_l + h->rho_g);
-        CKB(b, launch_reduce_slot(h->D, h->d_rho, h->d_u, h->d_type, h->cfg.nx, h->cfg.ny, h->cfg.nz, mid,
-                                  h->cfg.drop_hint, h->d_partials, h->d_err, b->d_stage + W * i, h->stream));
-        h->launches += 3;
+        h->launches += 1;
+        RedGrid& r = tab[i];
+        r.rho = h->d_rho;
+        r.u = h->d_u;
+        r.type = h->d_type;
+        r.err = h->d_err;
+        r.partials = h->d_partials;
+        r.out = b->d_stage + W * i;
+        r.rho_mid = 0.5 * (h->rho_l + h->rho_g);
+        for (int k = 0; k < 3; ++k) r.hint[k] = h->cfg.drop_hint[k];
+        r.nx = h->cfg.nx;
+        r.ny = h->cfg.ny;
+        r.nz = h->cfg.nz;
+        r.block0 = total;
+        r.nblk = reduce_blocks(h->N);
+        total += r.nblk;
+    }
+    // (from pageable memory: staged before the call returns)
+    CKB(b, cudaMemcpyAsync(b->d_redgrids, tab.data(), sizeof(RedGrid) * n, cudaMemcpyHostToDevice, b->stream));
+    CKB(b, launch_reduce_grids(b->inst[0]->D, b->d_redgrids, int(n), total, b->stream));
+    b->inst[0]->launches += 2;
+    for (size_t i = 0; i < n; ++i) {
+        lbm_handle* h = b->inst[i];
         if (rho_hosts && rho_hosts[i])
             CKB(b, cudaMemcpyAsync(rho_hosts[i], h->d_rho, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
         if (u_hosts && u_hosts[i])

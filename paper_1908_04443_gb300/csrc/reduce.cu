@@ -74,11 +74,13 @@ __device__ __forceinline__ int wrapp(int v, int n) { return v >= n ? v - n : v; 
 __device__ __forceinline__ long long ord_bits(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
 __device__ __forceinline__ long long ord(double x) { return ord_bits(__double_as_longlong(x)); }
 
+// Block `blk` of `nblk` over one grid: its nodes blk * RB + threadIdx.x + k * nblk * RB, combined into
+// partials[blk * NRED ..].
 template <int DIM>
-__global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ rho, const double* __restrict__ u,
-                                                     const uint8_t* __restrict__ type, int nx, int ny, int nz,
-                                                     double rho_mid, double hx, double hy, double hz,
-                                                     double* __restrict__ partials) {
+__device__ __forceinline__ void partial_block(const double* __restrict__ rho, const double* __restrict__ u,
+                                              const uint8_t* __restrict__ type, int nx, int ny, int nz,
+                                              double rho_mid, double hx, double hy, double hz, int blk, int nblk,
+                                              double* __restrict__ partials) {
     const long long N = (long long)nx * ny * nz;
     double v[NRED];
     init_slots(v);
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
     // are already in order
     long long kmax = ord(-DBL_MAX), kmin = ord(DBL_MAX), ku = 0;
     const long long kmid = ord(rho_mid);
-    for (long long g = blockIdx.x * (long long)RB + threadIdx.x; g < N; g += (long long)gridDim.x * RB) {
+    for (long long g = blk * (long long)RB + threadIdx.x; g < N; g += (long long)nblk * RB) {
         // (32-bit division: a grid holds fewer than 2^31 / 19 nodes)
         const unsigned gu = unsigned(g), q = gu / unsigned(nx);
         const int x = int(gu - q * unsigned(nx));
@@ -160,12 +162,21 @@ __global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ 
     v[1] = __longlong_as_double(ord_bits(kmax));
     v[2] = __longlong_as_double(ord_bits(kmin));
     v[3] = __longlong_as_double(ku);
-    block_combine(v, partials + (long long)blockIdx.x * NRED);
+    block_combine(v, partials + (long long)blk * NRED);
 }
 
-// err (optional): the grid's error word, stored after the NRED results
-__global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out,
-                                                   const unsigned* __restrict__ err = nullptr) {
+template <int DIM>
+__global__ void __launch_bounds__(RB) reduce_partial(const double* __restrict__ rho, const double* __restrict__ u,
+                                                     const uint8_t* __restrict__ type, int nx, int ny, int nz,
+                                                     double rho_mid, double hx, double hy, double hz,
+                                                     double* __restrict__ partials) {
+    partial_block<DIM>(rho, u, type, nx, ny, nz, rho_mid, hx, hy, hz, blockIdx.x, gridDim.x, partials);
+}
+
+// One block combining nparts partials; err (optional): the grid's error word, stored after the NRED
+// results
+__device__ __forceinline__ void final_block(const double* __restrict__ partials, int nparts, double* __restrict__ out,
+                                            const unsigned* __restrict__ err) {
     double v[NRED];
     init_slots(v);
     for (int i = threadIdx.x; i < nparts; i += RB) {
@@ -178,6 +189,31 @@ __global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ pa
     }
     block_combine(v, out);
     if (err && threadIdx.x == 0) *reinterpret_cast<unsigned*>(out + NRED) = *err;
+}
+
+__global__ void __launch_bounds__(RB) reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out,
+                                                   const unsigned* __restrict__ err = nullptr) {
+    final_block(partials, nparts, out, err);
+}
+
+// Several grids in one launch: grid k owns blocks [g[k].block0, g[k].block0 + g[k].nblk), which
+// cover its nodes exactly as a launch of g[k].nblk blocks of its own would (same sums, same order).
+template <int DIM>
+__global__ void __launch_bounds__(RB) reduce_partial_grids(const RedGrid* __restrict__ g, int ngrids) {
+    int lo = 0, hi = ngrids - 1;
+    while (lo < hi) {   // the last grid whose first block is at or before this one
+        const int mid = (lo + hi + 1) >> 1;
+        if (g[mid].block0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const RedGrid& r = g[lo];
+    partial_block<DIM>(r.rho, r.u, r.type, r.nx, r.ny, r.nz, r.rho_mid, r.hint[0], r.hint[1], r.hint[2],
+                       int(blockIdx.x) - r.block0, r.nblk, r.partials);
+}
+
+__global__ void __launch_bounds__(RB) reduce_final_grids(const RedGrid* __restrict__ g) {
+    const RedGrid& r = g[blockIdx.x];
+    final_block(r.partials, r.nblk, r.out, r.err);
 }
 
 // About 8 nodes per thread: each block ends with warp reductions of NRED doubles on the FP64 pipe,
@@ -207,18 +243,15 @@ cudaError_t launch_reduce(int dim, const double* rho, const double* u, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_slot(int dim, const double* rho, const double* u, const uint8_t* type, int nx, int ny,
-                               int nz, double rho_mid, const double* hint, double* partials, const unsigned* err,
-                               double* out, cudaStream_t s) {
-    const long long N = (long long)nx * ny * nz;
-    const int nb = n_blocks(N);
-    if (dim == 2)
-        reduce_partial<2><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
-    else
-        reduce_partial<3><<<nb, RB, 0, s>>>(rho, u, type, nx, ny, nz, rho_mid, hint[0], hint[1], hint[2], partials);
+int reduce_blocks(long long N) { return n_blocks(N); }
+
+cudaError_t launch_reduce_grids(int dim, const RedGrid* grids, int ngrids, int total_blocks, cudaStream_t s) {
+    if (ngrids < 1) return cudaSuccess;
+    if (dim == 2) reduce_partial_grids<2><<<total_blocks, RB, 0, s>>>(grids, ngrids);
+    else reduce_partial_grids<3><<<total_blocks, RB, 0, s>>>(grids, ngrids);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    reduce_final<<<1, RB, 0, s>>>(partials, nb, out, err);
+    reduce_final_grids<<<ngrids, RB, 0, s>>>(grids);
     return cudaGetLastError();
 }
 
