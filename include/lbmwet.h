@@ -385,8 +385,10 @@ int32_t lbm_batch_instance_kernel(const lbm_batch* b, int32_t i);
  * instances from their current state: the pair kernel (FP32) with 4, 3 and 2 resident CTAs per
  * SM, the tile kernel and the y-march, 2 warm-up steps then trial_steps (>= 2, rounded up to even)
  * steps between CUDA events.  The state is saved before and restored after the trials, so the
- * simulation is unchanged.  Each class then steps with its fastest candidate; instances of
- * different choices form groups whose kernels run as parallel branches of the captured steps.
+ * simulation is unchanged.  Each class then steps with its fastest candidate when that is more
+ * than 3 % faster than the first candidate (the kernel the batch runs untuned), else with the first:
+ * instances of different choices form groups whose kernels run as parallel branches of the
+ * captured steps, and a group of its own costs more than a near-tie gains.
  * The choices are kept per (device, lattice, precision, size class) for the process: a later
  * lbm_batch_init with LBM_KERNEL_AUTO uses them.  Synchronises the batch's stream.  Errors:
  * LBM_ERR_ARG (trial_steps < 2), LBM_ERR_CUDA, LBM_ERR_OOM. */

@@ -1537,8 +1537,14 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(saved[k], h->f[b->cur], h->fbytes, cudaMemcpyDeviceToDevice, b->stream);
             if (e != cudaSuccess) result = bfail(b, LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
         }
-        double best = 1e300;
-        TuneChoice pick = choice[mem[0]];
+        // The first candidate is the kernel the batch runs untuned; another one is taken only when it
+        // is faster by more than TUNE_MARGIN: a class whose choice differs from the others' forms a
+        // group of its own, stepped by a launch of its own, which costs more than a near-tie gains
+        // (a class choosing the tile kernel over the pair kernel on a 0.02 % difference made the 96-grid
+        // batch 8 % slower).
+        constexpr double TUNE_MARGIN = 0.03;
+        double best = 1e300, first_ms = 0.0;
+        TuneChoice pick = choice[mem[0]], best_c = pick;
         for (const TuneChoice& c : cand) {
             if (result != LBM_OK) break;
             BatchGroup g;
@@ -1565,11 +1571,13 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps) {
                           kv.first, mem.size(), nodes, kind_name(c.kind), c.ctas_per_sm, per_step,
                           nodes / (per_step * 1e3));
             report += line;
+            if (&c == &cand[0]) first_ms = per_step;
             if (per_step < best) {
                 best = per_step;
-                pick = c;
+                best_c = c;
             }
         }
+        pick = (best < (1.0 - TUNE_MARGIN) * first_ms) ? best_c : cand[0];
         // restore the state (the trials ran an even number of steps: the state is in f[cur] again)
         for (size_t k = 0; k < mem.size(); ++k) {
             if (!saved[k]) continue;
