@@ -79,6 +79,29 @@ def test_batched_step_matches_oracle(kernel):
         L.lbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_observables_report_an_unstable_instance(precision):
+    """An instance whose state has lost positivity (written from the host: every population -0.1,
+    so every fluid node's density is negative) makes the batched observables fail with its index:
+    the fields pass raises the instance's own flag on rho <= 0, and the flag reaches the host through
+    the one-launch reduction of all instances.  The other instances' flags stay clear."""
+    from paper_1908_04443_gb300 import lbmwet as L
+    cases = _cases("pair" if precision == "fp32" else "tile")
+    b = _batch(cases, precision)
+    try:
+        L.lbm_batch_step(b, 2)
+        assert len(L.lbm_batch_observables(b)) == len(cases)
+        L.lbm_set_state(L.lbm_batch_handle(b, 1), np.full(9 * cases[1].mask.size, -0.1), step=2)
+        for call in (lambda: L.lbm_batch_observables(b), lambda: L.lbm_batch_observables_fields(b)):
+            with pytest.raises(L.LbmError) as ei:
+                call()
+            assert ei.value.status == L.LBM_ERR_UNSTABLE
+            assert "instance 1:" in str(ei.value)
+        assert L.lbm_observables(L.lbm_batch_handle(b, 0)).step == 2
+    finally:
+        L.lbm_batch_destroy(b)
+
+
 def test_batch_member_rules():
     from paper_1908_04443_gb300 import lbmwet as L
     cases = _cases()
